@@ -1,0 +1,173 @@
+"""Seeded synthetic galactic-binary catalogs (inputs only; none of the subtraction's arithmetic).
+
+Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+written from its published definition.  Every number a catalog needs is a pure
+function of (seed, source index, stream), so any slice of a catalog can be
+regenerated independently and the same catalog is produced on any machine.
+
+Distributions (the synthetic stand-in for the paper's population catalogs):
+  f     : truncated power law p(f) ~ f^-gamma on [1e-4, 1e-2] Hz, by inverse CDF
+  A     : 1e-23 X (f / 1e-3 Hz)^(2/3), X ~ Gamma(shape k, scale 1) (Marsaglia-Tsang)
+  fdot  : (96/5) pi^(8/3) (G Mc / c^3)^(5/3) f^(11/3), Mc ~ U(0.2, 0.8) Msun
+          (the GW-driven chirp of Sec. II.A)
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+YEAR = 365.25 * 86400.0
+GMSUN_C3 = 4.925490947e-6  # G Msun / c^3 in seconds
+F_MIN, F_MAX = 1e-4, 1e-2
+
+_M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+_W0, _W1 = 0x9E3779B9, 0xBB67AE85
+_MASK = np.uint64(0xFFFFFFFF)
+_S32 = np.uint64(32)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0: int, k1: int):
+    """Philox4x32 with 10 rounds over arrays of 32-bit counters; returns 4 uint32 arrays."""
+    c0 = np.asarray(c0, dtype=np.uint64) & _MASK
+    c1 = np.asarray(c1, dtype=np.uint64) & _MASK
+    c2 = np.asarray(c2, dtype=np.uint64) & _MASK
+    c3 = np.asarray(c3, dtype=np.uint64) & _MASK
+    c0, c1, c2, c3 = np.broadcast_arrays(c0, c1, c2, c3)
+    k0 &= 0xFFFFFFFF
+    k1 &= 0xFFFFFFFF
+    for r in range(10):
+        if r:
+            k0 = (k0 + _W0) & 0xFFFFFFFF
+            k1 = (k1 + _W1) & 0xFFFFFFFF
+        p0 = _M0 * c0
+        p1 = _M1 * c2
+        hi0, lo0 = p0 >> _S32, p0 & _MASK
+        hi1, lo1 = p1 >> _S32, p1 & _MASK
+        c0, c1, c2, c3 = (hi1 ^ c1 ^ np.uint64(k0), lo1, hi0 ^ c3 ^ np.uint64(k1), lo0)
+    return (c0.astype(np.uint32), c1.astype(np.uint32), c2.astype(np.uint32),
+            c3.astype(np.uint32))
+
+
+def u53(a, b):
+    """Uniform double in (0, 1) from two 32-bit words (53 random bits, centred)."""
+    a = np.asarray(a, dtype=np.uint64) >> np.uint64(5)
+    b = np.asarray(b, dtype=np.uint64) >> np.uint64(6)
+    return ((a * np.uint64(67108864) + b).astype(np.float64) + 0.5) / 9007199254740992.0
+
+
+def u32(a):
+    """Uniform double in (0, 1) from one 32-bit word."""
+    return (np.asarray(a, dtype=np.float64) + 0.5) / 4294967296.0
+
+
+# Stream identifiers (third counter word).
+_STREAM_FM = 0          # f and chirp mass
+_STREAM_GAMMA = 1       # Gamma attempts use streams 1..16
+_MAX_GAMMA_TRIES = 16
+_STREAM_POP = 0xFFFFFFF0  # per-catalog population parameters
+
+
+def _power_law_icdf(u, gamma, fmin=F_MIN, fmax=F_MAX):
+    if abs(gamma - 1.0) < 1e-12:
+        return fmin * np.exp(u * math.log(fmax / fmin))
+    e = 1.0 - gamma
+    a, b = fmin ** e, fmax ** e
+    return (a + u * (b - a)) ** (1.0 / e)
+
+
+def _gamma(k: float, idx: np.ndarray, k0: int, k1: int):
+    """Gamma(k, 1), k >= 1, by Marsaglia-Tsang with counter-based attempts."""
+    if k < 1.0:
+        raise ValueError("shape must be >= 1")
+    d = k - 1.0 / 3.0
+    c = 1.0 / math.sqrt(9.0 * d)
+    out = np.full(idx.shape, d, dtype=np.float64)
+    todo = np.arange(idx.size)
+    lo = (idx & 0xFFFFFFFF).astype(np.uint64)
+    hi = (idx >> 32).astype(np.uint64)
+    for t in range(_MAX_GAMMA_TRIES):
+        if todo.size == 0:
+            break
+        x0, x1, x2, x3 = philox4x32_10(lo[todo], hi[todo], _STREAM_GAMMA + t, 0, k0, k1)
+        u1 = u53(x0, x1)
+        z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u32(x2))
+        v = 1.0 + c * z
+        ok = v > 0.0
+        v = np.where(ok, v * v * v, 1.0)
+        ua = u32(x3)
+        acc = ok & (np.log(ua) < 0.5 * z * z + d - d * v + d * np.log(v))
+        out[todo[acc]] = d * v[acc]
+        todo = todo[~acc]
+    return out
+
+
+@dataclass
+class Population:
+    gamma: float = 11.0 / 3.0    # power-law index of p(f) ~ f^-gamma
+    shape: float = 2.0           # Gamma shape of the amplitude factor X
+
+
+def catalog(n: int, seed: int, pop: Population | None = None, start: int = 0,
+            chunk: int = 1 << 22):
+    """Sources start .. start+n-1 of the catalog with this seed: returns (A, f, fdot) FP64."""
+    pop = pop or Population()
+    k0, k1 = seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF
+    A = np.empty(n)
+    f = np.empty(n)
+    fdot = np.empty(n)
+    pref = 96.0 / 5.0 * math.pi ** (8.0 / 3.0)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        idx = np.arange(start + s, start + e, dtype=np.int64)
+        lo = (idx & 0xFFFFFFFF).astype(np.uint64)
+        hi = (idx >> 32).astype(np.uint64)
+        x0, x1, x2, x3 = philox4x32_10(lo, hi, _STREAM_FM, 0, k0, k1)
+        fs = _power_law_icdf(u53(x0, x1), pop.gamma)
+        mc = (0.2 + 0.6 * u53(x2, x3)) * GMSUN_C3
+        X = _gamma(pop.shape, idx, k0, k1)
+        f[s:e] = fs
+        fdot[s:e] = pref * mc ** (5.0 / 3.0) * fs ** (11.0 / 3.0)
+        A[s:e] = 1e-23 * X * (fs / 1e-3) ** (2.0 / 3.0)
+    return A, f, fdot
+
+
+def population_draw(seed: int, index: int, gamma_range=(3.0, 4.5), shape_range=(1.5, 3.0)):
+    """Per-catalog population parameters drawn uniformly from the given ranges."""
+    x0, x1, x2, x3 = philox4x32_10(index & 0xFFFFFFFF, index >> 32, _STREAM_POP, 0,
+                                   seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    ug, uk = float(u53(x0, x1)), float(u53(x2, x3))
+    return Population(gamma=gamma_range[0] + ug * (gamma_range[1] - gamma_range[0]),
+                      shape=shape_range[0] + uk * (shape_range[1] - shape_range[0]))
+
+
+def job_draw(seed: int, index: int, n_range=(1e5, 3e7), years=(1, 2, 4)):
+    """Size and observation time of a batched catalog or served job: N log-uniform, T from a set."""
+    x0, x1, x2, x3 = philox4x32_10(index & 0xFFFFFFFF, index >> 32, _STREAM_POP + 1, 0,
+                                   seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    un, ut = float(u53(x0, x1)), float(u32(x2))
+    lo, hi = math.log(n_range[0]), math.log(n_range[1])
+    n = int(round(math.exp(lo + un * (hi - lo))))
+    T = years[min(len(years) - 1, int(ut * len(years)))] * YEAR
+    return n, T, float(u32(x3))
+
+
+# The benchmark and parity workloads (sizes, observation times, populations).
+@dataclass
+class Workload:
+    name: str
+    n_sources: int
+    T_obs: float
+    seed: int
+    pop: Population
+
+
+def workload(name: str) -> Workload:
+    if name == "nb1e4_1yr":
+        return Workload(name, 10_000, 1 * YEAR, 0, Population(11.0 / 3.0, 2.0))
+    if name == "nb1e6_4yr":
+        return Workload(name, 1_000_000, 4 * YEAR, 1, Population(11.0 / 3.0, 2.0))
+    if name == "nb3e7_4yr":
+        return Workload(name, 30_000_000, 4 * YEAR, 2, population_draw(2, 0))
+    raise KeyError(name)

@@ -1,0 +1,53 @@
+"""The seeded input generator: Philox4x32-10 known-answer vectors (Random123's
+published test vectors) and the catalog distributions."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2602_18560_gb300 import synth
+
+
+@pytest.mark.parametrize("ctr, key, expect", [
+    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+])
+def test_philox_known_answers(ctr, key, expect):
+    out = synth.philox4x32_10(*ctr, *key)
+    assert tuple(int(x) for x in out) == expect
+
+
+def test_catalog_is_a_pure_function_of_index():
+    a = synth.catalog(5000, 7)
+    b = synth.catalog(1000, 7, start=3000)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x[3000:4000], y)
+    c = synth.catalog(5000, 8)
+    assert not np.array_equal(a[0], c[0])
+
+
+def test_catalog_distributions():
+    pop = synth.Population(gamma=11.0 / 3.0, shape=2.0)
+    A, f, fdot = synth.catalog(200_000, 3, pop)
+    assert f.min() >= synth.F_MIN and f.max() <= synth.F_MAX
+    # power-law CDF at a few points
+    e = 1 - pop.gamma
+    for q in (1.2e-4, 2e-4, 5e-4):
+        cdf = (q**e - synth.F_MIN**e) / (synth.F_MAX**e - synth.F_MIN**e)
+        assert np.mean(f < q) == pytest.approx(cdf, abs=4e-3)
+    X = A / (1e-23 * (f / 1e-3) ** (2 / 3))
+    assert X.mean() == pytest.approx(pop.shape, rel=0.01)
+    assert X.var() == pytest.approx(pop.shape, rel=0.03)
+    mc = (fdot / (96 / 5 * math.pi ** (8 / 3) * f ** (11 / 3))) ** 0.6 / synth.GMSUN_C3
+    assert mc.min() >= 0.2 - 1e-9 and mc.max() <= 0.8 + 1e-9
+    assert mc.mean() == pytest.approx(0.5, abs=3e-3)
+
+
+def test_population_and_job_draws_in_range():
+    for i in range(50):
+        p = synth.population_draw(3, i)
+        assert 3.0 <= p.gamma <= 4.5 and 1.5 <= p.shape <= 3.0
+        n, T, _ = synth.job_draw(4, i)
+        assert 1e5 <= n <= 3e7 and T / synth.YEAR in (1, 2, 4)
