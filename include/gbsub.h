@@ -1,0 +1,176 @@
+/*
+ * gbsub.h -- C ABI of the GB300 library for the iterative galactic-binary
+ * subtraction of arXiv 2602.18560 (Sec. III.A and App. D, "Subtraction
+ * algorithm").
+ *
+ * A catalog of N_b sources (amplitude A, frequency f, frequency derivative
+ * fdot) goes in; the foreground S_gal(f_k) on the DFT grid f_k = k / T_obs
+ * inside [f_min, f_max], and the set of individually resolved sources, come out.
+ *
+ * Conventions shared by every call:
+ *   - Return codes: SUB_OK (0) or a negative SUB_E* code. SUB_ENOTCONVERGED
+ *     means the loop hit max_iter; the results are valid for the last
+ *     iteration (S_gal re-estimated from the final resolved set).
+ *   - sub_last_error() gives a human-readable reason for the last failure.
+ *   - All device work of a context is issued on one CUDA stream: the caller's
+ *     (sub_create's stream argument, a cudaStream_t) or one the context owns.
+ *     sub_load_catalog and sub_run only enqueue work; sub_run with a non-null
+ *     stats pointer, sub_get_stats, sub_get_spectrum and sub_get_resolved_mask
+ *     synchronise the stream before they return.
+ *   - Input and output buffers belong to the caller; the library copies from
+ *     and into them and keeps no pointer after the call returns.  A buffer is
+ *     host memory (SUB_HOST, pinned or pageable) or device memory of the
+ *     current device (SUB_DEVICE), as the `where` argument says.
+ *   - The context owns all of its device memory and frees it in sub_destroy.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef GBSUB_H
+#define GBSUB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define SUB_OK 0
+#define SUB_EINVAL (-1)          /* invalid argument or parameter                      */
+#define SUB_ENOMEM (-2)          /* device or host allocation failed                   */
+#define SUB_ECUDA (-3)           /* a CUDA runtime call failed                         */
+#define SUB_ENOTCONVERGED (-4)   /* max_iter reached; results valid, not converged     */
+#define SUB_ETIMEOUT (-5)        /* a bounded device wait gave up                      */
+#define SUB_EBUDGET (-6)         /* the context would exceed its hbm_budget            */
+#define SUB_ERANGE (-7)          /* a deposited power exceeded the fixed-point range   */
+#define SUB_ESTATE (-8)          /* call out of order (e.g. sub_run before a catalog)  */
+
+/* Running estimators of App. D: Eq. (running mean), Eq. (running median) with
+ * the chi^2_2 bias constant C = (1 - 2/(9 nu))^-3 = 729/512, and the median
+ * followed by the mean over the same window. */
+#define SUB_MEAN 0
+#define SUB_MEDIAN 1
+#define SUB_MEDIAN_MEAN 2
+
+/* Arithmetic of the per-iteration steps.  SUB_FP64: SNR and selection in FP64.
+ * SUB_MIXED: SNR and median selection in FP32 (rescaled units); deposition,
+ * window sums and the convergence test stay exact/FP64. */
+#define SUB_FP64 0
+#define SUB_MIXED 1
+
+/* Location of a caller buffer. */
+#define SUB_HOST 0
+#define SUB_DEVICE 1
+
+/* Problem statement (Sec. III.A: T_obs, band, grid 1/T_obs; App. C S_instr;
+ * App. D window N, rho_th, kappa). */
+typedef struct {
+  double T_obs;        /* observation time in seconds (> 0); grid spacing 1/T_obs   */
+  double f_min;        /* band lower edge in Hz (> 0); paper: 0.1 mHz               */
+  double f_max;        /* band upper edge in Hz (> f_min); paper: 10 mHz            */
+  int32_t window;      /* smoothing window N in bins, 1 .. 8192; paper: 2000        */
+  int32_t estimator;   /* SUB_MEAN | SUB_MEDIAN | SUB_MEDIAN_MEAN                   */
+  double rho_th;       /* SNR threshold (> 0); paper: 7                             */
+  double kappa;        /* pre-filter factor: candidates have rho_0 >= kappa rho_th  */
+  int32_t max_iter;    /* iteration cap (>= 1)                                      */
+  int32_t tdi2;        /* 1: apply the TDI-2.0 factor 4 sin^2(2 f/f*) (App. C)      */
+  int32_t precision;   /* SUB_FP64 | SUB_MIXED                                      */
+  int32_t reserved0;   /* must be 0                                                 */
+  double conv_rtol;    /* also stop when max_k |dS_n|/S_n <= conv_rtol; 0 = off     */
+  uint64_t hbm_budget; /* bytes of device memory the context may hold; 0 = no cap   */
+} sub_params;
+
+/* Result summary of sub_run. */
+typedef struct {
+  int32_t iterations;     /* loop iterations executed (the last one found no source) */
+  int32_t converged;      /* 1 if the loop stopped because nothing crossed rho_th    */
+  int64_t n_sources;      /* N_b of the loaded catalog                               */
+  int64_t n_candidates;   /* sources with rho_0 >= kappa rho_th                      */
+  int64_t n_resolved;     /* sources removed                                         */
+  int64_t n_bins;         /* bins in the band                                        */
+  int64_t k_lo;           /* DFT index of the first bin: f = (k_lo + j) / T_obs       */
+  int32_t status;         /* return code of the run                                  */
+  int32_t reserved;
+} sub_stats;
+
+typedef struct sub_ctx sub_ctx;
+
+/* Fill *p with the paper's defaults: T_obs = 4 yr, band [1e-4, 1e-2] Hz,
+ * window 2000, running mean, rho_th = 7, kappa = 1/7, max_iter = 100, TDI-2 on,
+ * FP64, no rtol, no budget.  Returns SUB_EINVAL if p is null. */
+int sub_params_default(sub_params* p);
+
+/* Create a context: validates *p, builds the grid k_lo .. k_hi
+ * (k_lo = ceil(f_min T), k_hi = floor(f_max T)) and the per-bin tables
+ * S_instr(f_k) and R(f_k) (App. B, App. C) on the device.
+ *   p      : parameters, copied.
+ *   stream : cudaStream_t to issue work on, or NULL for a stream the context owns.
+ *   out    : receives the context; *out is NULL on failure.
+ * Errors: SUB_EINVAL (bad parameters), SUB_ENOMEM, SUB_ECUDA, SUB_EBUDGET. */
+int sub_create(const sub_params* p, void* stream, sub_ctx** out);
+
+/* Copy a catalog of n sources into the context (SoA, FP64, n >= 0).
+ *   A    : strain amplitudes (>= 0), Eq. (GB waveform).
+ *   f    : frequencies in Hz at t = 0, Eq. (phase Taylor expansion).
+ *   fdot : frequency derivatives in Hz/s (either sign).
+ *   where: SUB_HOST or SUB_DEVICE for all three arrays.
+ * Replaces any previous catalog.  Errors: SUB_EINVAL, SUB_ENOMEM, SUB_EBUDGET,
+ * SUB_ECUDA. */
+int sub_load_catalog(sub_ctx* ctx, const double* A, const double* f, const double* fdot,
+                     int64_t n, int where);
+
+/* Run the subtraction of App. D on the loaded catalog:
+ *   rho_0 against S_instr; candidates rho_0 >= kappa rho_th; then repeat
+ *   { S_gal = estimator of the residual power; rho against S_instr + S_gal;
+ *     resolve every candidate with rho > rho_th } until none is resolved.
+ * The loop runs on the device.  If stats is non-null the call waits for the
+ * result and fills it; otherwise it returns after enqueueing.
+ * Returns SUB_OK, SUB_ENOTCONVERGED (results valid), SUB_ERANGE, SUB_ESTATE,
+ * SUB_ECUDA. */
+int sub_run(sub_ctx* ctx, sub_stats* stats);
+
+/* Wait for the last sub_run and fill *stats (also returns its status). */
+int sub_get_stats(sub_ctx* ctx, sub_stats* stats);
+
+/* Number of sources resolved in each iteration of the last run: hist[i] for
+ * iteration i+1, for min(cap, iterations) entries; returns that count (or a
+ * negative error code).  Synchronises. */
+int sub_get_history(sub_ctx* ctx, int32_t* hist, int32_t cap);
+
+/* Copy S_gal(f_k), k = k_lo .. k_hi, into S_gal (cap doubles at least n_bins).
+ * n_bins and k_lo may be null.  where: SUB_HOST or SUB_DEVICE.
+ * Errors: SUB_EINVAL (cap too small), SUB_ESTATE (no run yet), SUB_ECUDA. */
+int sub_get_spectrum(sub_ctx* ctx, double* S_gal, int64_t cap, int64_t* n_bins, int64_t* k_lo,
+                     int where);
+
+/* Copy the resolved mask in catalog order (1 = resolved) into mask[0 .. n).
+ * n must equal the catalog size.  where: SUB_HOST or SUB_DEVICE. */
+int sub_get_resolved_mask(sub_ctx* ctx, uint8_t* mask, int64_t n, int where);
+
+/* Apply the context's running estimator (window, estimator) to a given spectrum:
+ * out = est_W(P) over the n_bins bins of the band, as in Eqs. (running mean) /
+ * (running median) of App. D without S_instr; App. E applies the estimators to
+ * the residual data in this way.  P and out hold n doubles (n must equal
+ * n_bins; P >= 0) in `where` memory; they may not overlap.
+ * Errors: SUB_EINVAL, SUB_ECUDA.  Synchronises before returning. */
+int sub_estimate(sub_ctx* ctx, const double* P, double* out, int64_t n, int where);
+
+/* Copy the per-bin tables S_instr(f_k) (App. C, A channel, times the TDI-2
+ * factor when tdi2) and R(f_k) (App. B, same factor) into S and R (n_bins
+ * doubles each; either may be null).  where: SUB_HOST or SUB_DEVICE. */
+int sub_get_tables(sub_ctx* ctx, double* S, double* R, int64_t n, int where);
+
+/* Bytes of device memory the context holds now. */
+int64_t sub_device_bytes(const sub_ctx* ctx);
+
+/* Free the context and everything it owns; null is allowed. */
+void sub_destroy(sub_ctx* ctx);
+
+/* Reason for the last failure of a call on ctx (or of sub_create when ctx is
+ * null); never null. */
+const char* sub_last_error(const sub_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSUB_H */

@@ -1,0 +1,560 @@
+// C ABI of the GB300 subtraction library (declarations and contracts in include/gbsub.h).
+//
+// A context owns the grid, the per-bin tables, the catalog copy and every work buffer of a
+// run.  sub_run launches one CUDA graph: a pre-loop part (clear the spectrum, one pass over
+// the catalog) followed by a conditional WHILE node whose body is one iteration of App. D
+// (estimate S_gal, SNR of the candidates, remove the resolved ones, loop control).  The
+// loop condition is set on the device, so a run crosses the host/device boundary only when
+// the caller asks for results.
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <cstdarg>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gbsub.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace gbsub;
+
+struct sub_ctx {
+  sub_params p;
+  Grid grid;
+  SmoothPlan plan;
+  cudaStream_t stream = nullptr;   // where work is issued
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  int nsm = 0;
+  int device = 0;
+  // bookkeeping
+  std::vector<std::pair<void*, int64_t>> allocs;
+  int64_t bytes = 0;
+  std::string err;
+  // tables
+  double *S = nullptr, *R = nullptr, *gq = nullptr;
+  // spectrum and smoothing buffers
+  unsigned long long *acc_lo = nullptr, *acc_hi = nullptr;
+  double *P = nullptr, *M = nullptr, *Sg = nullptr;
+  unsigned long long* skey = nullptr;
+  uint16_t* srank = nullptr;
+  uint32_t* snap = nullptr;
+  unsigned long long *pre_lo = nullptr, *pre_hi = nullptr;
+  unsigned* uflow = nullptr;
+  // catalog and per-source buffers
+  int64_t N = -1;        // sources loaded (-1: none)
+  int64_t cap_N = 0;     // capacity of the per-source buffers
+  double *A = nullptr, *f = nullptr, *fdot = nullptr;
+  Cand* cand = nullptr;
+  unsigned char* cres = nullptr;
+  unsigned char* resolved = nullptr;
+  // run state
+  RunState* rs = nullptr;
+  int* new_hist = nullptr;
+  RunState* h_rs = nullptr;  // pinned copy
+  bool ran = false;
+  // graph
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int64_t graph_N = -1;
+  bool use_graph = true;
+};
+
+static std::string g_create_err = "no error";
+
+static void set_err(sub_ctx* c, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_create_err = buf;
+}
+
+#define CU(call, ctx)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      set_err(ctx, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return SUB_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+static int dalloc(sub_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (c->p.hbm_budget && (uint64_t)(c->bytes + (int64_t)bytes) > c->p.hbm_budget) {
+    set_err(c, "device memory budget exceeded: need %lld more bytes, hold %lld of %llu",
+            (long long)bytes, (long long)c->bytes, (unsigned long long)c->p.hbm_budget);
+    return SUB_EBUDGET;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_err(c, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return SUB_ENOMEM;
+  }
+  c->allocs.push_back(std::make_pair(*p, (int64_t)bytes));
+  c->bytes += (int64_t)bytes;
+  return SUB_OK;
+}
+
+static void dfree(sub_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i) {
+    if (c->allocs[i].first == p) {
+      c->bytes -= c->allocs[i].second;
+      c->allocs.erase(c->allocs.begin() + i);
+      break;
+    }
+  }
+  cudaFree(p);
+}
+
+static void drop_graph(sub_ctx* c) {
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->exec = nullptr;
+  c->graph = nullptr;
+  c->graph_N = -1;
+}
+
+extern "C" int sub_params_default(sub_params* p) {
+  if (!p) return SUB_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->T_obs = 4.0 * 365.25 * 86400.0;
+  p->f_min = 1e-4;
+  p->f_max = 1e-2;
+  p->window = 2000;
+  p->estimator = SUB_MEAN;
+  p->rho_th = 7.0;
+  p->kappa = 1.0 / 7.0;
+  p->max_iter = 100;
+  p->tdi2 = 1;
+  p->precision = SUB_FP64;
+  p->conv_rtol = 0.0;
+  p->hbm_budget = 0;
+  return SUB_OK;
+}
+
+static int validate(const sub_params* p, int64_t* k_lo, int64_t* n) {
+  if (!p) { set_err(nullptr, "params is null"); return SUB_EINVAL; }
+  if (!(p->T_obs > 0.0) || !std::isfinite(p->T_obs)) { set_err(nullptr, "T_obs must be > 0"); return SUB_EINVAL; }
+  if (!(p->f_min > 0.0) || !(p->f_max > p->f_min) || !std::isfinite(p->f_max)) {
+    set_err(nullptr, "band must satisfy 0 < f_min < f_max");
+    return SUB_EINVAL;
+  }
+  if (p->window < 1 || p->window > kMaxWindow) { set_err(nullptr, "window must be in 1..%d", kMaxWindow); return SUB_EINVAL; }
+  if (p->estimator < SUB_MEAN || p->estimator > SUB_MEDIAN_MEAN) { set_err(nullptr, "unknown estimator %d", p->estimator); return SUB_EINVAL; }
+  if (!(p->rho_th > 0.0) || !(p->kappa >= 0.0)) { set_err(nullptr, "rho_th must be > 0 and kappa >= 0"); return SUB_EINVAL; }
+  if (p->max_iter < 1) { set_err(nullptr, "max_iter must be >= 1"); return SUB_EINVAL; }
+  if (p->precision != SUB_FP64 && p->precision != SUB_MIXED) { set_err(nullptr, "unknown precision %d", p->precision); return SUB_EINVAL; }
+  if (!(p->conv_rtol >= 0.0)) { set_err(nullptr, "conv_rtol must be >= 0"); return SUB_EINVAL; }
+  double a = std::ceil(p->f_min * p->T_obs);
+  double b = std::floor(p->f_max * p->T_obs);
+  if (!(b >= a) || b - a + 1 > 16.0e6) { set_err(nullptr, "band holds %g bins (1 .. 16e6 allowed)", b - a + 1); return SUB_EINVAL; }
+  *k_lo = (int64_t)a;
+  *n = (int64_t)(b - a + 1);
+  return SUB_OK;
+}
+
+static SmoothPlan make_plan(int W, int64_t n) {
+  SmoothPlan pl;
+  pl.W = W;
+  int kc = ((W + 31) / 32) * 32;
+  if (kc < 32) kc = 32;
+  pl.Kc = kc;
+  pl.nw = kc / 32;
+  pl.nch = (int)((n + kc - 1) / kc);
+  pl.nsnap = kc / kSnapStride + 1;
+  int kp = 1;
+  while (kp < kc) kp <<= 1;
+  pl.kpad = kp;
+  pl.L = 32;
+  int t = (96 * 1024) / (8 * pl.nw);
+  t = (t / 32) * 32;
+  if (t > 128) t = 128;
+  if (t < 32) t = 32;
+  pl.slide_threads = t;
+  return pl;
+}
+
+extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
+  if (!out) { set_err(nullptr, "out is null"); return SUB_EINVAL; }
+  *out = nullptr;
+  int64_t k_lo, n;
+  int rc = validate(p, &k_lo, &n);
+  if (rc) return rc;
+  sub_ctx* c = new (std::nothrow) sub_ctx();
+  if (!c) { set_err(nullptr, "host allocation failed"); return SUB_ENOMEM; }
+  c->p = *p;
+  c->grid.T = p->T_obs;
+  c->grid.T2 = p->T_obs * p->T_obs;
+  c->grid.t5 = p->T_obs / 5.0;
+  c->grid.k_lo = k_lo;
+  c->grid.nb = n;
+  c->plan = make_plan(p->window, n);
+  auto fail = [&](int code) {
+    g_create_err = c->err;
+    sub_destroy(c);
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) { c->err = std::string("cudaGetDevice: ") + cudaGetErrorString(e); return fail(SUB_ECUDA); }
+  cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+  if (c->nsm <= 0) c->nsm = 1;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    // a blocking stream orders itself after work on the legacy default stream
+    e = cudaStreamCreate(&c->stream);
+    if (e != cudaSuccess) { c->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e); return fail(SUB_ECUDA); }
+    c->own_stream = true;
+  }
+  e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { c->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e); return fail(SUB_ECUDA); }
+  configure_kernels();
+  const SmoothPlan& pl = c->plan;
+  int64_t ncell = (int64_t)pl.nch * pl.Kc;
+  struct { void** p; size_t b; } want[] = {
+      {(void**)&c->S, (size_t)n * 8}, {(void**)&c->R, (size_t)n * 8}, {(void**)&c->gq, (size_t)n * 8},
+      {(void**)&c->acc_lo, (size_t)n * 8}, {(void**)&c->acc_hi, (size_t)n * 8},
+      {(void**)&c->P, (size_t)n * 8}, {(void**)&c->Sg, (size_t)n * 8},
+      {(void**)&c->pre_lo, (size_t)ncell * 8}, {(void**)&c->pre_hi, (size_t)ncell * 8},
+      {(void**)&c->uflow, (size_t)pl.nch * 4},
+      {(void**)&c->rs, sizeof(RunState)}, {(void**)&c->new_hist, (size_t)p->max_iter * 4},
+  };
+  for (auto& w : want) {
+    rc = dalloc(c, w.p, w.b);
+    if (rc) return fail(rc);
+  }
+  if (p->estimator != SUB_MEAN) {
+    rc = dalloc(c, (void**)&c->skey, (size_t)ncell * 8);
+    if (!rc) rc = dalloc(c, (void**)&c->srank, (size_t)ncell * 2);
+    if (!rc) rc = dalloc(c, (void**)&c->snap, (size_t)pl.nch * pl.nsnap * pl.nw * 4);
+    if (!rc && p->estimator == SUB_MEDIAN_MEAN) rc = dalloc(c, (void**)&c->M, (size_t)n * 8);
+    if (rc) return fail(rc);
+  }
+  e = cudaMallocHost((void**)&c->h_rs, sizeof(RunState));
+  if (e != cudaSuccess) { c->err = "cudaMallocHost failed"; return fail(SUB_ENOMEM); }
+  std::memset(c->h_rs, 0, sizeof(RunState));
+  launch_tables(c->grid, p->tdi2, c->S, c->R, c->gq, c->stream);
+  e = cudaMemsetAsync(c->Sg, 0, (size_t)n * 8, c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) { c->err = std::string("table build: ") + cudaGetErrorString(e); return fail(SUB_ECUDA); }
+  *out = c;
+  return SUB_OK;
+}
+
+extern "C" int sub_load_catalog(sub_ctx* c, const double* A, const double* f, const double* fdot,
+                                int64_t n, int where) {
+  if (!c) return SUB_EINVAL;
+  if (n < 0 || (n > 0 && (!A || !f || !fdot)) || (where != SUB_HOST && where != SUB_DEVICE)) {
+    set_err(c, "invalid catalog arguments");
+    return SUB_EINVAL;
+  }
+  if (n > ((int64_t)1 << 40)) { set_err(c, "catalog too large"); return SUB_EINVAL; }
+  if (n > c->cap_N || c->A == nullptr) {
+    drop_graph(c);
+    dfree(c, c->A); dfree(c, c->f); dfree(c, c->fdot);
+    dfree(c, c->cand); dfree(c, c->cres); dfree(c, c->resolved);
+    c->A = c->f = c->fdot = nullptr;
+    c->cand = nullptr;
+    c->cres = c->resolved = nullptr;
+    c->cap_N = 0;
+    c->N = -1;
+    int rc;
+    size_t m = (size_t)(n > 0 ? n : 1);
+    if ((rc = dalloc(c, (void**)&c->A, m * 8)) || (rc = dalloc(c, (void**)&c->f, m * 8)) ||
+        (rc = dalloc(c, (void**)&c->fdot, m * 8)) || (rc = dalloc(c, (void**)&c->cand, m * sizeof(Cand))) ||
+        (rc = dalloc(c, (void**)&c->cres, m)) || (rc = dalloc(c, (void**)&c->resolved, m))) {
+      return rc;
+    }
+    c->cap_N = (int64_t)m;
+  }
+  if (n > 0) {
+    cudaMemcpyKind k = where == SUB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CU(cudaMemcpyAsync(c->A, A, (size_t)n * 8, k, c->stream), c);
+    CU(cudaMemcpyAsync(c->f, f, (size_t)n * 8, k, c->stream), c);
+    CU(cudaMemcpyAsync(c->fdot, fdot, (size_t)n * 8, k, c->stream), c);
+  }
+  if (c->N != n) drop_graph(c);
+  c->N = n;
+  c->ran = false;
+  return SUB_OK;
+}
+
+// ---------------------------------------------------------------- enqueue helpers
+
+static double thr_q_of(const sub_ctx* c) {
+  double pre = c->p.kappa * c->p.rho_th;
+  // candidates: rho_0^2 = 4 sum(q) 2^-64 >= pre^2; the bound is lowered by 1e-12 relative so
+  // that rounding can only add candidates (a larger candidate set cannot change the result:
+  // S_n >= S_instr makes rho <= rho_0 < rho_th for every extra one).
+  return pre * pre / 4.0 * kQScale * (1.0 - 1e-12);
+}
+
+static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
+  const int64_t n = c->grid.nb;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->acc_lo, 0, (size_t)n * 8, st))) return e;
+  if ((e = cudaMemsetAsync(c->acc_hi, 0, (size_t)n * 8, st))) return e;
+  if ((e = cudaMemsetAsync(c->rs, 0, sizeof(RunState), st))) return e;
+  if ((e = cudaMemsetAsync(c->new_hist, 0, (size_t)c->p.max_iter * 4, st))) return e;
+  if (c->N > 0) {
+    if ((e = cudaMemsetAsync(c->resolved, 0, (size_t)c->N, st))) return e;
+    if ((e = cudaMemsetAsync(c->cres, 0, (size_t)c->N, st))) return e;
+  }
+  launch_prepass(c->A, c->f, c->fdot, c->N, c->grid, c->gq, thr_q_of(c), c->acc_lo, c->acc_hi,
+                 c->cand, c->rs, c->nsm, st);
+  return cudaGetLastError();
+}
+
+static cudaError_t enqueue_body(sub_ctx* c, cudaStream_t st, unsigned long long handle, int use_cond) {
+  const int64_t n = c->grid.nb;
+  const SmoothPlan& pl = c->plan;
+  const int rtol_on = c->p.conv_rtol > 0.0 ? 1 : 0;
+  RunState* rs = c->rs;
+  launch_q2p(c->acc_lo, c->acc_hi, c->S, n, c->P, rs, 0, st);
+  switch (c->p.estimator) {
+    case SUB_MEAN:
+      launch_chunk_prefix(c->P, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st);
+      launch_window_mean(c->P, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, c->Sg, c->S, rtol_on, rs, st);
+      break;
+    case SUB_MEDIAN:
+      launch_chunk_sort(c->P, n, pl, c->skey, c->srank, c->snap, rs, st);
+      launch_median_slide(c->skey, c->srank, c->snap, n, pl, c->Sg, nullptr, c->S, rtol_on, rs, st);
+      break;
+    default:
+      launch_chunk_sort(c->P, n, pl, c->skey, c->srank, c->snap, rs, st);
+      launch_median_slide(c->skey, c->srank, c->snap, n, pl, c->M, &rs->max_m_bits, c->S, 0, rs, st);
+      launch_chunk_prefix(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st);
+      launch_window_mean(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, c->Sg, c->S, rtol_on, rs, st);
+      break;
+  }
+  double th2 = c->p.rho_th * c->p.rho_th;
+  launch_snr_resolve(c->cand, c->N > 0 ? c->N : 1, c->grid, c->S, c->R, c->gq, c->Sg, th2,
+                     c->p.conv_rtol, c->cres, c->resolved, c->acc_lo, c->acc_hi, rs, c->nsm, st);
+  launch_control(rs, c->p.max_iter, c->p.conv_rtol, c->new_hist, handle, use_cond, st);
+  return cudaGetLastError();
+}
+
+static int build_graph(sub_ctx* c) {
+  drop_graph(c);
+  cudaGraph_t g = nullptr, pre = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e) { set_err(c, "cudaGraphCreate: %s", cudaGetErrorString(e)); return SUB_ECUDA; }
+  e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (!e) {
+    cudaError_t e2 = enqueue_pre(c, c->cap_stream);
+    e = cudaStreamEndCapture(c->cap_stream, &pre);
+    if (!e) e = e2;
+  }
+  cudaGraphNode_t pre_node = nullptr, cond_node = nullptr;
+  if (!e) e = cudaGraphAddChildGraphNode(&pre_node, g, nullptr, 0, pre);
+  if (pre) cudaGraphDestroy(pre);
+  cudaGraphConditionalHandle h = 0;
+  if (!e) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (!e) e = cudaGraphAddNode(&cond_node, g, &pre_node, nullptr, 1, &cp);
+  if (!e) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (!e) {
+      cudaError_t e2 = enqueue_body(c, c->cap_stream, (unsigned long long)h, 1);
+      cudaGraph_t got = nullptr;
+      e = cudaStreamEndCapture(c->cap_stream, &got);
+      if (!e) e = e2;
+    }
+  }
+  if (!e) e = cudaGraphInstantiate(&c->exec, g, 0);
+  if (e) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    c->exec = nullptr;
+    set_err(c, "graph build failed: %s", cudaGetErrorString(e));
+    return SUB_ECUDA;
+  }
+  c->graph = g;
+  c->graph_N = c->N;
+  return SUB_OK;
+}
+
+static int run_host_loop(sub_ctx* c) {
+  CU(enqueue_pre(c, c->stream), c);
+  for (int it = 0; it <= c->p.max_iter + 1; ++it) {
+    CU(enqueue_body(c, c->stream, 0ull, 0), c);
+    CU(cudaMemcpyAsync(c->h_rs, c->rs, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream), c);
+    CU(cudaStreamSynchronize(c->stream), c);
+    if (c->h_rs->stopped) break;
+  }
+  return SUB_OK;
+}
+
+static int fill_stats(sub_ctx* c, sub_stats* st) {
+  CU(cudaMemcpyAsync(c->h_rs, c->rs, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream), c);
+  CU(cudaStreamSynchronize(c->stream), c);
+  const RunState& r = *c->h_rs;
+  int status = SUB_OK;
+  if (r.err & ERR_RANGE) {
+    status = SUB_ERANGE;
+    set_err(c, "a deposited power exceeded the fixed-point range (P/S_instr >= 2^31 in one bin)");
+  } else if (!r.converged) {
+    status = SUB_ENOTCONVERGED;
+    set_err(c, "max_iter (%d) reached before convergence", c->p.max_iter);
+  }
+  if (st) {
+    st->iterations = r.iter;
+    st->converged = r.converged;
+    st->n_sources = c->N;
+    st->n_candidates = (int64_t)r.ncand;
+    st->n_resolved = (int64_t)r.nres;
+    st->n_bins = c->grid.nb;
+    st->k_lo = c->grid.k_lo;
+    st->status = status;
+    st->reserved = 0;
+  }
+  return status;
+}
+
+extern "C" int sub_run(sub_ctx* c, sub_stats* st) {
+  if (!c) return SUB_EINVAL;
+  if (c->N < 0) { set_err(c, "no catalog loaded"); return SUB_ESTATE; }
+  if (c->use_graph && c->graph_N != c->N) {
+    if (build_graph(c) != SUB_OK) c->use_graph = false;  // conditional nodes unavailable
+  }
+  if (c->use_graph) {
+    CU(cudaGraphLaunch(c->exec, c->stream), c);
+  } else {
+    int rc = run_host_loop(c);
+    if (rc) return rc;
+  }
+  c->ran = true;
+  if (!st) return SUB_OK;
+  return fill_stats(c, st);
+}
+
+extern "C" int sub_get_stats(sub_ctx* c, sub_stats* st) {
+  if (!c || !st) return SUB_EINVAL;
+  if (!c->ran) { set_err(c, "no run yet"); return SUB_ESTATE; }
+  return fill_stats(c, st);
+}
+
+extern "C" int sub_get_spectrum(sub_ctx* c, double* S_gal, int64_t cap, int64_t* n_bins,
+                                int64_t* k_lo, int where) {
+  if (!c) return SUB_EINVAL;
+  if (n_bins) *n_bins = c->grid.nb;
+  if (k_lo) *k_lo = c->grid.k_lo;
+  if (!S_gal) return SUB_OK;
+  if (cap < c->grid.nb) { set_err(c, "cap %lld < n_bins %lld", (long long)cap, (long long)c->grid.nb); return SUB_EINVAL; }
+  if (where != SUB_HOST && where != SUB_DEVICE) { set_err(c, "bad where"); return SUB_EINVAL; }
+  if (!c->ran) { set_err(c, "no run yet"); return SUB_ESTATE; }
+  CU(cudaMemcpyAsync(S_gal, c->Sg, (size_t)c->grid.nb * 8,
+                     where == SUB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream), c);
+  CU(cudaStreamSynchronize(c->stream), c);
+  return SUB_OK;
+}
+
+extern "C" int sub_get_resolved_mask(sub_ctx* c, uint8_t* mask, int64_t n, int where) {
+  if (!c) return SUB_EINVAL;
+  if (!c->ran) { set_err(c, "no run yet"); return SUB_ESTATE; }
+  if (n != c->N || (n > 0 && !mask)) { set_err(c, "mask length %lld != catalog %lld", (long long)n, (long long)c->N); return SUB_EINVAL; }
+  if (where != SUB_HOST && where != SUB_DEVICE) { set_err(c, "bad where"); return SUB_EINVAL; }
+  if (n == 0) return SUB_OK;
+  CU(cudaMemcpyAsync(mask, c->resolved, (size_t)n,
+                     where == SUB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream), c);
+  CU(cudaStreamSynchronize(c->stream), c);
+  return SUB_OK;
+}
+
+extern "C" int sub_get_history(sub_ctx* c, int32_t* hist, int32_t cap) {
+  if (!c || (cap > 0 && !hist)) return SUB_EINVAL;
+  if (!c->ran) { set_err(c, "no run yet"); return SUB_ESTATE; }
+  CU(cudaMemcpyAsync(c->h_rs, c->rs, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream), c);
+  CU(cudaStreamSynchronize(c->stream), c);
+  int m = c->h_rs->iter < cap ? c->h_rs->iter : cap;
+  if (m > 0) {
+    CU(cudaMemcpy(hist, c->new_hist, (size_t)m * 4, cudaMemcpyDeviceToHost), c);
+  }
+  return m;
+}
+
+extern "C" int sub_estimate(sub_ctx* c, const double* P, double* out, int64_t n, int where) {
+  if (!c) return SUB_EINVAL;
+  if (n != c->grid.nb || !P || !out) { set_err(c, "sub_estimate needs n == n_bins (%lld) and two buffers", (long long)c->grid.nb); return SUB_EINVAL; }
+  if (where != SUB_HOST && where != SUB_DEVICE) { set_err(c, "bad where"); return SUB_EINVAL; }
+  const SmoothPlan& pl = c->plan;
+  cudaStream_t st = c->stream;
+  double* in = c->P;
+  double* res = c->Sg;
+  cudaMemcpyKind k_in = where == SUB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaMemcpyKind k_out = where == SUB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CU(cudaMemcpyAsync(in, P, (size_t)n * 8, k_in, st), c);
+  CU(cudaMemsetAsync(c->rs, 0, sizeof(RunState), st), c);
+  RunState* rs = c->rs;
+  // the maximum of the input fixes the fixed-point scale of the window sums
+  launch_max_bits(in, n, &rs->max_p_bits, st);
+  switch (c->p.estimator) {
+    case SUB_MEAN:
+      launch_chunk_prefix(in, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st);
+      launch_window_mean(in, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, res, c->S, 0, rs, st);
+      break;
+    case SUB_MEDIAN:
+      launch_chunk_sort(in, n, pl, c->skey, c->srank, c->snap, rs, st);
+      launch_median_slide(c->skey, c->srank, c->snap, n, pl, res, nullptr, c->S, 0, rs, st);
+      break;
+    default:
+      launch_chunk_sort(in, n, pl, c->skey, c->srank, c->snap, rs, st);
+      launch_median_slide(c->skey, c->srank, c->snap, n, pl, c->M, &rs->max_m_bits, c->S, 0, rs, st);
+      launch_chunk_prefix(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st);
+      launch_window_mean(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, res, c->S, 0, rs, st);
+      break;
+  }
+  CU(cudaGetLastError(), c);
+  CU(cudaMemcpyAsync(out, res, (size_t)n * 8, k_out, st), c);
+  CU(cudaStreamSynchronize(st), c);
+  c->ran = false;  // the run's S_gal was overwritten
+  return SUB_OK;
+}
+
+extern "C" int sub_get_tables(sub_ctx* c, double* S, double* R, int64_t n, int where) {
+  if (!c) return SUB_EINVAL;
+  if (n != c->grid.nb) { set_err(c, "n must equal n_bins"); return SUB_EINVAL; }
+  if (where != SUB_HOST && where != SUB_DEVICE) { set_err(c, "bad where"); return SUB_EINVAL; }
+  cudaMemcpyKind k = where == SUB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (S) CU(cudaMemcpyAsync(S, c->S, (size_t)n * 8, k, c->stream), c);
+  if (R) CU(cudaMemcpyAsync(R, c->R, (size_t)n * 8, k, c->stream), c);
+  CU(cudaStreamSynchronize(c->stream), c);
+  return SUB_OK;
+}
+
+extern "C" int64_t sub_device_bytes(const sub_ctx* c) { return c ? c->bytes : 0; }
+
+extern "C" void sub_destroy(sub_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  for (auto& q : c->allocs) cudaFree(q.first);
+  c->allocs.clear();
+  if (c->h_rs) cudaFreeHost(c->h_rs);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+extern "C" const char* sub_last_error(const sub_ctx* c) {
+  return c ? c->err.c_str() : g_create_err.c_str();
+}

@@ -1,0 +1,291 @@
+"""Python binding of libgbsub.so (C ABI declared in include/gbsub.h).
+
+Argument marshalling only: every step of the subtraction runs in the library's
+CUDA kernels.  Functions keep the C names (sub_create, sub_load_catalog, sub_run,
+sub_get_spectrum, sub_get_resolved_mask, sub_destroy, ...); ``Subtraction`` wraps
+a context for convenience.  Buffers are numpy arrays (host memory) or torch CUDA
+tensors (device memory, passed by data_ptr()).  There is no fallback: if the
+library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ETIMEOUT, EBUDGET, ERANGE, ESTATE = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+MEAN, MEDIAN, MEDIAN_MEAN = 0, 1, 2
+FP64, MIXED = 0, 1
+HOST, DEVICE = 0, 1
+YEAR = 365.25 * 86400.0
+
+_ERRNAMES = {OK: "SUB_OK", EINVAL: "SUB_EINVAL", ENOMEM: "SUB_ENOMEM", ECUDA: "SUB_ECUDA",
+             ENOTCONVERGED: "SUB_ENOTCONVERGED", ETIMEOUT: "SUB_ETIMEOUT",
+             EBUDGET: "SUB_EBUDGET", ERANGE: "SUB_ERANGE", ESTATE: "SUB_ESTATE"}
+
+
+class SubError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_ERRNAMES.get(code, code), msg))
+        self.code = code
+
+
+class sub_params(ctypes.Structure):
+    _fields_ = [
+        ("T_obs", ctypes.c_double), ("f_min", ctypes.c_double), ("f_max", ctypes.c_double),
+        ("window", ctypes.c_int32), ("estimator", ctypes.c_int32),
+        ("rho_th", ctypes.c_double), ("kappa", ctypes.c_double),
+        ("max_iter", ctypes.c_int32), ("tdi2", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("conv_rtol", ctypes.c_double), ("hbm_budget", ctypes.c_uint64),
+    ]
+
+
+class sub_stats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+        ("n_sources", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
+        ("n_resolved", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("k_lo", ctypes.c_int64),
+        ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+_lock = threading.Lock()
+EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_run", "sub_get_stats",
+           "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
+           "sub_get_tables", "sub_device_bytes", "sub_destroy", "sub_last_error")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libgbsub.so (building it first if it is missing and nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError("libgbsub.so is not built: run paper_2602_18560_gb300.build")
+            _build.build()
+        L = ctypes.CDLL(path)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        sig = {
+            "sub_params_default": (i32, [ctypes.POINTER(sub_params)]),
+            "sub_create": (i32, [ctypes.POINTER(sub_params), P, ctypes.POINTER(P)]),
+            "sub_load_catalog": (i32, [P, P, P, P, i64, i32]),
+            "sub_run": (i32, [P, ctypes.POINTER(sub_stats)]),
+            "sub_get_stats": (i32, [P, ctypes.POINTER(sub_stats)]),
+            "sub_get_history": (i32, [P, P, i32]),
+            "sub_get_spectrum": (i32, [P, P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), i32]),
+            "sub_get_resolved_mask": (i32, [P, P, i64, i32]),
+            "sub_estimate": (i32, [P, P, P, i64, i32]),
+            "sub_get_tables": (i32, [P, P, P, i64, i32]),
+            "sub_device_bytes": (i64, [P]),
+            "sub_destroy": (None, [P]),
+            "sub_last_error": (ctypes.c_char_p, [P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return _lib
+
+
+# ------------------------------------------------------------------ marshalling
+
+def _is_torch(x):
+    return hasattr(x, "data_ptr") and hasattr(x, "is_cuda")
+
+
+def _ptr(x, dtype):
+    """(pointer, where, n) of a numpy array (host) or a torch CUDA tensor (device)."""
+    if x is None:
+        return None, HOST, 0
+    if _is_torch(x):
+        import torch
+        want = {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError("tensor must be contiguous %s" % want)
+        if x.is_cuda:
+            # the library's stream waits for nothing torch queued: make it visible first
+            torch.cuda.current_stream(x.device).synchronize()
+            return ctypes.c_void_p(x.data_ptr()), DEVICE, x.numel()
+        return ctypes.c_void_p(x.data_ptr()), HOST, x.numel()
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError("array must be contiguous %s" % np.dtype(dtype))
+    return a.ctypes.data_as(ctypes.c_void_p), HOST, a.size
+
+
+def _check(ctx, rc, allow=()):
+    if rc < 0 and rc not in allow:
+        raise SubError(rc, lib().sub_last_error(ctx).decode())
+    return rc
+
+
+def sub_params_default(**overrides) -> sub_params:
+    p = sub_params()
+    _check(None, lib().sub_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def sub_create(params: sub_params, stream=None):
+    ctx = ctypes.c_void_p()
+    st = ctypes.c_void_p(int(stream) if stream else 0)
+    rc = lib().sub_create(ctypes.byref(params), st, ctypes.byref(ctx))
+    if rc != OK:
+        raise SubError(rc, lib().sub_last_error(None).decode())
+    return ctx
+
+
+def sub_load_catalog(ctx, A, f, fdot):
+    (pa, wa, na), (pf, wf, nf), (pd, wd, nd) = (_ptr(A, np.float64), _ptr(f, np.float64),
+                                                _ptr(fdot, np.float64))
+    if not (na == nf == nd) or not (wa == wf == wd):
+        raise ValueError("A, f, fdot must have the same length and location")
+    return _check(ctx, lib().sub_load_catalog(ctx, pa, pf, pd, na, wa))
+
+
+def sub_run(ctx, wait: bool = True):
+    if not wait:
+        _check(ctx, lib().sub_run(ctx, None))
+        return None
+    st = sub_stats()
+    _check(ctx, lib().sub_run(ctx, ctypes.byref(st)), allow=(ENOTCONVERGED,))
+    return st
+
+
+def sub_get_stats(ctx):
+    st = sub_stats()
+    _check(ctx, lib().sub_get_stats(ctx, ctypes.byref(st)), allow=(ENOTCONVERGED,))
+    return st
+
+
+def sub_get_history(ctx, cap: int = 1024):
+    h = np.zeros(cap, np.int32)
+    m = _check(ctx, lib().sub_get_history(ctx, h.ctypes.data_as(ctypes.c_void_p), cap))
+    return h[:m]
+
+
+def n_bins_of(ctx):
+    n = ctypes.c_int64()
+    k = ctypes.c_int64()
+    _check(ctx, lib().sub_get_spectrum(ctx, None, 0, ctypes.byref(n), ctypes.byref(k), HOST))
+    return n.value, k.value
+
+
+def sub_get_spectrum(ctx, out=None):
+    nb, _ = n_bins_of(ctx)
+    if out is None:
+        out = np.empty(nb)
+    p, w, n = _ptr(out, np.float64)
+    _check(ctx, lib().sub_get_spectrum(ctx, p, n, None, None, w))
+    return out
+
+
+def sub_get_resolved_mask(ctx, n: int, out=None):
+    if out is None:
+        out = np.empty(n, np.uint8)
+    p, w, m = _ptr(out, np.uint8)
+    _check(ctx, lib().sub_get_resolved_mask(ctx, p, m, w))
+    return out
+
+
+def sub_estimate(ctx, P, out=None):
+    if out is None:
+        out = np.empty_like(P) if not _is_torch(P) else P.new_empty(P.shape)
+    pi, wi, n = _ptr(P, np.float64)
+    po, wo, m = _ptr(out, np.float64)
+    if wi != wo or n != m:
+        raise ValueError("P and out must have the same length and location")
+    _check(ctx, lib().sub_estimate(ctx, pi, po, n, wi))
+    return out
+
+
+def sub_get_tables(ctx):
+    nb, _ = n_bins_of(ctx)
+    S = np.empty(nb)
+    R = np.empty(nb)
+    _check(ctx, lib().sub_get_tables(ctx, S.ctypes.data_as(ctypes.c_void_p),
+                                     R.ctypes.data_as(ctypes.c_void_p), nb, HOST))
+    return S, R
+
+
+def sub_device_bytes(ctx) -> int:
+    return lib().sub_device_bytes(ctx)
+
+
+def sub_destroy(ctx):
+    if ctx:
+        lib().sub_destroy(ctx)
+
+
+class Subtraction:
+    """One context: ``Subtraction(T_obs=..., window=..., estimator=...)``."""
+
+    def __init__(self, params: sub_params | None = None, stream=None, **kw):
+        self.params = params if params is not None else sub_params_default(**kw)
+        self.ctx = sub_create(self.params, stream)
+        self.n_sources = None
+
+    def load(self, A, f, fdot):
+        sub_load_catalog(self.ctx, A, f, fdot)
+        self.n_sources = int(len(A))
+        return self
+
+    def run(self, wait=True):
+        return sub_run(self.ctx, wait)
+
+    def spectrum(self, out=None):
+        return sub_get_spectrum(self.ctx, out)
+
+    def resolved(self, out=None):
+        return sub_get_resolved_mask(self.ctx, self.n_sources, out)
+
+    def history(self):
+        return sub_get_history(self.ctx)
+
+    def estimate(self, P, out=None):
+        return sub_estimate(self.ctx, P, out)
+
+    def tables(self):
+        return sub_get_tables(self.ctx)
+
+    @property
+    def grid(self):
+        return n_bins_of(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            sub_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
