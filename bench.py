@@ -1,0 +1,409 @@
+"""Benchmark of the GB300 subtraction path (one JSON line on stdout).
+
+Default workload: one catalog of N_b = 3e7 sources, T_obs = 4 yr, band 0.1-10 mHz,
+running median-then-mean over W = 1000 bins, rho_th = 7, kappa = 1/7, FP64 path.  A step
+is one sub_run: the pass over the device-resident catalog and every iteration of the
+subtraction until no source crosses the threshold.  Metric: sources subtracted per second
+to convergence (N_b / step time), whole job over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own catalog (seed + rank): weak scaling, no collective on
+the data path (replicas).  --impl reference times the FP64 CPU oracle on bounded samples of
+the same workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2602_18560_gb300 import synth  # noqa: E402
+
+EST = {"mean": 0, "median": 1, "median_mean": 2}
+GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize_nb3e7_4yr.json")
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="nb3e7_4yr")
+    ap.add_argument("--estimator", choices=list(EST), default="median_mean")
+    ap.add_argument("--window", type=int, default=1000)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rk = int(os.environ.get("RANK", "0"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rk, lr
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return FALLBACK_HBM, "of fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        if self.proc is not None:  # wait for the first sample so the region is covered
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.05)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def kernels_per_iteration(est):
+    return {0: 5, 1: 5, 2: 7}[est]
+
+
+def algorithmic_bytes(kernel, N, nb, ncand, plan_chunks, kc, nsnap):
+    """Bytes a kernel must move per launch (reads + writes of its inputs/outputs)."""
+    if kernel == "prepass":
+        return 24 * N + 16 * nb + 32 * ncand
+    if kernel == "q2p":
+        return 16 * nb + 8 * nb + 8 * nb
+    if kernel == "sort":
+        return 8 * nb + 8 * nb + 2 * nb + plan_chunks * nsnap * (kc // 32) * 4
+    if kernel == "slide":
+        return 8 * nb + 2 * nb + 8 * nb
+    if kernel == "prefix":
+        return 8 * nb + 16 * nb
+    if kernel == "mean":
+        return 16 * nb + 8 * nb
+    if kernel == "snr":
+        return 32 * ncand + 8 * 3 * ncand
+    return 0
+
+
+def cpu_oracle_sample(A, f, fdot, T, est, W, iters_hint):
+    """The oracle as it stands, one thread: a max_iter = 1 run on the full catalog
+    (the pre-filter, one iteration and the final re-estimate), scaled to a whole run
+    of `iters_hint` iterations as t * iters / 2."""
+    import oracle
+    oracle.lib()
+    t0 = time.perf_counter()
+    r = oracle.run(oracle.make_params(T_obs=T, estimator=est, window=W, max_iter=1), A, f, fdot)
+    dt = time.perf_counter() - t0
+    est_total = dt * max(1, iters_hint) / 2.0
+    return dt, est_total, r
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    w = synth.workload(args.workload)
+    A, f, fdot = synth.catalog(w.n_sources, w.seed, w.pop)
+    est = EST[args.estimator]
+    iters = 16
+    try:
+        with open(GOLDEN) as fh:
+            g = json.load(fh)
+        key = {2: "median_mean", 0: "mean"}.get(est)
+        if key and g["workload"] == w.name:
+            iters = g["estimators"][key]["iterations"]
+    except Exception:
+        pass
+    times = []
+    steps = min(args.steps, 3)  # each oracle step is a bounded sample of ~10-20 s
+    warm = min(args.warmup, 1)
+    for i in range(warm + steps):
+        dt, tot, _ = cpu_oracle_sample(A, f, fdot, w.T_obs, est, args.window, iters)
+        if i >= warm:
+            times.append(tot)
+    t = sum(times) / len(times)
+    value = w.n_sources / t
+    sample = ("oracle (1 thread) with max_iter=1 on the full %s catalog, i.e. pre-filter + one "
+              "iteration + final re-estimate, scaled by iterations/2 = %d/2" % (w.name, iters))
+    line = {"impl": "reference", "metric": "sources subtracted/sec to convergence",
+            "value": value, "unit": "sources/s", "n_gpus": ws, "steps": steps,
+            "warmup": warm, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "estimator": args.estimator, "window": args.window},
+            "cpu_baseline": {"value": value, "unit": "sources/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "sources/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local_rank = dist_env()
+    if args.impl == "reference":
+        if ws > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    from paper_2602_18560_gb300 import gbsub
+
+    w = synth.workload(args.workload)
+    seed = w.seed + 1000 * rank
+    A, f, fdot = synth.catalog(w.n_sources, seed, w.pop)
+    N = w.n_sources
+    est = EST[args.estimator]
+    stream = torch.cuda.Stream()
+    prm = gbsub.sub_params_default(T_obs=w.T_obs, window=args.window, estimator=est,
+                                   precision=0 if args.precision == "fp64" else 1)
+    sub = gbsub.Subtraction(prm, stream=stream.cuda_stream)
+    dev = [torch.from_numpy(x).to("cuda") for x in (A, f, fdot)]
+    torch.cuda.synchronize()
+    sub.load(*dev)
+    for _ in range(max(3, args.warmup)):
+        sub.run(wait=True)
+
+    # ---------------------------------------------------------------- timed region
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            gbsub.sub_run(sub.ctx, wait=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = gbsub.sub_get_stats(sub.ctx)
+    pre_ms, loop_ms, tot_ms = sub.timing()
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_max = float(t.item())
+    else:
+        ms_max = ms
+    value = ws * N / (ms_max * 1e-3)
+
+    # ---------------------------------------------------------------- parity vs stored oracle values
+    parity = None
+    sg = sub.spectrum()
+    res = sub.resolved()
+    if rank == 0 and w.name == "nb3e7_4yr" and os.path.exists(GOLDEN):
+        with open(GOLDEN) as fh:
+            g = json.load(fh)
+        key = {2: "median_mean", 0: "mean"}.get(est)
+        if key and g["window"] == args.window and args.precision == "fp64":
+            ge = g["estimators"][key]
+            idx = np.array(g["sample_bins"])
+            ref = np.array([float.fromhex(x) for x in ge["S_gal_sample"]])
+            nz = ref != 0
+            err = float(np.max(np.abs(sg[idx][nz] - ref[nz]) / ref[nz])) if nz.any() else 0.0
+            sha = hashlib.sha256(np.nonzero(res)[0].astype(np.int64).tobytes()).hexdigest()
+            parity = {"against": "oracle values in tests/golden", "S_gal_max_rel_err_sampled": err,
+                      "sampled_bins": int(idx.size), "zeros_match": bool(np.all(sg[idx][~nz] == 0)),
+                      "resolved_set_identical": sha == ge["resolved_sha256"],
+                      "iterations_match": st.iterations == ge["iterations"],
+                      "n_resolved": st.n_resolved, "n_resolved_oracle": ge["n_resolved"]}
+
+    # ---------------------------------------------------------------- per-kernel profile
+    prof_runs = 2
+    acc = {}
+    for _ in range(prof_runs):
+        pr, _ = sub.profile()
+        for k, (t, n) in pr.items():
+            a = acc.setdefault(k, [0.0, 0])
+            a[0] += t
+            a[1] += n
+    kernels = {k: {"ms_per_run": v[0] / prof_runs, "launches_per_run": v[1] / prof_runs}
+               for k, v in acc.items() if v[1] > 0}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_run"])
+    plan_kc = ((args.window + 31) // 32) * 32
+    nb = st.n_bins
+    nch = (nb + plan_kc - 1) // plan_kc
+    nsnap = plan_kc // 32 + 1
+    per_launch_ms = kernels[dom]["ms_per_run"] / kernels[dom]["launches_per_run"]
+    algo = algorithmic_bytes(dom, N, nb, st.n_candidates, nch, plan_kc, nsnap)
+    hbm, hbm_kind = peaks()
+    achieved = algo / (per_launch_ms * 1e-3) / 1e9
+    # the catalog pass separately (timed inside the graph of the last timed step)
+    pre_algo = algorithmic_bytes("prepass", N, nb, st.n_candidates, nch, plan_kc, nsnap)
+    whole_bytes = pre_algo + st.iterations * (
+        algorithmic_bytes("q2p", N, nb, 0, nch, plan_kc, nsnap)
+        + (algorithmic_bytes("sort", N, nb, 0, nch, plan_kc, nsnap)
+           + algorithmic_bytes("slide", N, nb, 0, nch, plan_kc, nsnap) if est else 0)
+        + (algorithmic_bytes("prefix", N, nb, 0, nch, plan_kc, nsnap)
+           + algorithmic_bytes("mean", N, nb, 0, nch, plan_kc, nsnap) if est != 1 else 0)
+        + algorithmic_bytes("snr", N, nb, st.n_candidates, nch, plan_kc, nsnap)) + N
+    traffic = None
+    prof_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof_path):
+        try:
+            with open(prof_path) as fh:
+                tr = json.load(fh)
+            ent = tr.get(w.name, {}).get(dom)
+            if ent and ent.get("kernel_source_sha256") == source_digest():
+                traffic = ent["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_kind": hbm_kind,
+                "traffic": traffic, "algorithmic_bytes_per_launch": algo,
+                "ms_per_launch": per_launch_ms,
+                "catalog_pass": {"ms": pre_ms, "GB/s": pre_algo / (pre_ms * 1e-3) / 1e9,
+                                 "frac": pre_algo / (pre_ms * 1e-3) / 1e9 / hbm},
+                "whole_run": {"algorithmic_bytes": whole_bytes,
+                              "GB/s": whole_bytes / (ms * 1e-3) / 1e9,
+                              "frac": whole_bytes / (ms * 1e-3) / 1e9 / hbm}}
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        hA, hf, hfd = (torch.from_numpy(x).pin_memory() for x in (A, f, fdot))
+        hs = torch.empty(nb, dtype=torch.float64).pin_memory()
+        hm = torch.empty(N, dtype=torch.uint8).pin_memory()
+        reps = 3
+        times = []
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sub.load(hA, hf, hfd)
+            sub.run(wait=True)
+            sub.spectrum(hs)
+            sub.resolved(hm)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        te = sum(times[1:]) / reps
+        if pg:
+            t = torch.tensor([te], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": ws * N / te, "unit": "sources/s", "h2d_bytes_per_step": 24 * N,
+               "d2h_bytes_per_step": 8 * nb + N, "ms_per_step": te * 1e3,
+               "api": "sub_load_catalog(SUB_HOST pinned) + sub_run + sub_get_spectrum + "
+                      "sub_get_resolved_mask"}
+
+    # ---------------------------------------------------------------- CPU baseline (oracle)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, tot, _ = cpu_oracle_sample(A, f, fdot, w.T_obs, est, args.window, st.iterations)
+        cpu = {"value": N / tot, "unit": "sources/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle (1 thread) with max_iter=1 on the full catalog: pre-filter, one "
+                         "iteration and the final re-estimate took %.1f s; scaled to the run's %d "
+                         "iterations as t*%d/2" % (dt, st.iterations, st.iterations)}
+
+    launches = args.steps * (1 + st.iterations * kernels_per_iteration(est)
+                             + (0 if st.converged else kernels_per_iteration(est) - 1))
+    line = {
+        "metric": "sources subtracted/sec to convergence", "value": value, "unit": "sources/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": "%s: N_b=%d, T_obs=%g yr, band 0.1-10 mHz, %d bins, power-law "
+                               "gamma=%.3f, Gamma shape=%.3f" % (w.name, N, w.T_obs / synth.YEAR,
+                                                                 nb, w.pop.gamma, w.pop.shape),
+                   "estimator": args.estimator, "window": args.window, "rho_th": 7.0,
+                   "kappa": 1 / 7.0, "precision": args.precision,
+                   "l2": "inputs larger than L2 (catalog %d MB)" % (24 * N // 2**20),
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "stats": {"iterations": st.iterations, "converged": bool(st.converged),
+                  "n_candidates": st.n_candidates, "n_resolved": st.n_resolved,
+                  "prepass_ms": pre_ms, "loop_ms": loop_ms},
+        "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "parity": parity,
+    }
+    line["clocks"] = clk.summary()
+    sub.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def source_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2602_18560_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+if __name__ == "__main__":
+    main()

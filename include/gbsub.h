@@ -159,6 +159,31 @@ int sub_estimate(sub_ctx* ctx, const double* P, double* out, int64_t n, int wher
  * doubles each; either may be null).  where: SUB_HOST or SUB_DEVICE. */
 int sub_get_tables(sub_ctx* ctx, double* S, double* R, int64_t n, int where);
 
+/* Device time of the last sub_run split at the end of the catalog pass:
+ * prepass_ms (clear + pass over the catalog), loop_ms (all iterations) and
+ * total_ms, from CUDA events recorded inside the run's graph.  Synchronises.
+ * Any pointer may be null. */
+int sub_get_timing(sub_ctx* ctx, float* prepass_ms, float* loop_ms, float* total_ms);
+
+/* Kernels of the path, in the order of SUB_K_* below. */
+#define SUB_K_PREPASS 0   /* catalog pass: sweep, deposit, rho_0, candidates */
+#define SUB_K_Q2P 1       /* fixed-point spectrum -> P_k                      */
+#define SUB_K_SORT 2      /* per-chunk sort + active-set snapshots (median)   */
+#define SUB_K_SLIDE 3     /* sliding median                                   */
+#define SUB_K_PREFIX 4    /* exact per-chunk prefix sums (mean)               */
+#define SUB_K_MEAN 5      /* window means                                     */
+#define SUB_K_SNR 6       /* SNR, threshold, removal                          */
+#define SUB_K_CONTROL 7   /* loop control                                     */
+#define SUB_K_COUNT 8
+
+/* Run the loaded catalog once more with the same kernels launched one by one
+ * from the host (no graph), recording a CUDA event pair around every launch;
+ * ms[k] receives the summed device time and launches[k] the launch count of
+ * kernel k (SUB_K_*).  Results and stats are those of a normal run.  Meant
+ * for measurement, not for throughput.  Synchronises. */
+int sub_profile(sub_ctx* ctx, float ms[SUB_K_COUNT], int32_t launches[SUB_K_COUNT],
+                sub_stats* stats);
+
 /* Bytes of device memory the context holds now. */
 int64_t sub_device_bytes(const sub_ctx* ctx);
 

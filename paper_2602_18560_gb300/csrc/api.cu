@@ -64,6 +64,12 @@ struct sub_ctx {
   cudaGraph_t graph = nullptr;
   int64_t graph_N = -1;
   bool use_graph = true;
+  // timing
+  cudaEvent_t ev_start = nullptr, ev_pre = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_k[2] = {nullptr, nullptr};
+  float prof_ms[SUB_K_COUNT];
+  int prof_n[SUB_K_COUNT];
+  bool profiling = false;
 };
 
 static std::string g_create_err = "no error";
@@ -221,6 +227,13 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { c->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e); return fail(SUB_ECUDA); }
   configure_kernels();
+  {
+    cudaEvent_t* evs[] = {&c->ev_start, &c->ev_pre, &c->ev_end, &c->ev_k[0], &c->ev_k[1]};
+    for (cudaEvent_t* ev : evs) {
+      e = cudaEventCreate(ev);
+      if (e != cudaSuccess) { c->err = std::string("cudaEventCreate: ") + cudaGetErrorString(e); return fail(SUB_ECUDA); }
+    }
+  }
   const SmoothPlan& pl = c->plan;
   int64_t ncell = (int64_t)pl.nch * pl.Kc;
   struct { void** p; size_t b; } want[] = {
@@ -302,6 +315,26 @@ static double thr_q_of(const sub_ctx* c) {
   return pre * pre / 4.0 * kQScale * (1.0 - 1e-12);
 }
 
+// While profiling, every launch is bracketed by an event pair and its device time added
+// to the kernel's total (this synchronises after each launch).
+struct KTimer {
+  sub_ctx* c;
+  cudaStream_t st;
+  int k;
+  KTimer(sub_ctx* c_, cudaStream_t st_, int k_) : c(c_), st(st_), k(k_) {
+    if (c->profiling) cudaEventRecord(c->ev_k[0], st);
+  }
+  ~KTimer() {
+    if (!c->profiling) return;
+    cudaEventRecord(c->ev_k[1], st);
+    cudaEventSynchronize(c->ev_k[1]);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev_k[0], c->ev_k[1]);
+    c->prof_ms[k] += ms;
+    c->prof_n[k] += 1;
+  }
+};
+
 static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
   const int64_t n = c->grid.nb;
   cudaError_t e;
@@ -313,8 +346,11 @@ static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
     if ((e = cudaMemsetAsync(c->resolved, 0, (size_t)c->N, st))) return e;
     if ((e = cudaMemsetAsync(c->cres, 0, (size_t)c->N, st))) return e;
   }
-  launch_prepass(c->A, c->f, c->fdot, c->N, c->grid, c->gq, thr_q_of(c), c->acc_lo, c->acc_hi,
-                 c->cand, c->rs, c->nsm, st);
+  {
+    KTimer t(c, st, SUB_K_PREPASS);
+    launch_prepass(c->A, c->f, c->fdot, c->N, c->grid, c->gq, thr_q_of(c), c->acc_lo, c->acc_hi,
+                   c->cand, c->rs, c->nsm, st);
+  }
   return cudaGetLastError();
 }
 
@@ -323,27 +359,30 @@ static cudaError_t enqueue_body(sub_ctx* c, cudaStream_t st, unsigned long long 
   const SmoothPlan& pl = c->plan;
   const int rtol_on = c->p.conv_rtol > 0.0 ? 1 : 0;
   RunState* rs = c->rs;
-  launch_q2p(c->acc_lo, c->acc_hi, c->S, n, c->P, rs, 0, st);
+  { KTimer t(c, st, SUB_K_Q2P); launch_q2p(c->acc_lo, c->acc_hi, c->S, n, c->P, rs, 0, st); }
   switch (c->p.estimator) {
     case SUB_MEAN:
-      launch_chunk_prefix(c->P, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st);
-      launch_window_mean(c->P, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, c->Sg, c->S, rtol_on, rs, st);
+      { KTimer t(c, st, SUB_K_PREFIX); launch_chunk_prefix(c->P, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st); }
+      { KTimer t(c, st, SUB_K_MEAN); launch_window_mean(c->P, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, c->Sg, c->S, rtol_on, rs, st); }
       break;
     case SUB_MEDIAN:
-      launch_chunk_sort(c->P, n, pl, c->skey, c->srank, c->snap, rs, st);
-      launch_median_slide(c->skey, c->srank, c->snap, n, pl, c->Sg, nullptr, c->S, rtol_on, rs, st);
+      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(c->P, n, pl, c->skey, c->srank, c->snap, rs, st); }
+      { KTimer t(c, st, SUB_K_SLIDE); launch_median_slide(c->skey, c->srank, c->snap, n, pl, c->Sg, nullptr, c->S, rtol_on, rs, st); }
       break;
     default:
-      launch_chunk_sort(c->P, n, pl, c->skey, c->srank, c->snap, rs, st);
-      launch_median_slide(c->skey, c->srank, c->snap, n, pl, c->M, &rs->max_m_bits, c->S, 0, rs, st);
-      launch_chunk_prefix(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st);
-      launch_window_mean(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, c->Sg, c->S, rtol_on, rs, st);
+      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(c->P, n, pl, c->skey, c->srank, c->snap, rs, st); }
+      { KTimer t(c, st, SUB_K_SLIDE); launch_median_slide(c->skey, c->srank, c->snap, n, pl, c->M, &rs->max_m_bits, c->S, 0, rs, st); }
+      { KTimer t(c, st, SUB_K_PREFIX); launch_chunk_prefix(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st); }
+      { KTimer t(c, st, SUB_K_MEAN); launch_window_mean(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, c->Sg, c->S, rtol_on, rs, st); }
       break;
   }
   double th2 = c->p.rho_th * c->p.rho_th;
-  launch_snr_resolve(c->cand, c->N > 0 ? c->N : 1, c->grid, c->S, c->R, c->gq, c->Sg, th2,
-                     c->p.conv_rtol, c->cres, c->resolved, c->acc_lo, c->acc_hi, rs, c->nsm, st);
-  launch_control(rs, c->p.max_iter, c->p.conv_rtol, c->new_hist, handle, use_cond, st);
+  {
+    KTimer t(c, st, SUB_K_SNR);
+    launch_snr_resolve(c->cand, c->N > 0 ? c->N : 1, c->grid, c->S, c->R, c->gq, c->Sg, th2,
+                       c->p.conv_rtol, c->cres, c->resolved, c->acc_lo, c->acc_hi, rs, c->nsm, st);
+  }
+  { KTimer t(c, st, SUB_K_CONTROL); launch_control(rs, c->p.max_iter, c->p.conv_rtol, c->new_hist, handle, use_cond, st); }
   return cudaGetLastError();
 }
 
@@ -354,7 +393,10 @@ static int build_graph(sub_ctx* c) {
   if (e) { set_err(c, "cudaGraphCreate: %s", cudaGetErrorString(e)); return SUB_ECUDA; }
   e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (!e) {
-    cudaError_t e2 = enqueue_pre(c, c->cap_stream);
+    // external records become event nodes of the graph (timing the run inside the graph)
+    cudaError_t e2 = cudaEventRecordWithFlags(c->ev_start, c->cap_stream, cudaEventRecordExternal);
+    if (!e2) e2 = enqueue_pre(c, c->cap_stream);
+    if (!e2) e2 = cudaEventRecordWithFlags(c->ev_pre, c->cap_stream, cudaEventRecordExternal);
     e = cudaStreamEndCapture(c->cap_stream, &pre);
     if (!e) e = e2;
   }
@@ -380,6 +422,8 @@ static int build_graph(sub_ctx* c) {
       if (!e) e = e2;
     }
   }
+  cudaGraphNode_t end_node = nullptr;
+  if (!e) e = cudaGraphAddEventRecordNode(&end_node, g, &cond_node, 1, c->ev_end);
   if (!e) e = cudaGraphInstantiate(&c->exec, g, 0);
   if (e) {
     cudaGetLastError();
@@ -394,13 +438,16 @@ static int build_graph(sub_ctx* c) {
 }
 
 static int run_host_loop(sub_ctx* c) {
+  CU(cudaEventRecord(c->ev_start, c->stream), c);
   CU(enqueue_pre(c, c->stream), c);
+  CU(cudaEventRecord(c->ev_pre, c->stream), c);
   for (int it = 0; it <= c->p.max_iter + 1; ++it) {
     CU(enqueue_body(c, c->stream, 0ull, 0), c);
     CU(cudaMemcpyAsync(c->h_rs, c->rs, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream), c);
     CU(cudaStreamSynchronize(c->stream), c);
     if (c->h_rs->stopped) break;
   }
+  CU(cudaEventRecord(c->ev_end, c->stream), c);
   return SUB_OK;
 }
 
@@ -541,6 +588,37 @@ extern "C" int sub_get_tables(sub_ctx* c, double* S, double* R, int64_t n, int w
   return SUB_OK;
 }
 
+extern "C" int sub_get_timing(sub_ctx* c, float* prepass_ms, float* loop_ms, float* total_ms) {
+  if (!c) return SUB_EINVAL;
+  if (!c->ran) { set_err(c, "no run yet"); return SUB_ESTATE; }
+  CU(cudaEventSynchronize(c->ev_end), c);
+  float a = 0.f, b = 0.f;
+  CU(cudaEventElapsedTime(&a, c->ev_start, c->ev_pre), c);
+  CU(cudaEventElapsedTime(&b, c->ev_pre, c->ev_end), c);
+  if (prepass_ms) *prepass_ms = a;
+  if (loop_ms) *loop_ms = b;
+  if (total_ms) *total_ms = a + b;
+  return SUB_OK;
+}
+
+extern "C" int sub_profile(sub_ctx* c, float ms[SUB_K_COUNT], int32_t launches[SUB_K_COUNT],
+                           sub_stats* st) {
+  if (!c) return SUB_EINVAL;
+  if (c->N < 0) { set_err(c, "no catalog loaded"); return SUB_ESTATE; }
+  for (int k = 0; k < SUB_K_COUNT; ++k) { c->prof_ms[k] = 0.f; c->prof_n[k] = 0; }
+  CU(cudaStreamSynchronize(c->stream), c);
+  c->profiling = true;
+  int rc = run_host_loop(c);
+  c->profiling = false;
+  if (rc) return rc;
+  c->ran = true;
+  for (int k = 0; k < SUB_K_COUNT; ++k) {
+    if (ms) ms[k] = c->prof_ms[k];
+    if (launches) launches[k] = c->prof_n[k];
+  }
+  return fill_stats(c, st);
+}
+
 extern "C" int64_t sub_device_bytes(const sub_ctx* c) { return c ? c->bytes : 0; }
 
 extern "C" void sub_destroy(sub_ctx* c) {
@@ -550,6 +628,9 @@ extern "C" void sub_destroy(sub_ctx* c) {
   for (auto& q : c->allocs) cudaFree(q.first);
   c->allocs.clear();
   if (c->h_rs) cudaFreeHost(c->h_rs);
+  cudaEvent_t evs[] = {c->ev_start, c->ev_pre, c->ev_end, c->ev_k[0], c->ev_k[1]};
+  for (cudaEvent_t ev : evs)
+    if (ev) cudaEventDestroy(ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -62,7 +62,9 @@ _lib = None
 _lock = threading.Lock()
 EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_run", "sub_get_stats",
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
-           "sub_get_tables", "sub_device_bytes", "sub_destroy", "sub_last_error")
+           "sub_get_tables", "sub_get_timing", "sub_profile", "sub_device_bytes", "sub_destroy",
+           "sub_last_error")
+KERNELS = ("prepass", "q2p", "sort", "slide", "prefix", "mean", "snr", "control")
 
 
 def library_path() -> str:
@@ -93,6 +95,8 @@ def lib(build_if_missing: bool = True):
             "sub_get_resolved_mask": (i32, [P, P, i64, i32]),
             "sub_estimate": (i32, [P, P, P, i64, i32]),
             "sub_get_tables": (i32, [P, P, P, i64, i32]),
+            "sub_get_timing": (i32, [P, P, P, P]),
+            "sub_profile": (i32, [P, P, P, ctypes.POINTER(sub_stats)]),
             "sub_device_bytes": (i64, [P]),
             "sub_destroy": (None, [P]),
             "sub_last_error": (ctypes.c_char_p, [P]),
@@ -229,6 +233,22 @@ def sub_get_tables(ctx):
     return S, R
 
 
+def sub_get_timing(ctx):
+    """(prepass_ms, loop_ms, total_ms) of the last run, from events inside its graph."""
+    a, b, t = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    _check(ctx, lib().sub_get_timing(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t)))
+    return a.value, b.value, t.value
+
+
+def sub_profile(ctx):
+    """Per-kernel device time (ms) and launch counts of one host-driven run."""
+    ms = (ctypes.c_float * len(KERNELS))()
+    n = (ctypes.c_int32 * len(KERNELS))()
+    st = sub_stats()
+    _check(ctx, lib().sub_profile(ctx, ms, n, ctypes.byref(st)), allow=(ENOTCONVERGED,))
+    return {k: (ms[i], n[i]) for i, k in enumerate(KERNELS)}, st
+
+
 def sub_device_bytes(ctx) -> int:
     return lib().sub_device_bytes(ctx)
 
@@ -268,6 +288,12 @@ class Subtraction:
 
     def tables(self):
         return sub_get_tables(self.ctx)
+
+    def timing(self):
+        return sub_get_timing(self.ctx)
+
+    def profile(self):
+        return sub_profile(self.ctx)
 
     @property
     def grid(self):

@@ -168,6 +168,8 @@ def workload(name: str) -> Workload:
         return Workload(name, 10_000, 1 * YEAR, 0, Population(11.0 / 3.0, 2.0))
     if name == "nb1e6_4yr":
         return Workload(name, 1_000_000, 4 * YEAR, 1, Population(11.0 / 3.0, 2.0))
+    if name == "nb1e7_4yr":  # profiling size: the full-size population, a third of the sources
+        return Workload(name, 10_000_000, 4 * YEAR, 2, population_draw(2, 0))
     if name == "nb3e7_4yr":
         return Workload(name, 30_000_000, 4 * YEAR, 2, population_draw(2, 0))
     raise KeyError(name)
