@@ -184,6 +184,31 @@ int sub_get_timing(sub_ctx* ctx, float* prepass_ms, float* loop_ms, float* total
 int sub_profile(sub_ctx* ctx, float ms[SUB_K_COUNT], int32_t launches[SUB_K_COUNT],
                 sub_stats* stats);
 
+/* Largest inputs of sub_running_mean_noalloc (the size of its static scratch). */
+#define SUB_NOALLOC_MAX_BINS 1310720
+#define SUB_NOALLOC_MAX_WINDOW 8192
+
+/* Running mean of a caller's spectrum without any device allocation.  The paper
+ * has no counterpart to this call; it serves callers that cannot allocate device
+ * memory, e.g. a plug-in handed device buffers by a host framework that owns all
+ * device memory, or a latency-critical loop that must not enter cudaMalloc (which
+ * can synchronise the device and can fail at run time).
+ *   x, out : device pointers to n doubles (x >= 0), owned by the caller; they may
+ *            not overlap.  out[j] = mean of x over [j - W/2, j - W/2 + W - 1]
+ *            cut to [0, n), the same values as sub_estimate with SUB_MEAN.
+ *   n      : 1 .. SUB_NOALLOC_MAX_BINS;  window: 1 .. SUB_NOALLOC_MAX_WINDOW.
+ *   stream : cudaStream_t to run on (NULL: the legacy default stream).  The call
+ *            returns after enqueueing.
+ * Scratch lives in one static device array of about 21 MB that every GPU loading
+ * the library holds until the process exits.  The first call on a device (with
+ * that device current) looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents: calls that overlap on the GPU race and must be serialised by
+ * the caller.  Sizes beyond the limits return SUB_EINVAL with a message in
+ * sub_last_error(NULL); CUDA failures return SUB_ECUDA. */
+int sub_running_mean_noalloc(const double* x, double* out, int64_t n, int32_t window,
+                             void* stream);
+
 /* Bytes of device memory the context holds now. */
 int64_t sub_device_bytes(const sub_ctx* ctx);
 

@@ -74,6 +74,11 @@ struct sub_ctx {
 
 static std::string g_create_err = "no error";
 
+namespace gbsub {
+// Message of a failure that has no context (sub_create, sub_running_mean_noalloc).
+void set_global_error(const char* msg) { g_create_err = msg; }
+}  // namespace gbsub
+
 static void set_err(sub_ctx* c, const char* fmt, ...) {
   char buf[512];
   va_list ap;

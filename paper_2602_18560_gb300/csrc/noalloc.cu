@@ -1,0 +1,126 @@
+// Running mean of a caller's spectrum with no device allocation at all.
+//
+// Some callers cannot call cudaMalloc: a plug-in that only receives device
+// buffers from a host framework which owns every byte of device memory and does
+// not allow allocations behind its back, or a latency-critical loop that must not
+// enter the allocator (cudaMalloc may synchronise the device and may fail at run
+// time).  For them, sub_running_mean_noalloc computes the same running mean as the
+// context path (exact 128-bit window sums over chunks, App. D Eq. running mean)
+// with its scratch in one file-scope device array below.
+//
+// The array is part of the library image: every GPU that loads the library holds
+// it (about 21 MB) until the process exits.  Every call shares it and it keeps the
+// last call's contents, so calls whose work overlaps on the GPU (different streams,
+// or different host threads) race with each other and must be serialised by the
+// caller.  The window maximum that fixes the fixed-point scale is cleared at the
+// start of every call; the prefix sums and underflow flags are fully rewritten for
+// the bins a call uses.
+
+#include <cstdio>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gbsub.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace gbsub {
+void set_global_error(const char* msg);
+}
+
+using namespace gbsub;
+
+namespace {
+
+constexpr long long kNoAllocMaxBins = SUB_NOALLOC_MAX_BINS;
+constexpr long long kNoAllocMaxWindow = SUB_NOALLOC_MAX_WINDOW;
+// chunk cells: at most one chunk beyond the bins, chunks of >= 32 and <= max window
+constexpr long long kCells = kNoAllocMaxBins + kNoAllocMaxWindow + 32;
+constexpr long long kChunks = kNoAllocMaxBins / 32 + 2;
+// layout in 8-byte words: pre_lo[kCells] | pre_hi[kCells] | uflow (u32)[kChunks] | max bits
+constexpr long long kWords = 2 * kCells + (kChunks + 1) / 2 + 1;
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kWords];
+
+std::mutex g_mu;
+unsigned long long* g_addr[128] = {nullptr};  // device address of the array, per device
+
+}  // namespace
+
+extern "C" int sub_running_mean_noalloc(const double* x, double* out, int64_t n, int32_t window,
+                                        void* stream) {
+  char msg[256];
+  if (!x || !out) {
+    set_global_error("sub_running_mean_noalloc: x and out must be device pointers");
+    return SUB_EINVAL;
+  }
+  if (n < 1 || n > kNoAllocMaxBins) {
+    snprintf(msg, sizeof(msg),
+             "sub_running_mean_noalloc: n = %lld bins is outside 1 .. %lld (the size of its "
+             "static scratch)", (long long)n, kNoAllocMaxBins);
+    set_global_error(msg);
+    return SUB_EINVAL;
+  }
+  if (window < 1 || window > kNoAllocMaxWindow) {
+    snprintf(msg, sizeof(msg), "sub_running_mean_noalloc: window %d is outside 1 .. %lld",
+             window, kNoAllocMaxWindow);
+    set_global_error(msg);
+    return SUB_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 128) {
+    snprintf(msg, sizeof(msg), "sub_running_mean_noalloc: cudaGetDevice failed: %s",
+             cudaGetErrorString(e));
+    set_global_error(msg);
+    return SUB_ECUDA;
+  }
+  unsigned long long* base = nullptr;
+  {
+    // Once per device, with that device current: the host-side name of the array is
+    // only a stand-in, so ask the runtime for its device address.
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        snprintf(msg, sizeof(msg), "sub_running_mean_noalloc: cudaGetSymbolAddress failed: %s",
+                 cudaGetErrorString(e));
+        set_global_error(msg);
+        return SUB_ECUDA;
+      }
+      g_addr[dev] = (unsigned long long*)p;
+    }
+    base = g_addr[dev];
+  }
+  SmoothPlan pl;
+  pl.W = window;
+  pl.Kc = ((window + 31) / 32) * 32;
+  if (pl.Kc < 32) pl.Kc = 32;
+  pl.nw = pl.Kc / 32;
+  pl.nch = (int)((n + pl.Kc - 1) / pl.Kc);
+  pl.nsnap = pl.Kc / kSnapStride + 1;
+  pl.kpad = 0;
+  pl.L = 0;
+  pl.slide_threads = 0;
+  unsigned long long* pre_lo = base;
+  unsigned long long* pre_hi = base + kCells;
+  unsigned* uflow = (unsigned*)(base + 2 * kCells);
+  unsigned long long* max_bits = base + kWords - 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  e = cudaMemsetAsync(max_bits, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    launch_max_bits(x, n, max_bits, st);
+    launch_chunk_prefix(x, n, pl, max_bits, pre_lo, pre_hi, uflow, nullptr, st);
+    launch_window_mean(x, n, pl, max_bits, pre_lo, pre_hi, uflow, out, nullptr, 0, nullptr, st);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    snprintf(msg, sizeof(msg), "sub_running_mean_noalloc: launch failed: %s",
+             cudaGetErrorString(e));
+    set_global_error(msg);
+    return SUB_ECUDA;
+  }
+  return SUB_OK;
+}

@@ -63,7 +63,7 @@ _lock = threading.Lock()
 EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_run", "sub_get_stats",
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
            "sub_get_tables", "sub_get_timing", "sub_profile", "sub_device_bytes", "sub_destroy",
-           "sub_last_error")
+           "sub_last_error", "sub_running_mean_noalloc")
 KERNELS = ("prepass", "q2p", "sort", "slide", "prefix", "mean", "snr", "control")
 
 
@@ -100,6 +100,7 @@ def lib(build_if_missing: bool = True):
             "sub_device_bytes": (i64, [P]),
             "sub_destroy": (None, [P]),
             "sub_last_error": (ctypes.c_char_p, [P]),
+            "sub_running_mean_noalloc": (i32, [P, P, i64, i32, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
