@@ -129,25 +129,24 @@ class ClockSampler:
 
 
 def kernels_per_iteration(est):
-    return {0: 5, 1: 5, 2: 7}[est]
+    return {0: 4, 1: 4, 2: 6}[est]
 
 
-def algorithmic_bytes(kernel, N, nb, ncand, plan_chunks, kc, nsnap):
-    """Bytes a kernel must move per launch (reads + writes of its inputs/outputs)."""
-    if kernel == "prepass":
-        return 24 * N + 16 * nb + 32 * ncand
-    if kernel == "q2p":
-        return 16 * nb + 8 * nb + 8 * nb
-    if kernel == "sort":
-        return 8 * nb + 8 * nb + 2 * nb + plan_chunks * nsnap * (kc // 32) * 4
-    if kernel == "slide":
-        return 8 * nb + 2 * nb + 8 * nb
-    if kernel == "prefix":
-        return 8 * nb + 16 * nb
-    if kernel == "mean":
-        return 16 * nb + 8 * nb
-    if kernel == "snr":
-        return 32 * ncand + 8 * 3 * ncand
+def algorithmic_bytes(kernel, N, nb, nlive, est, plan_chunks, kc, nsnap):
+    """Bytes a kernel must move per launch: reads of its inputs plus writes of its outputs."""
+    snap = plan_chunks * nsnap * (kc // 32) * 4
+    if kernel == "prepass":   # catalog, cleared spectrum (4 words/bin), kept candidates
+        return 24 * N + 32 * nb + 53 * nlive
+    if kernel == "sort":      # spectrum words + S_instr -> keys, ranks, snapshots
+        return 32 * nb + 8 * nb + 2 * nb + snap
+    if kernel == "slide":     # keys, ranks, snapshots -> median (+ inv_f when it is S_gal)
+        return 10 * nb + snap + 8 * nb + (4 * nb if est == 1 else 0)
+    if kernel == "prefix":    # input (spectrum words + S, or the median) -> prefix sums
+        return (40 * nb + 8 * nb if est == 0 else 8 * nb) + 16 * nb
+    if kernel == "mean":      # two prefix sums per output -> S_gal + inv_f
+        return 16 * nb + 12 * nb
+    if kernel == "snr":       # kept candidates + two FP32 table reads per bin
+        return 40 * nlive
     return 0
 
 
@@ -299,18 +298,15 @@ def main():
     nch = (nb + plan_kc - 1) // plan_kc
     nsnap = plan_kc // 32 + 1
     per_launch_ms = kernels[dom]["ms_per_run"] / kernels[dom]["launches_per_run"]
-    algo = algorithmic_bytes(dom, N, nb, st.n_candidates, nch, plan_kc, nsnap)
+    nlive = st.n_live
+    algo = algorithmic_bytes(dom, N, nb, nlive, est, nch, plan_kc, nsnap)
     hbm, hbm_kind = peaks()
     achieved = algo / (per_launch_ms * 1e-3) / 1e9
     # the catalog pass separately (timed inside the graph of the last timed step)
-    pre_algo = algorithmic_bytes("prepass", N, nb, st.n_candidates, nch, plan_kc, nsnap)
-    whole_bytes = pre_algo + st.iterations * (
-        algorithmic_bytes("q2p", N, nb, 0, nch, plan_kc, nsnap)
-        + (algorithmic_bytes("sort", N, nb, 0, nch, plan_kc, nsnap)
-           + algorithmic_bytes("slide", N, nb, 0, nch, plan_kc, nsnap) if est else 0)
-        + (algorithmic_bytes("prefix", N, nb, 0, nch, plan_kc, nsnap)
-           + algorithmic_bytes("mean", N, nb, 0, nch, plan_kc, nsnap) if est != 1 else 0)
-        + algorithmic_bytes("snr", N, nb, st.n_candidates, nch, plan_kc, nsnap)) + N
+    pre_algo = algorithmic_bytes("prepass", N, nb, nlive, est, nch, plan_kc, nsnap)
+    per_iter = sum(algorithmic_bytes(k, N, nb, nlive, est, nch, plan_kc, nsnap)
+                   for k in kernels if k not in ("prepass", "control"))
+    whole_bytes = pre_algo + st.iterations * per_iter + N
     traffic = None
     prof_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof_path):
@@ -383,7 +379,9 @@ def main():
                    "l2": "inputs larger than L2 (catalog %d MB)" % (24 * N // 2**20),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "stats": {"iterations": st.iterations, "converged": bool(st.converged),
-                  "n_candidates": st.n_candidates, "n_resolved": st.n_resolved,
+                  "n_candidates": st.n_candidates, "n_live": st.n_live,
+                  "n_exact_snr": st.n_exact, "n_resolved": st.n_resolved,
+                  "resolved_per_iteration": [int(x) for x in sub.history()],
                   "prepass_ms": pre_ms, "loop_ms": loop_ms},
         "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "parity": parity,

@@ -51,11 +51,18 @@ extern "C" {
 #define SUB_MEDIAN 1
 #define SUB_MEDIAN_MEAN 2
 
-/* Arithmetic of the per-iteration steps.  SUB_FP64: SNR and selection in FP64.
- * SUB_MIXED: SNR and median selection in FP32 (rescaled units); deposition,
- * window sums and the convergence test stay exact/FP64. */
+/* Arithmetic of the per-iteration SNR decision and median selection.
+ *   SUB_FP64        : FP64 results.  Each rho^2 > rho_th^2 decision is first
+ *                     evaluated in FP32 with a proven error bound; only when
+ *                     rho^2 lies within that bound of rho_th^2 is it recomputed
+ *                     in FP64, so every decision equals the FP64 one.
+ *   SUB_MIXED       : the FP32 value of rho^2 decides alone, and the median
+ *                     selects on FP32 keys; deposition and window sums stay exact.
+ *   SUB_FP64_STRICT : every rho^2 computed in FP64 (for verification).
+ * The spectrum itself is always an exact fixed-point sum. */
 #define SUB_FP64 0
 #define SUB_MIXED 1
+#define SUB_FP64_STRICT 2
 
 /* Location of a caller buffer. */
 #define SUB_HOST 0
@@ -73,7 +80,7 @@ typedef struct {
   double kappa;        /* pre-filter factor: candidates have rho_0 >= kappa rho_th  */
   int32_t max_iter;    /* iteration cap (>= 1)                                      */
   int32_t tdi2;        /* 1: apply the TDI-2.0 factor 4 sin^2(2 f/f*) (App. C)      */
-  int32_t precision;   /* SUB_FP64 | SUB_MIXED                                      */
+  int32_t precision;   /* SUB_FP64 | SUB_MIXED | SUB_FP64_STRICT                    */
   int32_t reserved0;   /* must be 0                                                 */
   double conv_rtol;    /* also stop when max_k |dS_n|/S_n <= conv_rtol; 0 = off     */
   uint64_t hbm_budget; /* bytes of device memory the context may hold; 0 = no cap   */
@@ -90,6 +97,10 @@ typedef struct {
   int64_t k_lo;           /* DFT index of the first bin: f = (k_lo + j) / T_obs       */
   int32_t status;         /* return code of the run                                  */
   int32_t reserved;
+  int64_t n_live;         /* candidates that can still be resolved: rho_0 > rho_th   */
+                          /* (rho <= rho_0 because S_n >= S_instr; the others are    */
+                          /* never tested again)                                     */
+  int64_t n_exact;        /* SNR decisions recomputed in FP64 (SUB_FP64)             */
 } sub_stats;
 
 typedef struct sub_ctx sub_ctx;
@@ -154,6 +165,13 @@ int sub_get_resolved_mask(sub_ctx* ctx, uint8_t* mask, int64_t n, int where);
  * Errors: SUB_EINVAL, SUB_ECUDA.  Synchronises before returning. */
 int sub_estimate(sub_ctx* ctx, const double* P, double* out, int64_t n, int where);
 
+/* Copy the residual power spectrum P_k of the sources not resolved so far
+ * (after a run: the residual the final S_gal was estimated from), the one-sided
+ * A-channel periodogram level of App. D, into P (n_bins doubles).  P_k is
+ * evaluated from the run's exact fixed-point spectrum.  where: SUB_HOST or
+ * SUB_DEVICE.  Errors: SUB_EINVAL, SUB_ESTATE (no run yet), SUB_ECUDA. */
+int sub_get_power(sub_ctx* ctx, double* P, int64_t n, int where);
+
 /* Copy the per-bin tables S_instr(f_k) (App. C, A channel, times the TDI-2
  * factor when tdi2) and R(f_k) (App. B, same factor) into S and R (n_bins
  * doubles each; either may be null).  where: SUB_HOST or SUB_DEVICE. */
@@ -166,15 +184,14 @@ int sub_get_tables(sub_ctx* ctx, double* S, double* R, int64_t n, int where);
 int sub_get_timing(sub_ctx* ctx, float* prepass_ms, float* loop_ms, float* total_ms);
 
 /* Kernels of the path, in the order of SUB_K_* below. */
-#define SUB_K_PREPASS 0   /* catalog pass: sweep, deposit, rho_0, candidates */
-#define SUB_K_Q2P 1       /* fixed-point spectrum -> P_k                      */
-#define SUB_K_SORT 2      /* per-chunk sort + active-set snapshots (median)   */
-#define SUB_K_SLIDE 3     /* sliding median                                   */
-#define SUB_K_PREFIX 4    /* exact per-chunk prefix sums (mean)               */
-#define SUB_K_MEAN 5      /* window means                                     */
-#define SUB_K_SNR 6       /* SNR, threshold, removal                          */
-#define SUB_K_CONTROL 7   /* loop control                                     */
-#define SUB_K_COUNT 8
+#define SUB_K_PREPASS 0   /* catalog pass: sweep, deposit, rho_0, candidates  */
+#define SUB_K_SORT 1      /* per-chunk sort + active-set snapshots (median)    */
+#define SUB_K_SLIDE 2     /* sliding median                                    */
+#define SUB_K_PREFIX 3    /* exact per-chunk prefix sums (mean)                */
+#define SUB_K_MEAN 4      /* window means                                      */
+#define SUB_K_SNR 5       /* SNR, threshold, removal                           */
+#define SUB_K_CONTROL 6   /* loop control                                      */
+#define SUB_K_COUNT 7
 
 /* Run the loaded catalog once more with the same kernels launched one by one
  * from the host (no graph), recording a CUDA event pair around every launch;

@@ -39,9 +39,14 @@ struct sub_ctx {
   std::string err;
   // tables
   double *S = nullptr, *R = nullptr, *gq = nullptr;
+  float *Gf = nullptr, *invSf = nullptr;
   // spectrum and smoothing buffers
-  unsigned long long *acc_lo = nullptr, *acc_hi = nullptr;
+  unsigned long long* acc = nullptr;  // 4 words per bin
   double *P = nullptr, *M = nullptr, *Sg = nullptr;
+  double* estimate_in = nullptr;  // input copy of sub_estimate
+  float* inv_f = nullptr;
+  int* sig = nullptr;
+  unsigned char* dirty = nullptr;  // two sets of one byte per chunk
   unsigned long long* skey = nullptr;
   uint16_t* srank = nullptr;
   uint32_t* snap = nullptr;
@@ -51,8 +56,7 @@ struct sub_ctx {
   int64_t N = -1;        // sources loaded (-1: none)
   int64_t cap_N = 0;     // capacity of the per-source buffers
   double *A = nullptr, *f = nullptr, *fdot = nullptr;
-  Cand* cand = nullptr;
-  unsigned char* cres = nullptr;
+  Cands cd = {};
   unsigned char* resolved = nullptr;
   // run state
   RunState* rs = nullptr;
@@ -166,7 +170,7 @@ static int validate(const sub_params* p, int64_t* k_lo, int64_t* n) {
   if (p->estimator < SUB_MEAN || p->estimator > SUB_MEDIAN_MEAN) { set_err(nullptr, "unknown estimator %d", p->estimator); return SUB_EINVAL; }
   if (!(p->rho_th > 0.0) || !(p->kappa >= 0.0)) { set_err(nullptr, "rho_th must be > 0 and kappa >= 0"); return SUB_EINVAL; }
   if (p->max_iter < 1) { set_err(nullptr, "max_iter must be >= 1"); return SUB_EINVAL; }
-  if (p->precision != SUB_FP64 && p->precision != SUB_MIXED) { set_err(nullptr, "unknown precision %d", p->precision); return SUB_EINVAL; }
+  if (p->precision < SUB_FP64 || p->precision > SUB_FP64_STRICT) { set_err(nullptr, "unknown precision %d", p->precision); return SUB_EINVAL; }
   if (!(p->conv_rtol >= 0.0)) { set_err(nullptr, "conv_rtol must be >= 0"); return SUB_EINVAL; }
   double a = std::ceil(p->f_min * p->T_obs);
   double b = std::floor(p->f_max * p->T_obs);
@@ -211,6 +215,14 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   c->grid.t5 = p->T_obs / 5.0;
   c->grid.k_lo = k_lo;
   c->grid.nb = n;
+  {
+    // T_obs = mT 2^eT with mT the 53-bit integer mantissa (for the exact f T in the prepass)
+    int ex = 0;
+    double m = std::frexp(p->T_obs, &ex);  // T = m 2^ex, m in [0.5, 1)
+    c->grid.mT = (unsigned long long)std::ldexp(m, 53);
+    c->grid.eT = ex - 53;
+    c->grid.T2f = (float)(p->T_obs * p->T_obs);
+  }
   c->plan = make_plan(p->window, n);
   auto fail = [&](int code) {
     g_create_err = c->err;
@@ -243,8 +255,11 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   int64_t ncell = (int64_t)pl.nch * pl.Kc;
   struct { void** p; size_t b; } want[] = {
       {(void**)&c->S, (size_t)n * 8}, {(void**)&c->R, (size_t)n * 8}, {(void**)&c->gq, (size_t)n * 8},
-      {(void**)&c->acc_lo, (size_t)n * 8}, {(void**)&c->acc_hi, (size_t)n * 8},
+      {(void**)&c->Gf, (size_t)n * 4}, {(void**)&c->invSf, (size_t)n * 4},
+      {(void**)&c->acc, (size_t)n * 32}, {(void**)&c->inv_f, (size_t)n * 4},
       {(void**)&c->P, (size_t)n * 8}, {(void**)&c->Sg, (size_t)n * 8},
+      {(void**)&c->sig, (size_t)pl.nch * 4}, {(void**)&c->estimate_in, (size_t)n * 8},
+      {(void**)&c->dirty, (size_t)pl.nch * 2},
       {(void**)&c->pre_lo, (size_t)ncell * 8}, {(void**)&c->pre_hi, (size_t)ncell * 8},
       {(void**)&c->uflow, (size_t)pl.nch * 4},
       {(void**)&c->rs, sizeof(RunState)}, {(void**)&c->new_hist, (size_t)p->max_iter * 4},
@@ -263,7 +278,7 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   e = cudaMallocHost((void**)&c->h_rs, sizeof(RunState));
   if (e != cudaSuccess) { c->err = "cudaMallocHost failed"; return fail(SUB_ENOMEM); }
   std::memset(c->h_rs, 0, sizeof(RunState));
-  launch_tables(c->grid, p->tdi2, c->S, c->R, c->gq, c->stream);
+  launch_tables(c->grid, p->tdi2, c->S, c->R, c->gq, c->Gf, c->invSf, c->stream);
   e = cudaMemsetAsync(c->Sg, 0, (size_t)n * 8, c->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -282,18 +297,25 @@ extern "C" int sub_load_catalog(sub_ctx* c, const double* A, const double* f, co
   if (n > ((int64_t)1 << 40)) { set_err(c, "catalog too large"); return SUB_EINVAL; }
   if (n > c->cap_N || c->A == nullptr) {
     drop_graph(c);
-    dfree(c, c->A); dfree(c, c->f); dfree(c, c->fdot);
-    dfree(c, c->cand); dfree(c, c->cres); dfree(c, c->resolved);
+    dfree(c, c->A); dfree(c, c->f); dfree(c, c->fdot); dfree(c, c->resolved);
+    void* cds[] = {c->cd.src, c->cd.ka, c->cd.nbin, c->cd.a2f, c->cd.flo, c->cd.len,
+                   c->cd.a2, c->cd.lo, c->cd.hi, c->cd.res};
+    for (void* q : cds) dfree(c, q);
     c->A = c->f = c->fdot = nullptr;
-    c->cand = nullptr;
-    c->cres = c->resolved = nullptr;
+    c->resolved = nullptr;
+    c->cd = Cands{};
     c->cap_N = 0;
     c->N = -1;
     int rc;
     size_t m = (size_t)(n > 0 ? n : 1);
+    // Candidate arrays hold every source in the worst case (a catalog of bright sources).
     if ((rc = dalloc(c, (void**)&c->A, m * 8)) || (rc = dalloc(c, (void**)&c->f, m * 8)) ||
-        (rc = dalloc(c, (void**)&c->fdot, m * 8)) || (rc = dalloc(c, (void**)&c->cand, m * sizeof(Cand))) ||
-        (rc = dalloc(c, (void**)&c->cres, m)) || (rc = dalloc(c, (void**)&c->resolved, m))) {
+        (rc = dalloc(c, (void**)&c->fdot, m * 8)) || (rc = dalloc(c, (void**)&c->resolved, m)) ||
+        (rc = dalloc(c, (void**)&c->cd.src, m * 8)) || (rc = dalloc(c, (void**)&c->cd.ka, m * 4)) ||
+        (rc = dalloc(c, (void**)&c->cd.nbin, m * 4)) || (rc = dalloc(c, (void**)&c->cd.a2f, m * 4)) ||
+        (rc = dalloc(c, (void**)&c->cd.flo, m * 4)) || (rc = dalloc(c, (void**)&c->cd.len, m * 4)) ||
+        (rc = dalloc(c, (void**)&c->cd.a2, m * 8)) || (rc = dalloc(c, (void**)&c->cd.lo, m * 8)) ||
+        (rc = dalloc(c, (void**)&c->cd.hi, m * 8)) || (rc = dalloc(c, (void**)&c->cd.res, m))) {
       return rc;
     }
     c->cap_N = (int64_t)m;
@@ -312,12 +334,29 @@ extern "C" int sub_load_catalog(sub_ctx* c, const double* A, const double* f, co
 
 // ---------------------------------------------------------------- enqueue helpers
 
-static double thr_q_of(const sub_ctx* c) {
+// Prepass thresholds on r = sum of the fixed-point contributions, rho_0^2 = 4 r 2^-96.
+// Both are lowered by 1e-12 relative so that rounding can only keep more sources: an extra
+// candidate cannot change the result, since S_n >= S_instr makes rho <= rho_0.
+static double thr_kappa_of(const sub_ctx* c) {
   double pre = c->p.kappa * c->p.rho_th;
-  // candidates: rho_0^2 = 4 sum(q) 2^-64 >= pre^2; the bound is lowered by 1e-12 relative so
-  // that rounding can only add candidates (a larger candidate set cannot change the result:
-  // S_n >= S_instr makes rho <= rho_0 < rho_th for every extra one).
   return pre * pre / 4.0 * kQScale * (1.0 - 1e-12);
+}
+static double thr_live_of(const sub_ctx* c) {
+  return c->p.rho_th * c->p.rho_th / 4.0 * kQScale * (1.0 - 1e-12);
+}
+
+static Tables tables_of(const sub_ctx* c) {
+  Tables t;
+  t.S = c->S;
+  t.R = c->R;
+  t.gq = c->gq;
+  t.Gf = c->Gf;
+  t.invSf = c->invSf;
+  return t;
+}
+
+static int snr_mode(const sub_ctx* c) {
+  return c->p.precision;  // 0: FP64 with FP32 screen, 1: FP32 decides, 2: FP64 always
 }
 
 // While profiling, every launch is bracketed by an event pair and its device time added
@@ -343,51 +382,94 @@ struct KTimer {
 static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
   const int64_t n = c->grid.nb;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(c->acc_lo, 0, (size_t)n * 8, st))) return e;
-  if ((e = cudaMemsetAsync(c->acc_hi, 0, (size_t)n * 8, st))) return e;
+  if ((e = cudaMemsetAsync(c->acc, 0, (size_t)n * 32, st))) return e;
   if ((e = cudaMemsetAsync(c->rs, 0, sizeof(RunState), st))) return e;
+  // the first iteration reads set 0: every chunk is new
+  if ((e = cudaMemsetAsync(c->dirty, 1, (size_t)c->plan.nch, st))) return e;
+  if ((e = cudaMemsetAsync(c->dirty + c->plan.nch, 0, (size_t)c->plan.nch, st))) return e;
   if ((e = cudaMemsetAsync(c->new_hist, 0, (size_t)c->p.max_iter * 4, st))) return e;
   if (c->N > 0) {
     if ((e = cudaMemsetAsync(c->resolved, 0, (size_t)c->N, st))) return e;
-    if ((e = cudaMemsetAsync(c->cres, 0, (size_t)c->N, st))) return e;
   }
   {
     KTimer t(c, st, SUB_K_PREPASS);
-    launch_prepass(c->A, c->f, c->fdot, c->N, c->grid, c->gq, thr_q_of(c), c->acc_lo, c->acc_hi,
-                   c->cand, c->rs, c->nsm, st);
+    launch_prepass(c->A, c->f, c->fdot, c->N, c->grid, tables_of(c), thr_kappa_of(c),
+                   thr_live_of(c), c->acc, c->cd, c->rs, c->nsm, st);
   }
   return cudaGetLastError();
 }
 
-static cudaError_t enqueue_body(sub_ctx* c, cudaStream_t st, unsigned long long handle, int use_cond) {
+// One estimate of S_gal from `in` into c->Sg (and inv_f when with_inv).  With track, only
+// the chunks whose inputs changed since the previous iteration are recomputed.
+static Dirty dirty_of(sub_ctx* c, bool track) {
+  Dirty d;
+  d.base = track ? c->dirty : nullptr;
+  d.nch = c->plan.nch;
+  d.rs = c->rs;
+  return d;
+}
+
+// Chunks around a changed chunk whose S_gal changes: the median and the mean read one chunk
+// on each side, median-then-mean two.
+static int sg_radius_of(const sub_ctx* c) { return c->p.estimator == SUB_MEDIAN_MEAN ? 2 : 1; }
+
+static void enqueue_estimate(sub_ctx* c, cudaStream_t st, SpecIn in, int rtol_on, bool with_inv,
+                             bool track) {
   const int64_t n = c->grid.nb;
   const SmoothPlan& pl = c->plan;
+  Dirty d = dirty_of(c, track);
+  SgOut o;
+  o.out = c->Sg;
+  o.inv_f = with_inv ? c->inv_f : nullptr;
+  o.S = c->S;
+  o.invSf = c->invSf;
+  o.rtol_on = rtol_on;
+  o.rs = c->rs;
+  switch (c->p.estimator) {
+    case SUB_MEAN: {
+      { KTimer t(c, st, SUB_K_PREFIX); launch_chunk_prefix(in, n, pl, c->pre_lo, c->pre_hi, c->sig, c->uflow, c->P, d, 0, st); }
+      { KTimer t(c, st, SUB_K_MEAN); launch_window_mean(c->P, n, pl, c->pre_lo, c->pre_hi, c->sig, c->uflow, o, d, 1, st); }
+      break;
+    }
+    case SUB_MEDIAN: {
+      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(in, n, pl, c->skey, c->srank, c->snap, d, st); }
+      { KTimer t(c, st, SUB_K_SLIDE); launch_median_slide(c->skey, c->srank, c->snap, n, pl, o, d, st); }
+      break;
+    }
+    default: {
+      SgOut om = o;
+      om.out = c->M;
+      om.inv_f = nullptr;
+      om.rtol_on = 0;
+      SpecIn mi;
+      mi.acc = nullptr;
+      mi.S = nullptr;
+      mi.x = c->M;
+      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(in, n, pl, c->skey, c->srank, c->snap, d, st); }
+      { KTimer t(c, st, SUB_K_SLIDE); launch_median_slide(c->skey, c->srank, c->snap, n, pl, om, d, st); }
+      { KTimer t(c, st, SUB_K_PREFIX); launch_chunk_prefix(mi, n, pl, c->pre_lo, c->pre_hi, c->sig, c->uflow, nullptr, d, 1, st); }
+      { KTimer t(c, st, SUB_K_MEAN); launch_window_mean(c->M, n, pl, c->pre_lo, c->pre_hi, c->sig, c->uflow, o, d, 2, st); }
+      break;
+    }
+  }
+}
+
+static cudaError_t enqueue_body(sub_ctx* c, cudaStream_t st, unsigned long long handle, int use_cond) {
   const int rtol_on = c->p.conv_rtol > 0.0 ? 1 : 0;
   RunState* rs = c->rs;
-  { KTimer t(c, st, SUB_K_Q2P); launch_q2p(c->acc_lo, c->acc_hi, c->S, n, c->P, rs, 0, st); }
-  switch (c->p.estimator) {
-    case SUB_MEAN:
-      { KTimer t(c, st, SUB_K_PREFIX); launch_chunk_prefix(c->P, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st); }
-      { KTimer t(c, st, SUB_K_MEAN); launch_window_mean(c->P, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, c->Sg, c->S, rtol_on, rs, st); }
-      break;
-    case SUB_MEDIAN:
-      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(c->P, n, pl, c->skey, c->srank, c->snap, rs, st); }
-      { KTimer t(c, st, SUB_K_SLIDE); launch_median_slide(c->skey, c->srank, c->snap, n, pl, c->Sg, nullptr, c->S, rtol_on, rs, st); }
-      break;
-    default:
-      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(c->P, n, pl, c->skey, c->srank, c->snap, rs, st); }
-      { KTimer t(c, st, SUB_K_SLIDE); launch_median_slide(c->skey, c->srank, c->snap, n, pl, c->M, &rs->max_m_bits, c->S, 0, rs, st); }
-      { KTimer t(c, st, SUB_K_PREFIX); launch_chunk_prefix(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st); }
-      { KTimer t(c, st, SUB_K_MEAN); launch_window_mean(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, c->Sg, c->S, rtol_on, rs, st); }
-      break;
-  }
+  SpecIn in;
+  in.acc = c->acc;
+  in.S = c->S;
+  in.x = nullptr;
+  enqueue_estimate(c, st, in, rtol_on, true, true);
   double th2 = c->p.rho_th * c->p.rho_th;
   {
     KTimer t(c, st, SUB_K_SNR);
-    launch_snr_resolve(c->cand, c->N > 0 ? c->N : 1, c->grid, c->S, c->R, c->gq, c->Sg, th2,
-                       c->p.conv_rtol, c->cres, c->resolved, c->acc_lo, c->acc_hi, rs, c->nsm, st);
+    launch_snr_resolve(c->cd, c->N > 0 ? c->N : 1, c->grid, tables_of(c), c->Sg, c->inv_f, th2,
+                       c->p.conv_rtol, snr_mode(c), c->resolved, c->acc, rs, dirty_of(c, true),
+                       c->plan.Kc, sg_radius_of(c), c->nsm, st);
   }
-  { KTimer t(c, st, SUB_K_CONTROL); launch_control(rs, c->p.max_iter, c->p.conv_rtol, c->new_hist, handle, use_cond, st); }
+  { KTimer t(c, st, SUB_K_CONTROL); launch_control(rs, c->p.max_iter, c->p.conv_rtol, c->new_hist, handle, use_cond, c->dirty, c->plan.nch, st); }
   return cudaGetLastError();
 }
 
@@ -478,6 +560,8 @@ static int fill_stats(sub_ctx* c, sub_stats* st) {
     st->k_lo = c->grid.k_lo;
     st->status = status;
     st->reserved = 0;
+    st->n_live = (int64_t)r.nlive;
+    st->n_exact = (int64_t)r.nexact;
   }
   return status;
 }
@@ -548,37 +632,35 @@ extern "C" int sub_estimate(sub_ctx* c, const double* P, double* out, int64_t n,
   if (!c) return SUB_EINVAL;
   if (n != c->grid.nb || !P || !out) { set_err(c, "sub_estimate needs n == n_bins (%lld) and two buffers", (long long)c->grid.nb); return SUB_EINVAL; }
   if (where != SUB_HOST && where != SUB_DEVICE) { set_err(c, "bad where"); return SUB_EINVAL; }
-  const SmoothPlan& pl = c->plan;
   cudaStream_t st = c->stream;
-  double* in = c->P;
-  double* res = c->Sg;
   cudaMemcpyKind k_in = where == SUB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   cudaMemcpyKind k_out = where == SUB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  CU(cudaMemcpyAsync(in, P, (size_t)n * 8, k_in, st), c);
+  // the input goes through the Sg buffer (as an input it is read before Sg is written)
+  double* in_buf = c->estimate_in;
+  CU(cudaMemcpyAsync(in_buf, P, (size_t)n * 8, k_in, st), c);
   CU(cudaMemsetAsync(c->rs, 0, sizeof(RunState), st), c);
-  RunState* rs = c->rs;
-  // the maximum of the input fixes the fixed-point scale of the window sums
-  launch_max_bits(in, n, &rs->max_p_bits, st);
-  switch (c->p.estimator) {
-    case SUB_MEAN:
-      launch_chunk_prefix(in, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st);
-      launch_window_mean(in, n, pl, &rs->max_p_bits, c->pre_lo, c->pre_hi, c->uflow, res, c->S, 0, rs, st);
-      break;
-    case SUB_MEDIAN:
-      launch_chunk_sort(in, n, pl, c->skey, c->srank, c->snap, rs, st);
-      launch_median_slide(c->skey, c->srank, c->snap, n, pl, res, nullptr, c->S, 0, rs, st);
-      break;
-    default:
-      launch_chunk_sort(in, n, pl, c->skey, c->srank, c->snap, rs, st);
-      launch_median_slide(c->skey, c->srank, c->snap, n, pl, c->M, &rs->max_m_bits, c->S, 0, rs, st);
-      launch_chunk_prefix(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, rs, st);
-      launch_window_mean(c->M, n, pl, &rs->max_m_bits, c->pre_lo, c->pre_hi, c->uflow, res, c->S, 0, rs, st);
-      break;
-  }
+  SpecIn in;
+  in.acc = nullptr;
+  in.S = nullptr;
+  in.x = in_buf;
+  enqueue_estimate(c, st, in, 0, false, false);
   CU(cudaGetLastError(), c);
-  CU(cudaMemcpyAsync(out, res, (size_t)n * 8, k_out, st), c);
+  CU(cudaMemcpyAsync(out, c->Sg, (size_t)n * 8, k_out, st), c);
   CU(cudaStreamSynchronize(st), c);
   c->ran = false;  // the run's S_gal was overwritten
+  return SUB_OK;
+}
+
+extern "C" int sub_get_power(sub_ctx* c, double* P, int64_t n, int where) {
+  if (!c) return SUB_EINVAL;
+  if (n != c->grid.nb || !P) { set_err(c, "n must equal n_bins"); return SUB_EINVAL; }
+  if (where != SUB_HOST && where != SUB_DEVICE) { set_err(c, "bad where"); return SUB_EINVAL; }
+  if (!c->ran) { set_err(c, "no run yet"); return SUB_ESTATE; }
+  launch_power_out(c->acc, c->S, n, c->estimate_in, c->stream);
+  CU(cudaGetLastError(), c);
+  CU(cudaMemcpyAsync(P, c->estimate_in, (size_t)n * 8,
+                     where == SUB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream), c);
+  CU(cudaStreamSynchronize(c->stream), c);
   return SUB_OK;
 }
 

@@ -15,11 +15,11 @@ constexpr double kL = 2.5e9;        // LISA arm, m (Sec. III.A)
 constexpr double kPi = 3.14159265358979323846;
 // Chi^2_2 bias of the running median, (1 - 2/(9*2))^-3 = (8/9)^-3 = 729/512 (App. D).
 constexpr double kMedianBias = 729.0 / 512.0;
-// Per-bin fixed point of the deposited power: q = (P_k / S_instr,k) * 2^64, i.e. the
-// unit is 2^-64 of the instrument noise in that bin.  A contribution must stay below
-// 2^95 units (P/S < 2^31); the accumulator of a bin holds < 2^96 units.
-constexpr double kQScale = 18446744073709551616.0;        // 2^64
-constexpr double kQLimit = 39614081257132168796771975168.0;  // 2^95
+// Per-bin fixed point of the deposited power: q = (P_k / S_instr,k) * 2^96, i.e. the
+// unit is 2^-96 of the instrument noise in that bin.  A contribution must stay below
+// 2^127 units (P/S < 2^31 in one bin).
+constexpr double kQScale = 79228162514264337593543950336.0;                   // 2^96
+constexpr double kQLimit = 170141183460469231731687303715884105728.0;          // 2^127
 constexpr int kMaxWindow = 8192;
 constexpr int kSnapStride = 32;   // positions between stored active-set snapshots
 
@@ -88,22 +88,87 @@ __device__ __forceinline__ double u128_to_dbl_scaled(U128 v, int sh) {
   return ldexp(__ull2double_rn(top), shift - sh);
 }
 
-// Split a fixed-point contribution q (a double holding an integer-valued
-// amount of units, q < 2^95) into the part below 2^32 and the part above.
-// Both halves are accumulated in 64-bit words: the low word takes fewer than
-// 2^32 terms below 2^32 each, so neither word overflows and the sum
-// acc_hi * 2^32 + acc_lo is exact whatever the order of the additions.
-__device__ __forceinline__ void q_split(double q, u64* lo32, u64* hi64) {
+// A bin of the spectrum is three 64-bit words: w0 sums bits 0-31 of every
+// contribution, w1 bits 32-63 and w2 bits 64-127 (a fourth word pads the bin to
+// 32 bytes).  w0 and w1 take fewer than 2^32 terms below 2^32, so no word overflows
+// and Q = w2 2^64 + w1 2^32 + w0 is exact whatever the order of the additions;
+// removing a contribution subtracts the same three parts.
+// Contributions are kept to whole multiples of 2^32 units (2^-64 S_instr,k): the
+// resolution stays far below any power that matters, and the lowest word is never
+// touched, so a deposit or a removal is two 64-bit atomics.
+__device__ __forceinline__ void q_parts(double q, u64* c0, u64* c1, u64* c2) {
   U128 v = dbl_to_u128_scaled(q, 0);
-  *lo32 = v.lo & 0xFFFFFFFFull;
-  *hi64 = (v.lo >> 32) | (v.hi << 32);
+  *c0 = 0ull;
+  *c1 = v.lo >> 32;
+  *c2 = v.hi;
 }
 
-__device__ __forceinline__ U128 q_combine(u64 acc_lo, u64 acc_hi) {
+// f * T rounded to nearest (ties to even), computed exactly in integer arithmetic, returned
+// as x = u + 1/2 split into its integer part k and the top 24 bits of its fraction.  T is
+// given by its 53-bit integer mantissa mT and exponent eT (T = mT 2^eT).  Returns false when
+// the product is out of the range handled here (f not a positive normal number, or
+// f T >= 2^30), in which case the caller uses plain FP64.
+__device__ __forceinline__ bool ft_bin(double f, u64 mT, int eT, long long* k, unsigned* frac24,
+                                       int* fracbits) {
+  u64 b = (u64)__double_as_longlong(f);
+  int e = (int)((b >> 52) & 0x7FF);
+  if ((b >> 63) || e == 0 || e == 0x7FF) return false;
+  u64 mf = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  u64 lo = mf * mT;
+  u64 hi = __umul64hi(mf, mT);  // product in [2^104, 2^106)
+  int sh = ((hi >> 41) & 1ull) ? 53 : 52;
+  // M = p >> sh with round-to-nearest-even on the dropped bits
+  u64 M = (hi << (64 - sh)) | (lo >> sh);
+  u64 rmask = (1ull << sh) - 1ull;
+  u64 r = lo & rmask;
+  u64 half = 1ull << (sh - 1);
+  if (r > half || (r == half && (M & 1ull))) {
+    ++M;
+    if (M >> 53) {
+      M >>= 1;
+      ++sh;
+    }
+  }
+  int E = (e - 1075) + eT + sh;  // f T = M 2^E
+  if (E > -23 || E < -62) return false;
+  int F = -E;                    // fraction bits of M
+  u64 x = M + (1ull << (F - 1)); // (f T + 1/2) 2^F
+  *k = (long long)(x >> F);
+  u64 fr = x & ((1ull << F) - 1ull);
+  *frac24 = (F >= 24) ? (unsigned)(fr >> (F - 24)) : (unsigned)(fr << (24 - F));
+  *fracbits = F;
+  return true;
+}
+
+// Signed FP32 value of a double (truncated mantissa); 0 below the FP32 normal range.
+__device__ __forceinline__ float dbl_to_f32_signed(double v) {
+  u64 b = (u64)__double_as_longlong(v);
+  int e = (int)((b >> 52) & 0x7FF);
+  int ef = e - 1023 + 127;
+  if (e == 0 || ef <= 0) return 0.0f;
+  if (ef >= 255) return __int_as_float(0x7FC00000);
+  unsigned fb = ((unsigned)(b >> 63) << 31) | ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7FFFFFu);
+  return __uint_as_float(fb);
+}
+
+__device__ __forceinline__ U128 q_combine3(u64 w0, u64 w1, u64 w2) {
   U128 r;
-  r.lo = acc_lo + (acc_hi << 32);
-  r.hi = (acc_hi >> 32) + (r.lo < acc_lo ? 1ull : 0ull);
+  r.lo = w0 + (w1 << 32);
+  r.hi = w2 + (w1 >> 32) + (r.lo < w0 ? 1ull : 0ull);
   return r;
+}
+
+// v * 2^sh as an FP32 number, truncated (relative error < 2^-23), flushed to 0 below
+// the normal range and saturated at the largest float.  Integer operations only.
+__device__ __forceinline__ float dbl_to_f32_scaled(double v, int sh) {
+  u64 b = (u64)__double_as_longlong(v);
+  int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0 || (b >> 63)) return 0.0f;
+  int ef = e - 1023 + 127 + sh;
+  if (ef <= 0) return 0.0f;
+  if (ef >= 255) return 3.4028234e38f;
+  unsigned fb = ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7FFFFFu);
+  return __uint_as_float(fb);
 }
 
 // ---------------------------------------------------------------- source pieces

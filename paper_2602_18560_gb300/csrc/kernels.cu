@@ -3,18 +3,22 @@
 //
 // Steps of one run:
 //   tables   : S_instr(f_k) (App. C, SciRDv1 A channel, TDI-2 factor), R(f_k) (App. B)
-//              and the fixed-point scale of each bin.                       [once per context]
+//              and the scales derived from them.                              [per context]
 //   prepass  : one pass over the catalog: the bins each chirp sweeps, its power deposited
-//              into an exact fixed-point spectrum, rho_0 against S_instr, candidates
-//              rho_0 >= kappa rho_th compacted.                            [once per run]
-//   loop     : P_k = S_k Q_k 2^-64; S_gal = estimator of P (running mean / running median /
-//              median then mean, Eqs. running mean, running median); rho of each unresolved
+//              into an exact fixed-point spectrum, rho_0 against S_instr, the paper's
+//              candidates (rho_0 >= kappa rho_th) counted and the ones that can still be
+//              resolved (rho_0 > rho_th) kept.                                [per run]
+//   loop     : S_gal = estimator of P_k = S_k Q_k 2^-96 (running mean / running median /
+//              median then mean, Eqs. running mean, running median); rho of each kept
 //              candidate against S_instr + S_gal (Eqs. SNR inner product, inner product);
-//              sources with rho > rho_th removed from the spectrum exactly; loop control on
-//              the device.
+//              sources with rho > rho_th removed from the spectrum exactly; loop control
+//              on the device.
 //
-// No floating-point atomics: the spectrum is an integer (units of 2^-64 S_instr,k per bin),
-// so deposits and removals commute and every run gives the same bits.
+// No floating-point atomics: the spectrum is an integer (units of 2^-96 S_instr,k per bin),
+// so deposits and removals commute and every run gives the same bits.  GB300 runs FP64 at
+// 1/58 of the FP32 rate, so per-iteration work avoids FP64: medians select on the integer
+// bits of the doubles, window sums are integer, and the SNR test is screened in FP32 with
+// a proven error margin (exact FP64 recomputation inside the margin).
 
 #include <cuda_runtime.h>
 #include <cuda_device_runtime_api.h>
@@ -27,7 +31,8 @@ namespace gbsub {
 // ============================================================================ tables
 
 __global__ void k_tables(Grid g, int tdi2, double* __restrict__ S, double* __restrict__ R,
-                         double* __restrict__ gq) {
+                         double* __restrict__ gq, float* __restrict__ Gf,
+                         float* __restrict__ invSf) {
   long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (j >= g.nb) return;
   const double fstar = kC / (2.0 * kPi * kL);
@@ -54,127 +59,199 @@ __global__ void k_tables(Grid g, int tdi2, double* __restrict__ S, double* __res
   }
   S[j] = s_aa;
   R[j] = resp;
-  // q = A^2 w * gq_k is the contribution in units of 2^-64 S_instr,k:
-  // P / S = (T/5) R A^2 w / S.
-  gq[j] = kQScale * (g.t5 * resp / s_aa);
+  double ratio = g.t5 * resp / s_aa;          // P / S per unit of A^2 w
+  gq[j] = kQScale * ratio;                    // fixed-point units per unit of A^2 w
+  // FP32 screen factors; outside the normal FP32 range they are NaN, which sends every
+  // SNR decision touching the bin to the exact FP64 path.
+  double gs = ldexp(4.0 * ratio, -160);       // rho^2 against S_instr per unit A^2 w 2^160
+  double is = 1.0 / ldexp(s_aa, 150);
+  const double fmin_n = 1.1754943508222875e-38, fmax_n = 3.4028234663852886e38;
+  Gf[j] = (gs >= fmin_n && gs <= fmax_n) ? (float)gs : __int_as_float(0x7FC00000);
+  invSf[j] = (is >= fmin_n && is <= fmax_n) ? (float)is : __int_as_float(0x7FC00000);
 }
 
-void launch_tables(const Grid& g, int tdi2, double* S, double* R, double* gq, cudaStream_t st) {
+void launch_tables(const Grid& g, int tdi2, double* S, double* R, double* gq, float* Gf,
+                   float* invSf, cudaStream_t st) {
   int th = 256;
   long long bl = (g.nb + th - 1) / th;
-  k_tables<<<(unsigned)bl, th, 0, st>>>(g, tdi2, S, R, gq);
+  k_tables<<<(unsigned)bl, th, 0, st>>>(g, tdi2, S, R, gq, Gf, invSf);
 }
 
-// ============================================================================ prepass
+// ============================================================================ spectrum I/O
 
-__device__ __forceinline__ void deposit_q(unsigned long long* acc_lo, unsigned long long* acc_hi,
-                                          long long j, double q, unsigned* err) {
+__device__ __forceinline__ void deposit_q(unsigned long long* acc, long long j, double q,
+                                          unsigned* err) {
   if (!(q < kQLimit)) {
     atomicOr(err, ERR_RANGE);
     return;
   }
-  u64 lo, hi;
-  q_split(q, &lo, &hi);
-  if (lo) atomicAdd(acc_lo + j, lo);
-  if (hi) atomicAdd(acc_hi + j, hi);
+  u64 c0, c1, c2;
+  q_parts(q, &c0, &c1, &c2);
+  u64* a = acc + 4 * j;
+  if (c0) atomicAdd(a + 0, c0);
+  if (c1) atomicAdd(a + 1, c1);
+  if (c2) atomicAdd(a + 2, c2);
 }
+
+__device__ __forceinline__ void remove_q(unsigned long long* acc, long long j, double q) {
+  if (!(q < kQLimit)) return;  // never deposited
+  u64 c0, c1, c2;
+  q_parts(q, &c0, &c1, &c2);
+  u64* a = acc + 4 * j;
+  if (c0) atomicAdd(a + 0, (u64)(0ull - c0));
+  if (c1) atomicAdd(a + 1, (u64)(0ull - c1));
+  if (c2) atomicAdd(a + 2, (u64)(0ull - c2));
+}
+
+// Estimator input of bin j: P_j = S_j Q_j 2^-96, or x[j].
+__device__ __forceinline__ double spec_value(const SpecIn& in, long long j) {
+  if (in.acc) {
+    const ulonglong2* a = reinterpret_cast<const ulonglong2*>(in.acc + 4 * j);
+    ulonglong2 w01 = a[0];
+    u64 w2 = in.acc[4 * j + 2];
+    U128 Q = q_combine3(w01.x, w01.y, w2);
+    return __dmul_rn(in.S[j], u128_to_dbl_scaled(Q, 96));
+  }
+  return in.x[j];
+}
+
+__global__ void k_power_out(const unsigned long long* __restrict__ acc, const double* __restrict__ S,
+                            long long n, double* __restrict__ P) {
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  SpecIn in;
+  in.acc = acc;
+  in.S = S;
+  in.x = nullptr;
+  P[j] = spec_value(in, j);
+}
+
+void launch_power_out(const unsigned long long* acc, const double* S, long long n, double* P,
+                      cudaStream_t st) {
+  int th = 256;
+  k_power_out<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(acc, S, n, P);
+}
+
+// ============================================================================ prepass
 
 __global__ void __launch_bounds__(256) k_prepass(
     const double* __restrict__ A, const double* __restrict__ f, const double* __restrict__ fdot,
-    long long N, Grid g, const double* __restrict__ gq, double thr_q,
-    unsigned long long* __restrict__ acc_lo, unsigned long long* __restrict__ acc_hi,
-    Cand* __restrict__ cand, RunState* rs) {
+    long long N, Grid g, Tables tb, double thr_kappa, double thr_live,
+    unsigned long long* __restrict__ acc, Cands cd, RunState* rs) {
   const int lane = threadIdx.x & 31;
   const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) - lane;
   const long long stride = (long long)gridDim.x * blockDim.x;
+  // thresholds on r >= 0 compared as the integer bits of non-negative doubles
+  const u64 tk_bits = (u64)__double_as_longlong(thr_kappa);
+  const u64 tl_bits = (u64)__double_as_longlong(thr_live);
+  unsigned long long nkappa = 0;
   for (long long base = warp0; base < N; base += stride) {
     long long s = base + lane;
-    bool is_cand = false;
-    Cand rec;
+    bool live = false;
+    double a2 = 0.0;
+    Sweep sw;
+    sw.lo = sw.hi = 0.0;
+    sw.ka = sw.kb = 0;
     if (s < N) {
       double a = A[s];
-      Sweep sw = make_sweep(f[s], fdot[s], g.T, g.T2);
-      double a2 = __dmul_rn(a, a);
-      double r = 0.0;  // sum of q: rho_0^2 = 4 r 2^-64
-      if (sw.ka == sw.kb) {
-        long long j = sw.ka - g.k_lo;
+      double fs = f[s], fds = fdot[s];
+      a2 = __dmul_rn(a, a);
+      double r = 0.0;  // sum of q: rho_0^2 = 4 r 2^-96
+      // Common case without FP64: bin of f T + 1/2 exactly, and an FP32 bound on the sweep
+      // fdot T^2 proving that f T + fdot T^2 + 1/2 stays in the same bin (the FP64 path
+      // takes every case the bound cannot settle).
+      long long k0;
+      unsigned fr24;
+      int fb;
+      bool single = false;
+      if (ft_bin(fs, g.mT, g.eT, &k0, &fr24, &fb)) {
+        float du = __fmul_rn(dbl_to_f32_signed(fds), g.T2f);
+        float phi = __fmul_rn((float)fr24, 5.9604644775390625e-8f);  // 2^-24
+        float m = __fadd_rn(9.5367431640625e-7f, __fmul_rn(4e-7f, fabsf(du)));  // 2^-20 + ...
+        float x = __fadd_rn(phi, du);
+        single = (x >= m) && (x < __fsub_rn(1.0f, m));
+      }
+      if (single) {
+        sw.ka = sw.kb = k0;
+        long long j = k0 - g.k_lo;
         if (j >= 0 && j < g.nb) {
-          double q = __dmul_rn(a2, gq[j]);
-          deposit_q(acc_lo, acc_hi, j, q, &rs->err);
+          double q = __dmul_rn(a2, tb.gq[j]);
+          deposit_q(acc, j, q, &rs->err);
           r = q;
         }
       } else {
-        long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
-        long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
-        for (long long k = k0; k <= k1; ++k) {
-          double w = sweep_weight(sw, k);
-          if (w > 0.0) {
-            long long j = k - g.k_lo;
-            double q = __dmul_rn(__dmul_rn(a2, w), gq[j]);
-            deposit_q(acc_lo, acc_hi, j, q, &rs->err);
-            r = __dadd_rn(r, q);
+        sw = make_sweep(fs, fds, g.T, g.T2);
+        if (sw.ka == sw.kb) {
+          long long j = sw.ka - g.k_lo;
+          if (j >= 0 && j < g.nb) {
+            double q = __dmul_rn(a2, tb.gq[j]);
+            deposit_q(acc, j, q, &rs->err);
+            r = q;
+          }
+        } else {
+          long long k0b = sw.ka > g.k_lo ? sw.ka : g.k_lo;
+          long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
+          for (long long k = k0b; k <= k1; ++k) {
+            double w = sweep_weight(sw, k);
+            if (w > 0.0) {
+              long long j = k - g.k_lo;
+              double q = __dmul_rn(__dmul_rn(a2, w), tb.gq[j]);
+              deposit_q(acc, j, q, &rs->err);
+              r = __dadd_rn(r, q);
+            }
           }
         }
       }
-      if (r >= thr_q) {
-        is_cand = true;
-        rec.src = s;
-        rec.a2 = a2;
-        rec.lo = sw.lo;
-        rec.hi = sw.hi;
-      }
+      u64 rb = (u64)__double_as_longlong(r);
+      if (rb >= tk_bits) ++nkappa;
+      live = (rb > tl_bits) && (rb >= tk_bits);
+      if (live && single) sw = make_sweep(fs, fds, g.T, g.T2);  // endpoints for the record
     }
-    unsigned m = __ballot_sync(0xFFFFFFFFu, is_cand);
+    unsigned m = __ballot_sync(0xFFFFFFFFu, live);
     if (m) {
       unsigned long long b0 = 0;
-      if (lane == __ffs(m) - 1) b0 = atomicAdd(&rs->ncand, (unsigned long long)__popc(m));
-      b0 = __shfl_sync(0xFFFFFFFFu, b0, __ffs(m) - 1);
-      if (is_cand) cand[b0 + __popc(m & ((1u << lane) - 1u))] = rec;
+      int leader = __ffs(m) - 1;
+      if (lane == leader) b0 = atomicAdd(&rs->nlive, (unsigned long long)__popc(m));
+      b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
+      if (live) {
+        long long c = (long long)b0 + __popc(m & ((1u << lane) - 1u));
+        cd.src[c] = s;
+        cd.ka[c] = (int)(sw.ka - g.k_lo);
+        cd.nbin[c] = (int)(sw.kb - sw.ka + 1);
+        cd.a2f[c] = dbl_to_f32_scaled(a2, 160);
+        cd.flo[c] = (float)(sw.lo - (double)sw.ka);
+        cd.len[c] = (float)(sw.hi - sw.lo);
+        cd.a2[c] = a2;
+        cd.lo[c] = sw.lo;
+        cd.hi[c] = sw.hi;
+        cd.res[c] = 0;
+      }
     }
   }
+  for (int o = 16; o > 0; o >>= 1) nkappa += __shfl_xor_sync(0xFFFFFFFFu, nkappa, o);
+  if (lane == 0 && nkappa) atomicAdd(&rs->ncand, nkappa);
 }
 
 void launch_prepass(const double* A, const double* f, const double* fdot, long long N,
-                    const Grid& g, const double* gq, double thr_q, unsigned long long* acc_lo,
-                    unsigned long long* acc_hi, Cand* cand, RunState* rs, int nsm,
-                    cudaStream_t st) {
+                    const Grid& g, const Tables& tb, double thr_kappa, double thr_live,
+                    unsigned long long* acc, Cands cd, RunState* rs, int nsm, cudaStream_t st) {
   if (N <= 0) return;
   int th = 256;
   long long want = (N + th - 1) / th;
   long long cap = (long long)nsm * 8;
   int bl = (int)(want < cap ? want : cap);
-  k_prepass<<<bl, th, 0, st>>>(A, f, fdot, N, g, gq, thr_q, acc_lo, acc_hi, cand, rs);
+  k_prepass<<<bl, th, 0, st>>>(A, f, fdot, N, g, tb, thr_kappa, thr_live, acc, cd, rs);
 }
 
-// ============================================================================ spectrum
+// ============================================================================ reductions
 
-__device__ __forceinline__ void block_max_bits(u64 v, u64* target) {
+__device__ __forceinline__ void warp_max_atomic(u64 v, u64* target) {
   // v are bits of non-negative doubles: their integer order is the value order.
   for (int o = 16; o > 0; o >>= 1) {
     u64 t = __shfl_xor_sync(0xFFFFFFFFu, v, o);
     v = t > v ? t : v;
   }
   if ((threadIdx.x & 31) == 0 && v) atomicMax(target, v);
-}
-
-__global__ void k_q2p(const unsigned long long* __restrict__ acc_lo,
-                      const unsigned long long* __restrict__ acc_hi, const double* __restrict__ S,
-                      long long nb, double* __restrict__ P, RunState* rs) {
-  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  u64 bits = 0;
-  if (j < nb) {
-    U128 Q = q_combine(acc_lo[j], acc_hi[j]);
-    double p = __dmul_rn(S[j], u128_to_dbl_scaled(Q, 64));
-    P[j] = p;
-    bits = (u64)__double_as_longlong(p);
-  }
-  block_max_bits(bits, &rs->max_p_bits);
-}
-
-void launch_q2p(const unsigned long long* acc_lo, const unsigned long long* acc_hi,
-                const double* S, long long nb, double* P, RunState* rs, int, cudaStream_t st) {
-  int th = 256;
-  k_q2p<<<(unsigned)((nb + th - 1) / th), th, 0, st>>>(acc_lo, acc_hi, S, nb, P, rs);
 }
 
 __global__ void k_max_bits(const double* __restrict__ x, long long n, unsigned long long* max_bits) {
@@ -184,12 +261,28 @@ __global__ void k_max_bits(const double* __restrict__ x, long long n, unsigned l
     b = (u64)__double_as_longlong(x[j]);
     if (b >> 63) b = 0ull;
   }
-  block_max_bits(b, max_bits);
+  warp_max_atomic(b, max_bits);
 }
 
 void launch_max_bits(const double* x, long long n, unsigned long long* max_bits, cudaStream_t st) {
   int th = 256;
   k_max_bits<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(x, n, max_bits);
+}
+
+// S_gal epilogue: store, fold the relative change of S_n for conv_rtol, and the FP32
+// factor 1 / (1 + S_gal / S_instr) that the SNR screen multiplies rho_0^2 by.
+__device__ __forceinline__ double sg_store(const SgOut& o, long long j, double v) {
+  double rel = 0.0;
+  if (o.rtol_on) {
+    double a = __dadd_rn(o.S[j], v), b = __dadd_rn(o.S[j], o.out[j]);
+    rel = fabs(__dsub_rn(a, b)) / a;
+  }
+  o.out[j] = v;
+  if (o.inv_f) {
+    float ratio = __fmul_rn(dbl_to_f32_scaled(v, 150), o.invSf[j]);
+    o.inv_f[j] = __frcp_rn(__fadd_rn(1.0f, ratio));
+  }
+  return rel;
 }
 
 // ============================================================================ chunk sort
@@ -200,19 +293,19 @@ void launch_max_bits(const double* x, long long n, unsigned long long* max_bits,
 // is stored as a bitset ("snapshot") so that a thread can build the active set of any
 // window quickly.
 
-__global__ void k_chunk_sort(const double* __restrict__ x, long long n, SmoothPlan pl,
+__global__ void k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
                              unsigned long long* __restrict__ skey, uint16_t* __restrict__ srank,
-                             uint32_t* __restrict__ snap) {
+                             uint32_t* __restrict__ snap, Dirty d) {
   extern __shared__ unsigned long long sm_keys[];
   uint16_t* sm_idx = (uint16_t*)(sm_keys + pl.kpad);
   const int b = blockIdx.x;
+  if (!d.any(b, 0)) return;  // unchanged input: keys, ranks and snapshots still hold
   const long long base = (long long)b * pl.Kc;
   const int len = (int)((n - base) < pl.Kc ? (n - base) : pl.Kc);
   for (int i = threadIdx.x; i < pl.kpad; i += blockDim.x) {
     u64 k = ~0ull;
     if (i < len) {
-      double v = x[base + i];
-      k = (u64)__double_as_longlong(v);
+      k = (u64)__double_as_longlong(spec_value(in, base + i));
       if (k >> 63) k = 0ull;  // -0.0 (or a negative value) sorts as zero
     }
     sm_keys[i] = k;
@@ -258,11 +351,11 @@ __global__ void k_chunk_sort(const double* __restrict__ x, long long n, SmoothPl
   }
 }
 
-void launch_chunk_sort(const double* x, long long n, const SmoothPlan& pl, unsigned long long* skey,
-                       uint16_t* srank, uint32_t* snap, const RunState*, cudaStream_t st) {
+void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
+                       uint16_t* srank, uint32_t* snap, Dirty d, cudaStream_t st) {
   size_t smem = (size_t)pl.kpad * (sizeof(u64) + sizeof(uint16_t));
   int th = pl.kpad >= 1024 ? 1024 : (pl.kpad < 64 ? 64 : pl.kpad);
-  k_chunk_sort<<<pl.nch, th, smem, st>>>(x, n, pl, skey, srank, snap);
+  k_chunk_sort<<<pl.nch, th, smem, st>>>(in, n, pl, skey, srank, snap, d);
 }
 
 // ============================================================================ median slide
@@ -334,7 +427,6 @@ __device__ __forceinline__ int merge_path(const SlideSide& A, const SlideSide& B
   int hi = P < A.len ? P : A.len;
   while (lo < hi) {
     int x = (lo + hi + 1) >> 1;  // try taking x elements of A
-    // valid iff A[x-1] precedes B[P-x] (or P-x == B.len)
     int y = P - x;
     bool ok = (y >= B.len) || (__ldg(A.key + x - 1) <= __ldg(B.key + y));
     if (ok) lo = x; else hi = x - 1;
@@ -344,8 +436,7 @@ __device__ __forceinline__ int merge_path(const SlideSide& A, const SlideSide& B
 
 __global__ void __launch_bounds__(128) k_median_slide(
     const unsigned long long* __restrict__ skey, const uint16_t* __restrict__ srank,
-    const uint32_t* __restrict__ snap, long long n, SmoothPlan pl, double* __restrict__ out,
-    unsigned long long* max_bits_out, const double* __restrict__ S, int rtol_on, RunState* rs) {
+    const uint32_t* __restrict__ snap, long long n, SmoothPlan pl, SgOut o, Dirty d) {
   extern __shared__ uint32_t sm_bits[];
   const int T = blockDim.x;
   const int tid = threadIdx.x;
@@ -354,9 +445,10 @@ __global__ void __launch_bounds__(128) k_median_slide(
   uint32_t* bsY = sm_bits + (size_t)nw * T + tid;
   const long long g = blockIdx.x * (long long)T + tid;
   const long long j0 = g * pl.L;
-  u64 mbits = 0;
   double relmax = 0.0;
-  if (j0 < n) {
+  // the outputs of this thread lie in one chunk (L divides Kc); their windows read chunks
+  // within one of it
+  if (j0 < n && d.any(j0 / pl.Kc, 1)) {
     const long long j1 = (j0 + pl.L < n) ? j0 + pl.L : n;
     const int h = pl.W / 2;
     long long s_cur = j0 - h > 0 ? j0 - h : 0;
@@ -500,76 +592,343 @@ __global__ void __launch_bounds__(128) k_median_slide(
                         0.5);
       }
       double v = __dmul_rn(kMedianBias, med);
-      if (rtol_on) {
-        double a = __dadd_rn(S[j], v), bprev = __dadd_rn(S[j], out[j]);
-        double rel = fabs(__dsub_rn(a, bprev)) / a;
-        relmax = rel > relmax ? rel : relmax;
-      }
-      out[j] = v;
-      u64 vb = (u64)__double_as_longlong(v);
-      mbits = vb > mbits ? vb : mbits;
+      double rel = sg_store(o, j, v);
+      relmax = rel > relmax ? rel : relmax;
     }
   }
-  if (max_bits_out) block_max_bits(mbits, max_bits_out);
-  if (rtol_on) block_max_bits((u64)__double_as_longlong(relmax), &rs->relchg_bits);
+  if (o.rtol_on) warp_max_atomic((u64)__double_as_longlong(relmax), &o.rs->relchg_bits);
+}
+
+// Same algorithm with the sorted keys and ranks of the three chunks a window of output
+// chunk c can touch (c-1, c, c+1) staged in shared memory: one CTA per output chunk, so
+// the dependent loads of each thread's merge-cut walk hit shared memory.  Snapshots are
+// read from global memory (a few independent loads per thread at set-up).
+__global__ void __launch_bounds__(256) k_median_slide_smem(
+    const unsigned long long* __restrict__ skey, const uint16_t* __restrict__ srank,
+    const uint32_t* __restrict__ snap, long long n, SmoothPlan pl, SgOut o, Dirty d) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int T = blockDim.x;
+  const int tid = threadIdx.x;
+  const int nw = pl.nw;
+  const int Kc = pl.Kc;
+  const long long c = blockIdx.x;
+  if (!d.any(c, 1)) return;  // no window of this chunk changed
+  u64* sk = (u64*)sm_raw;                                   // [3][Kc]
+  uint16_t* sr = (uint16_t*)(sk + 3 * (size_t)Kc);          // [3][Kc]
+  uint32_t* sb = (uint32_t*)(sr + 3 * (size_t)Kc);          // [2][nw][T]
+  const long long c0 = c - 1;  // chunk held in slot 0
+  for (int slot = 0; slot < 3; ++slot) {
+    long long ch = c0 + slot;
+    if (ch < 0 || ch >= pl.nch) continue;
+    long long base = ch * (long long)Kc;
+    int len = (int)((n - base) < Kc ? (n - base) : Kc);
+    const ulonglong2* gk = reinterpret_cast<const ulonglong2*>(skey + base);
+    ulonglong2* dk = reinterpret_cast<ulonglong2*>(sk + (size_t)slot * Kc);
+    for (int i = tid; i < (len + 1) / 2; i += T) dk[i] = gk[i];
+    for (int i = tid; i < len; i += T) sr[(size_t)slot * Kc + i] = srank[base + i];
+  }
+  __syncthreads();
+  uint32_t* bsX = sb + tid;
+  uint32_t* bsY = sb + (size_t)nw * T + tid;
+  const long long j0 = c * Kc + (long long)tid * pl.L;
+  double relmax = 0.0;
+  if (j0 < n) {
+    long long jend = (c + 1) * (long long)Kc;
+    long long j1 = j0 + pl.L < jend ? j0 + pl.L : jend;
+    if (j1 > n) j1 = n;
+    const int h = pl.W / 2;
+    long long s_cur = j0 - h > 0 ? j0 - h : 0;
+    long long e_cur = j0 - h + pl.W - 1 < n - 1 ? j0 - h + pl.W - 1 : n - 1;
+    long long chA = s_cur / Kc;
+    auto bind = [&](SlideSide& sd, long long ch) {
+      sd.base = ch * Kc;
+      long long rem = n - sd.base;
+      sd.len = rem <= 0 ? 0 : (rem < Kc ? (int)rem : Kc);
+      long long slot = ch - c0;
+      if (slot < 0) slot = 0;
+      if (slot > 2) slot = 2;
+      sd.key = sk + slot * Kc;
+      sd.rank = sr + slot * Kc;
+      long long chs = ch < pl.nch ? ch : pl.nch - 1;
+      sd.snap = snap + chs * (long long)pl.nsnap * nw;
+    };
+    SlideSide A, B;
+    bind(A, chA);
+    bind(B, chA + 1);
+    A.bs = bsX;
+    B.bs = bsY;
+    {
+      int pa0 = (int)(s_cur - A.base);
+      long long ea = e_cur - A.base + 1;
+      int pa1 = (int)(ea < A.len ? ea : A.len);
+      int m0 = pa0 / kSnapStride, m1 = pa1 / kSnapStride;
+      if (A.len == 0 || pa1 <= pa0) {
+        for (int w = 0; w < nw; ++w) A.bs[w * T] = 0u;
+      } else {
+        const uint32_t* s0 = A.snap + (size_t)m0 * nw;
+        const uint32_t* s1 = A.snap + (size_t)m1 * nw;
+        for (int w = 0; w < nw; ++w) A.bs[w * T] = __ldg(s0 + w) & ~__ldg(s1 + w);
+        for (int p = m0 * kSnapStride; p < pa0; ++p) bs_clear(A.bs, T, A.rank[p]);
+        int q0 = m1 * kSnapStride > pa0 ? m1 * kSnapStride : pa0;
+        for (int p = q0; p < pa1; ++p) bs_set(A.bs, T, A.rank[p]);
+      }
+      long long eb = e_cur - B.base + 1;
+      int pb1 = eb <= 0 ? 0 : (int)(eb < B.len ? eb : B.len);
+      if (B.len == 0 || pb1 <= 0) {
+        for (int w = 0; w < nw; ++w) B.bs[w * T] = 0u;
+      } else {
+        int mb = pb1 / kSnapStride;
+        const uint32_t* s0 = B.snap;
+        const uint32_t* s1 = B.snap + (size_t)mb * nw;
+        for (int w = 0; w < nw; ++w) B.bs[w * T] = __ldg(s0 + w) & ~__ldg(s1 + w);
+        for (int p = mb * kSnapStride; p < pb1; ++p) bs_set(B.bs, T, B.rank[p]);
+      }
+    }
+    int cnt = (int)(e_cur - s_cur + 1);
+    int kq = cnt / 2 + 1;
+    // initial cut: smallest merged position with kq active elements before it
+    int lo = kq, hi = A.len + B.len;
+    while (lo < hi) {
+      int P = (lo + hi) >> 1;
+      int lo2 = P - B.len > 0 ? P - B.len : 0, hi2 = P < A.len ? P : A.len;
+      while (lo2 < hi2) {
+        int x = (lo2 + hi2 + 1) >> 1;
+        int y = P - x;
+        bool ok = (y >= B.len) || (A.key[x - 1] <= B.key[y]);
+        if (ok) lo2 = x; else hi2 = x - 1;
+      }
+      int k2 = popc_prefix(A.bs, T, lo2) + popc_prefix(B.bs, T, P - lo2);
+      if (k2 >= kq) hi = P; else lo = P + 1;
+    }
+    int cA, cB;
+    {
+      int P = lo;
+      int lo2 = P - B.len > 0 ? P - B.len : 0, hi2 = P < A.len ? P : A.len;
+      while (lo2 < hi2) {
+        int x = (lo2 + hi2 + 1) >> 1;
+        int y = P - x;
+        bool ok = (y >= B.len) || (A.key[x - 1] <= B.key[y]);
+        if (ok) lo2 = x; else hi2 = x - 1;
+      }
+      cA = lo2;
+      cB = P - lo2;
+    }
+    int pc = kq;
+    for (long long j = j0; j < j1; ++j) {
+      if (j > j0) {
+        long long sj = j - h > 0 ? j - h : 0;
+        long long ej = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
+        if (sj > s_cur) {
+          int sx = A.rank[s_cur - A.base];
+          bs_clear(A.bs, T, sx);
+          --cnt;
+          if (sx < cA) --pc;
+          s_cur = sj;
+          if (s_cur >= A.base + A.len && B.len > 0) {
+            uint32_t* freed = A.bs;
+            A = B;
+            cA = cB;
+            ++chA;
+            bind(B, chA + 1);
+            B.bs = freed;
+            if (cA < A.len) {
+              u64 ka = A.key[cA];
+              int lo3 = 0, hi3 = B.len;
+              while (lo3 < hi3) {
+                int mid = (lo3 + hi3) >> 1;
+                if (B.key[mid] < ka) lo3 = mid + 1; else hi3 = mid;
+              }
+              cB = lo3;
+            } else {
+              cB = B.len;
+            }
+          }
+        }
+        if (ej > e_cur) {
+          e_cur = ej;
+          if (ej < A.base + A.len) {
+            int sx = A.rank[ej - A.base];
+            bs_set(A.bs, T, sx);
+            ++cnt;
+            if (sx < cA) ++pc;
+          } else {
+            int sx = B.rank[ej - B.base];
+            bs_set(B.bs, T, sx);
+            ++cnt;
+            if (sx < cB) ++pc;
+          }
+        }
+        kq = cnt / 2 + 1;
+        while (pc < kq) {
+          int nA = bs_next(A.bs, T, nw, cA, A.len);
+          int nB = bs_next(B.bs, T, nw, cB, B.len);
+          bool takeA = (nB >= B.len) || (nA < A.len && A.key[nA] <= B.key[nB]);
+          if (takeA) {
+            u64 ka = A.key[nA];
+            cA = nA + 1;
+            while (cB < B.len && B.key[cB] < ka) ++cB;
+          } else {
+            u64 kb = B.key[nB];
+            cB = nB + 1;
+            while (cA < A.len && A.key[cA] <= kb) ++cA;
+          }
+          ++pc;
+        }
+        while (pc > kq) {
+          int pA = bs_prev(A.bs, T, cA);
+          int pB = bs_prev(B.bs, T, cB);
+          bool takeB = (pA < 0) || (pB >= 0 && B.key[pB] >= A.key[pA]);
+          if (takeB) {
+            u64 kb = B.key[pB];
+            cB = pB;
+            while (cA > 0 && A.key[cA - 1] > kb) --cA;
+          } else {
+            u64 ka = A.key[pA];
+            cA = pA;
+            while (cB > 0 && B.key[cB - 1] >= ka) --cB;
+          }
+          --pc;
+        }
+      }
+      int pA = bs_prev(A.bs, T, cA);
+      int pB = bs_prev(B.bs, T, cB);
+      bool hiB = (pA < 0) || (pB >= 0 && B.key[pB] >= A.key[pA]);
+      u64 khi = hiB ? B.key[pB] : A.key[pA];
+      double med;
+      if (cnt & 1) {
+        med = __longlong_as_double((i64)khi);
+      } else {
+        int q1, q2;
+        u64 k1 = 0, k2 = 0;
+        bool h1 = false, h2 = false;
+        if (hiB) {
+          q1 = pA;
+          q2 = bs_prev(B.bs, T, pB);
+          if (q1 >= 0) { k1 = A.key[q1]; h1 = true; }
+          if (q2 >= 0) { k2 = B.key[q2]; h2 = true; }
+        } else {
+          q1 = pB;
+          q2 = bs_prev(A.bs, T, pA);
+          if (q1 >= 0) { k1 = B.key[q1]; h1 = true; }
+          if (q2 >= 0) { k2 = A.key[q2]; h2 = true; }
+        }
+        u64 klo = (h1 && h2) ? (k1 > k2 ? k1 : k2) : (h1 ? k1 : k2);
+        med = __dmul_rn(__dadd_rn(__longlong_as_double((i64)klo), __longlong_as_double((i64)khi)),
+                        0.5);
+      }
+      double v = __dmul_rn(kMedianBias, med);
+      double rel = sg_store(o, j, v);
+      relmax = rel > relmax ? rel : relmax;
+    }
+  }
+  if (o.rtol_on) warp_max_atomic((u64)__double_as_longlong(relmax), &o.rs->relchg_bits);
+}
+
+// Threads per chunk for the shared-memory slide, and whether its staging fits.
+static int smem_slide_threads(const SmoothPlan& pl) {
+  int t = pl.Kc / 16;
+  if (t < 32) t = 32;
+  if (t > 128) t = 128;
+  return t;
+}
+static size_t smem_slide_bytes(const SmoothPlan& pl, int T) {
+  return (size_t)3 * pl.Kc * (sizeof(u64) + sizeof(uint16_t)) + (size_t)2 * pl.nw * T * 4;
 }
 
 void launch_median_slide(const unsigned long long* skey, const uint16_t* srank,
-                         const uint32_t* snap, long long n, const SmoothPlan& pl, double* out,
-                         unsigned long long* max_bits_out, const double* S, int rtol_on,
-                         RunState* rs, cudaStream_t st) {
+                         const uint32_t* snap, long long n, const SmoothPlan& pl, SgOut o,
+                         Dirty d, cudaStream_t st) {
+  int ts = smem_slide_threads(pl);
+  size_t ss = smem_slide_bytes(pl, ts);
+  if (ss <= 160 * 1024) {
+    SmoothPlan p2 = pl;
+    p2.L = (pl.Kc + ts - 1) / ts;
+    k_median_slide_smem<<<pl.nch, ts, ss, st>>>(skey, srank, snap, n, p2, o, d);
+    return;
+  }
   int th = pl.slide_threads;
   long long threads = (n + pl.L - 1) / pl.L;
   long long bl = (threads + th - 1) / th;
   size_t smem = (size_t)2 * pl.nw * th * sizeof(uint32_t);
-  k_median_slide<<<(unsigned)bl, th, smem, st>>>(skey, srank, snap, n, pl, out, max_bits_out, S,
-                                                 rtol_on, rs);
+  k_median_slide<<<(unsigned)bl, th, smem, st>>>(skey, srank, snap, n, pl, o, d);
 }
 
 // ============================================================================ window mean
-// Exact window sums: every value becomes a 128-bit integer number of units 2^-sigma,
-// where sigma comes from the maximum of the input so that any sum of 2 Kc inputs fits;
-// each chunk stores its inclusive prefix sums, and a window (at most two chunks) is a
-// difference/sum of prefixes.  Integer sums are exact, so there is no cancellation
-// however large the dynamic range of the spectrum.
+// Exact window sums: inside chunk b every value becomes a 128-bit integer number of units
+// 2^-sig[b], sig[b] chosen from the chunk's maximum so that a sum over the chunk fits;
+// each chunk stores its inclusive prefix sums.  A window (at most two chunks) is one
+// difference of prefixes per chunk, each converted to double once, so there is no
+// cancellation however large the dynamic range of the spectrum.
 
 __device__ __forceinline__ int sigma_from_max(u64 maxbits) {
-  // max < 2^(e - 1022) with e the biased exponent; 2 Kc <= 2^14 terms stay below 2^127.
+  // max < 2^(e - 1022) with e the biased exponent; Kc <= 2^13 terms stay below 2^127.
   int e = (int)((maxbits >> 52) & 0x7FF);
   if (e == 0) e = 1;
-  return 1135 - e;
+  return 1136 - e;
 }
 
-__global__ void k_chunk_prefix(const double* __restrict__ x, long long n, SmoothPlan pl,
-                               const unsigned long long* max_bits,
+__global__ void k_chunk_prefix(SpecIn in, long long n, SmoothPlan pl,
                                unsigned long long* __restrict__ pre_lo,
-                               unsigned long long* __restrict__ pre_hi,
-                               unsigned* __restrict__ uflow) {
+                               unsigned long long* __restrict__ pre_hi, int* __restrict__ sig,
+                               unsigned* __restrict__ uflow, double* __restrict__ x_out, Dirty d,
+                               int in_radius) {
   __shared__ U128 warp_tot[32];
+  __shared__ u64 warp_max[32];
   __shared__ int any_uf;
   const int b = blockIdx.x;
+  if (!d.any(b, in_radius)) return;  // unchanged input: prefix sums still hold
   const long long base = (long long)b * pl.Kc;
   const int len = (int)((n - base) < pl.Kc ? (n - base) : pl.Kc);
-  const int sigma = sigma_from_max(*max_bits);
   const int per = (pl.Kc + blockDim.x - 1) / blockDim.x;
   const int p0 = threadIdx.x * per;
-  U128 run{0ull, 0ull};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // pass 1: values and the chunk maximum
+  double v[8];  // per <= 8 (Kc <= 8192 with 1024 threads)
+  u64 mb = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (i < per) {
+      int p = p0 + i;
+      double x = 0.0;
+      if (p < len) {
+        x = spec_value(in, base + p);
+        if (x_out) x_out[base + p] = x;
+      }
+      v[i] = x;
+      u64 bits = (u64)__double_as_longlong(x);
+      if (!(bits >> 63) && bits > mb) mb = bits;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    u64 t = __shfl_xor_sync(0xFFFFFFFFu, mb, o);
+    mb = t > mb ? t : mb;
+  }
+  if (lane == 0) warp_max[warp] = mb;
   if (threadIdx.x == 0) any_uf = 0;
   __syncthreads();
-  // pass 1: thread totals; note inputs > 0 that fall below one unit
+  if (threadIdx.x < 32) {
+    u64 t = threadIdx.x < nwarp ? warp_max[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      u64 u = __shfl_xor_sync(0xFFFFFFFFu, t, o);
+      t = u > t ? u : t;
+    }
+    if (threadIdx.x == 0) warp_max[0] = t;
+  }
+  __syncthreads();
+  const int sigma = sigma_from_max(warp_max[0]);
+  // pass 2: thread totals in fixed point; note inputs > 0 below one unit
+  U128 run{0ull, 0ull};
   int uf = 0;
-  for (int i = 0; i < per; ++i) {
-    int p = p0 + i;
-    if (p < len) {
-      double v = x[base + p];
-      U128 q = dbl_to_u128_scaled(v, sigma);
-      if (v > 0.0 && u128_is_zero(q)) uf = 1;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (i < per && p0 + i < len) {
+      U128 q = dbl_to_u128_scaled(v[i], sigma);
+      if (v[i] > 0.0 && u128_is_zero(q)) uf = 1;
       run = u128_add(run, q);
     }
   }
   if (uf) any_uf = 1;
   // exclusive scan of thread totals
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   U128 inc = run;
   for (int o = 1; o < 32; o <<= 1) {
     U128 t;
@@ -580,99 +939,108 @@ __global__ void k_chunk_prefix(const double* __restrict__ x, long long n, Smooth
   if (lane == 31) warp_tot[warp] = inc;
   __syncthreads();
   if (warp == 0) {
-    int nwarp = blockDim.x >> 5;
-    U128 v = lane < nwarp ? warp_tot[lane] : U128{0ull, 0ull};
+    U128 t2 = lane < nwarp ? warp_tot[lane] : U128{0ull, 0ull};
     for (int o = 1; o < 32; o <<= 1) {
       U128 t;
-      t.lo = __shfl_up_sync(0xFFFFFFFFu, v.lo, o);
-      t.hi = __shfl_up_sync(0xFFFFFFFFu, v.hi, o);
-      if (lane >= o) v = u128_add(v, t);
+      t.lo = __shfl_up_sync(0xFFFFFFFFu, t2.lo, o);
+      t.hi = __shfl_up_sync(0xFFFFFFFFu, t2.hi, o);
+      if (lane >= o) t2 = u128_add(t2, t);
     }
-    if (lane < nwarp) warp_tot[lane] = v;  // inclusive over warps
+    if (lane < nwarp) warp_tot[lane] = t2;  // inclusive over warps
   }
   __syncthreads();
   U128 offs = u128_sub(inc, run);  // exclusive within warp
   if (warp > 0) offs = u128_add(offs, warp_tot[warp - 1]);
-  // pass 2: write inclusive prefixes
-  for (int i = 0; i < per; ++i) {
-    int p = p0 + i;
-    if (p < len) {
-      offs = u128_add(offs, dbl_to_u128_scaled(x[base + p], sigma));
-      pre_lo[base + p] = offs.lo;
-      pre_hi[base + p] = offs.hi;
+  // pass 3: write inclusive prefixes
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (i < per && p0 + i < len) {
+      offs = u128_add(offs, dbl_to_u128_scaled(v[i], sigma));
+      pre_lo[base + p0 + i] = offs.lo;
+      pre_hi[base + p0 + i] = offs.hi;
     }
   }
-  if (threadIdx.x == 0) uflow[b] = (unsigned)any_uf;
+  if (threadIdx.x == 0) {
+    uflow[b] = (unsigned)any_uf;
+    sig[b] = sigma;
+  }
 }
 
-void launch_chunk_prefix(const double* x, long long n, const SmoothPlan& pl,
-                         const unsigned long long* max_bits, unsigned long long* pre_lo,
-                         unsigned long long* pre_hi, unsigned* uflow, const RunState*,
-                         cudaStream_t st) {
-  int th = 256;
-  k_chunk_prefix<<<pl.nch, th, 0, st>>>(x, n, pl, max_bits, pre_lo, pre_hi, uflow);
+void launch_chunk_prefix(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* pre_lo,
+                         unsigned long long* pre_hi, int* sig, unsigned* uflow, double* x_out,
+                         Dirty d, int in_radius, cudaStream_t st) {
+  int th = pl.Kc < 1024 ? pl.Kc : 1024;  // at most 8 values per thread
+  k_chunk_prefix<<<pl.nch, th, 0, st>>>(in, n, pl, pre_lo, pre_hi, sig, uflow, x_out, d,
+                                        in_radius);
+}
+
+// Sum of x[a .. e] inside one chunk as a double (a, e in the chunk, a <= e).
+__device__ __forceinline__ double part_sum(const double* __restrict__ x, long long cbase, long long a,
+                                           long long e, const unsigned long long* __restrict__ pre_lo,
+                                           const unsigned long long* __restrict__ pre_hi, int sigma,
+                                           unsigned uf) {
+  U128 pe{pre_lo[e], pre_hi[e]};
+  U128 sum = pe;
+  if (a > cbase) sum = u128_sub(pe, U128{pre_lo[a - 1], pre_hi[a - 1]});
+  long long cnt = e - a + 1;
+  // Each input lost less than one unit; if the sum holds fewer than cnt * 2^40 units the
+  // relative error could exceed 2^-40, so add the doubles directly instead.  A zero sum
+  // is exact only if no input of the chunk fell below one unit.
+  if (u128_is_zero(sum) && !uf) return 0.0;
+  bool small = (sum.hi == 0ull) && (sum.lo < ((unsigned long long)cnt << 40));
+  if (small) {
+    double acc = 0.0;
+    for (long long i = a; i <= e; ++i) acc = __dadd_rn(acc, x[i]);
+    return acc;
+  }
+  return u128_to_dbl_scaled(sum, sigma);
 }
 
 __global__ void k_window_mean(const double* __restrict__ x, long long n, SmoothPlan pl,
-                              const unsigned long long* max_bits,
                               const unsigned long long* __restrict__ pre_lo,
                               const unsigned long long* __restrict__ pre_hi,
-                              const unsigned* __restrict__ uflow, double* __restrict__ out,
-                              const double* __restrict__ S, int rtol_on, RunState* rs) {
+                              const int* __restrict__ sig, const unsigned* __restrict__ uflow,
+                              SgOut o, Dirty d, int out_radius) {
   long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double relmax = 0.0;
-  if (j < n) {
-    const int sigma = sigma_from_max(*max_bits);
+  if (j < n && d.any(j / pl.Kc, out_radius)) {
     const int h = pl.W / 2;
     long long s = j - h > 0 ? j - h : 0;
     long long e = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
     long long cs = s / pl.Kc, ce = e / pl.Kc;
-    U128 pe{pre_lo[e], pre_hi[e]};
-    U128 sum;
-    U128 before{0ull, 0ull};
-    if (s > cs * pl.Kc) before = U128{pre_lo[s - 1], pre_hi[s - 1]};
+    long long cnt = e - s + 1;
+    double sum;
     if (cs == ce) {
-      sum = u128_sub(pe, before);
+      sum = part_sum(x, cs * pl.Kc, s, e, pre_lo, pre_hi, sig[cs], uflow[cs]);
     } else {
       long long last = cs * pl.Kc + pl.Kc - 1;
-      U128 tot{pre_lo[last], pre_hi[last]};
-      sum = u128_add(u128_sub(tot, before), pe);
+      double s1 = part_sum(x, cs * pl.Kc, s, last, pre_lo, pre_hi, sig[cs], uflow[cs]);
+      double s2 = part_sum(x, ce * pl.Kc, ce * pl.Kc, e, pre_lo, pre_hi, sig[ce], uflow[ce]);
+      sum = __dadd_rn(s1, s2);
     }
-    long long cnt = e - s + 1;
-    double v;
-    // Each input lost less than one unit; if the sum holds fewer than cnt * 2^40 units
-    // the relative error could exceed 2^-40, so add the doubles directly instead.  A zero
-    // sum is exact only if no input of these chunks fell below one unit.
-    bool small = (sum.hi == 0ull) && (sum.lo < ((unsigned long long)cnt << 40));
-    if (u128_is_zero(sum) && !(uflow[cs] | uflow[ce])) {
-      v = 0.0;
-    } else if (small) {
-      double acc = 0.0;
-      for (long long i = s; i <= e; ++i) acc = __dadd_rn(acc, x[i]);
-      v = __ddiv_rn(acc, (double)cnt);
-    } else {
-      double sd = u128_to_dbl_scaled(sum, sigma);
-      v = (cnt == pl.W) ? __dmul_rn(sd, 1.0 / (double)pl.W) : __ddiv_rn(sd, (double)cnt);
-    }
-    if (rtol_on) {
-      double a = __dadd_rn(S[j], v), bprev = __dadd_rn(S[j], out[j]);
-      relmax = fabs(__dsub_rn(a, bprev)) / a;
-    }
-    out[j] = v;
+    double v = (cnt == pl.W) ? __dmul_rn(sum, 1.0 / (double)pl.W) : __ddiv_rn(sum, (double)cnt);
+    relmax = sg_store(o, j, v);
   }
-  if (rtol_on) block_max_bits((u64)__double_as_longlong(relmax), &rs->relchg_bits);
+  if (o.rtol_on) warp_max_atomic((u64)__double_as_longlong(relmax), &o.rs->relchg_bits);
 }
 
 void launch_window_mean(const double* x, long long n, const SmoothPlan& pl,
-                        const unsigned long long* max_bits, const unsigned long long* pre_lo,
-                        const unsigned long long* pre_hi, const unsigned* uflow, double* out,
-                        const double* S, int rtol_on, RunState* rs, cudaStream_t st) {
+                        const unsigned long long* pre_lo, const unsigned long long* pre_hi,
+                        const int* sig, const unsigned* uflow, SgOut o, Dirty d, int out_radius,
+                        cudaStream_t st) {
   int th = 256;
-  k_window_mean<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(x, n, pl, max_bits, pre_lo, pre_hi,
-                                                               uflow, out, S, rtol_on, rs);
+  k_window_mean<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(x, n, pl, pre_lo, pre_hi, sig, uflow,
+                                                               o, d, out_radius);
 }
 
 // ============================================================================ SNR + resolve
+// rho^2 = 4 (T/5) A^2 sum_k w_k R_k / (S_k + S_gal,k) = sum_k rho0_k / (1 + S_gal,k / S_k).
+// The screen evaluates it in FP32 as sum_k a2f w_k Gf_k inv_f_k; its relative error is
+// below 2.2e-6 + 2e-7 per bin (FP32 roundings of the inputs, the ratio, the reciprocal,
+// the products and the sum of positive terms), so outside a margin of 1e-5 + 4e-7 per
+// bin around rho_th^2 the FP64 decision is known.  Inside it, and always when the
+// caller asks for the strict path, rho^2 is recomputed in FP64 exactly as the oracle
+// does.  In the mixed-precision mode the FP32 value decides alone.
 
 __device__ __forceinline__ bool rtol_stop(const RunState* rs, double rtol) {
   if (!(rtol > 0.0) || rs->iter < 1) return false;
@@ -680,82 +1048,156 @@ __device__ __forceinline__ bool rtol_stop(const RunState* rs, double rtol) {
   return r <= rtol;
 }
 
-__device__ __forceinline__ void remove_q(unsigned long long* acc_lo, unsigned long long* acc_hi,
-                                         long long j, double q) {
-  if (!(q < kQLimit)) return;  // never deposited
-  u64 lo, hi;
-  q_split(q, &lo, &hi);
-  if (lo) atomicAdd(acc_lo + j, (u64)(0ull - lo));
-  if (hi) atomicAdd(acc_hi + j, (u64)(0ull - hi));
+__device__ double rho2_exact(const Grid& g, const Tables& tb, const double* __restrict__ Sg,
+                             double a2, double lo, double hi) {
+  Sweep sw;
+  sw.lo = lo;
+  sw.hi = hi;
+  sw.ka = (i64)floor(__dadd_rn(lo, 0.5));
+  sw.kb = (i64)floor(__dadd_rn(hi, 0.5));
+  bool single = (sw.ka == sw.kb);
+  long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
+  long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
+  double acc = 0.0;
+  for (long long k = k0; k <= k1; ++k) {
+    double w = single ? 1.0 : sweep_weight(sw, k);
+    if (w > 0.0) {
+      long long j = k - g.k_lo;
+      double sn = __dadd_rn(tb.S[j], Sg[j]);
+      double psk = __dmul_rn(__dmul_rn(__dmul_rn(g.t5, tb.R[j]), a2), w);
+      acc = __dadd_rn(acc, __ddiv_rn(psk, sn));
+    }
+  }
+  return __dmul_rn(4.0, acc);
 }
 
 __global__ void __launch_bounds__(256) k_snr_resolve(
-    const Cand* __restrict__ cand, Grid g, const double* __restrict__ S,
-    const double* __restrict__ R, const double* __restrict__ gq, const double* __restrict__ Sg,
-    double th2, double rtol, unsigned char* __restrict__ cres, unsigned char* __restrict__ resolved,
-    unsigned long long* __restrict__ acc_lo, unsigned long long* __restrict__ acc_hi,
-    RunState* rs) {
+    Cands cd, Grid g, Tables tb, const double* __restrict__ Sg, const float* __restrict__ inv_f,
+    double th2, double rtol, int mode, unsigned char* __restrict__ resolved,
+    unsigned long long* __restrict__ acc, RunState* rs, Dirty d, int Kc, int sg_radius) {
   if (rs->final_pass || rtol_stop(rs, rtol)) return;
-  const long long ncand = (long long)rs->ncand;
+  const long long nlive = (long long)rs->nlive;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  unsigned local_new = 0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncand; c += stride) {
-    if (cres[c]) continue;
-    Cand cd = cand[c];
-    Sweep sw;
-    sw.lo = cd.lo;
-    sw.hi = cd.hi;
-    sw.ka = (i64)floor(__dadd_rn(sw.lo, 0.5));
-    sw.kb = (i64)floor(__dadd_rn(sw.hi, 0.5));
-    double acc = 0.0;
-    long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
-    long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
-    bool single = (sw.ka == sw.kb);
-    for (long long k = k0; k <= k1; ++k) {
-      double w = single ? 1.0 : sweep_weight(sw, k);
-      if (w > 0.0) {
-        long long j = k - g.k_lo;
-        double sn = __dadd_rn(S[j], Sg[j]);
-        double psk = __dmul_rn(__dmul_rn(__dmul_rn(g.t5, R[j]), cd.a2), w);
-        acc = __dadd_rn(acc, __ddiv_rn(psk, sn));
+  const float th2f = (float)th2;
+  unsigned local_new = 0, local_exact = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nlive; c += stride) {
+    if (cd.res[c]) continue;
+    const int ka = cd.ka[c];
+    const int nbin = cd.nbin[c];
+    {
+      // S_n unchanged on every bin of the sweep: rho is the value already found below rho_th
+      long long c0 = ka < 0 ? 0 : ka / Kc;
+      long long kl = (long long)ka + nbin - 1;
+      if (kl > g.nb - 1) kl = g.nb - 1;
+      if (kl < 0) continue;
+      long long c1 = kl / Kc;
+      bool changed = false;
+      for (long long cc = c0; cc <= c1 && !changed; ++cc) changed = d.any(cc, sg_radius);
+      if (!changed) continue;
+    }
+    const float a2f = cd.a2f[c];
+    float r2 = 0.0f;
+    int kcount = 0;
+    if (nbin == 1) {
+      if (ka >= 0 && ka < g.nb) {
+        r2 = __fmul_rn(__fmul_rn(a2f, tb.Gf[ka]), inv_f[ka]);
+        kcount = 1;
+      }
+    } else {
+      const float flo = cd.flo[c], fhi = __fadd_rn(flo, cd.len[c]), invlen = 1.0f / cd.len[c];
+      int t0 = ka < 0 ? -ka : 0;
+      int t1 = (long long)ka + nbin > g.nb ? (int)(g.nb - ka) : nbin;
+      for (int t = t0; t < t1; ++t) {
+        float a = fmaxf(flo, (float)t - 0.5f);
+        float b = fminf(fhi, (float)t + 0.5f);
+        if (b > a) {
+          float w = __fmul_rn(__fsub_rn(b, a), invlen);
+          int k = ka + t;
+          r2 = __fadd_rn(r2, __fmul_rn(__fmul_rn(__fmul_rn(a2f, w), tb.Gf[k]), inv_f[k]));
+          ++kcount;
+        }
       }
     }
-    double rho2 = __dmul_rn(4.0, acc);
-    if (rho2 > th2) {
-      cres[c] = 1;
-      resolved[cd.src] = 1;
+    bool resolve;
+    if (mode == 1) {
+      resolve = r2 > th2f;
+    } else {
+      float m = 1e-5f + 4e-7f * (float)kcount;
+      if (mode == 0 && r2 > th2f * (1.0f + m)) {
+        resolve = true;
+      } else if (mode == 0 && r2 < th2f * (1.0f - m)) {
+        resolve = false;
+      } else {
+        ++local_exact;
+        resolve = rho2_exact(g, tb, Sg, cd.a2[c], cd.lo[c], cd.hi[c]) > th2;
+      }
+    }
+    if (resolve) {
+      cd.res[c] = 1;
+      resolved[cd.src[c]] = 1;
       ++local_new;
-      for (long long k = k0; k <= k1; ++k) {
-        double w = single ? 1.0 : sweep_weight(sw, k);
-        if (w > 0.0) {
-          long long j = k - g.k_lo;
-          double q = single ? __dmul_rn(cd.a2, gq[j]) : __dmul_rn(__dmul_rn(cd.a2, w), gq[j]);
-          remove_q(acc_lo, acc_hi, j, q);
+      // remove exactly the parts the prepass deposited
+      Sweep sw;
+      sw.lo = cd.lo[c];
+      sw.hi = cd.hi[c];
+      sw.ka = (i64)floor(__dadd_rn(sw.lo, 0.5));
+      sw.kb = (i64)floor(__dadd_rn(sw.hi, 0.5));
+      double a2 = cd.a2[c];
+      if (sw.ka == sw.kb) {
+        long long j = sw.ka - g.k_lo;
+        if (j >= 0 && j < g.nb) {
+          remove_q(acc, j, __dmul_rn(a2, tb.gq[j]));
+          d.mark_next(j / Kc);
+        }
+      } else {
+        long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
+        long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
+        for (long long k = k0; k <= k1; ++k) {
+          double w = sweep_weight(sw, k);
+          if (w > 0.0) {
+            long long j = k - g.k_lo;
+            remove_q(acc, j, __dmul_rn(__dmul_rn(a2, w), tb.gq[j]));
+            d.mark_next(j / Kc);
+          }
         }
       }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) local_new += __shfl_xor_sync(0xFFFFFFFFu, local_new, o);
-  if ((threadIdx.x & 31) == 0 && local_new) atomicAdd(&rs->count_new, (unsigned long long)local_new);
+  for (int o = 16; o > 0; o >>= 1) {
+    local_new += __shfl_xor_sync(0xFFFFFFFFu, local_new, o);
+    local_exact += __shfl_xor_sync(0xFFFFFFFFu, local_exact, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (local_new) atomicAdd(&rs->count_new, (unsigned long long)local_new);
+    if (local_exact) atomicAdd(&rs->nexact, (unsigned long long)local_exact);
+  }
 }
 
-void launch_snr_resolve(const Cand* cand, long long ncand_cap, const Grid& g, const double* S,
-                        const double* R, const double* gq, const double* Sg, double th2,
-                        double rtol, unsigned char* cres, unsigned char* resolved,
-                        unsigned long long* acc_lo, unsigned long long* acc_hi, RunState* rs,
-                        int nsm, cudaStream_t st) {
+void launch_snr_resolve(Cands cd, long long ncap, const Grid& g, const Tables& tb,
+                        const double* Sg, const float* inv_f, double th2, double rtol, int mode,
+                        unsigned char* resolved, unsigned long long* acc, RunState* rs,
+                        Dirty d, int Kc, int sg_radius, int nsm, cudaStream_t st) {
   int th = 256;
-  long long want = (ncand_cap + th - 1) / th;
+  long long want = (ncap + th - 1) / th;
   long long cap = (long long)nsm * 8;
   int bl = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
-  k_snr_resolve<<<bl, th, 0, st>>>(cand, g, S, R, gq, Sg, th2, rtol, cres, resolved, acc_lo, acc_hi,
-                                   rs);
+  k_snr_resolve<<<bl, th, 0, st>>>(cd, g, tb, Sg, inv_f, th2, rtol, mode, resolved, acc, rs, d, Kc,
+                                   sg_radius);
 }
 
 // ============================================================================ loop control
 
 __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist,
-                          unsigned long long cond_handle, int use_cond) {
+                          unsigned long long cond_handle, int use_cond, unsigned char* dirty,
+                          int nch) {
+  // every thread clears part of the dirty set this iteration read (rs->iter still holds
+  // the previous count); the new set was marked by this iteration's removals
+  if (dirty) {
+    unsigned char* cur = dirty + (size_t)(rs->iter & 1) * nch;
+    for (int i = threadIdx.x; i < nch; i += blockDim.x) cur[i] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   unsigned go = 1u;
   if (rs->final_pass) {
     go = 0u;
@@ -775,21 +1217,21 @@ __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist
     }
   }
   rs->count_new = 0ull;
-  rs->max_p_bits = 0ull;
-  rs->max_m_bits = 0ull;
   rs->relchg_bits = 0ull;
   if (!go) rs->stopped = 1;
   if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, go);
 }
 
 void launch_control(RunState* rs, int max_iter, double rtol, int* new_hist,
-                    unsigned long long cond_handle, int use_cond, cudaStream_t st) {
-  k_control<<<1, 1, 0, st>>>(rs, max_iter, rtol, new_hist, cond_handle, use_cond);
+                    unsigned long long cond_handle, int use_cond, unsigned char* dirty, int nch,
+                    cudaStream_t st) {
+  k_control<<<1, 256, 0, st>>>(rs, max_iter, rtol, new_hist, cond_handle, use_cond, dirty, nch);
 }
 
 void configure_kernels() {
   cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   cudaFuncSetAttribute(k_median_slide, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(k_median_slide_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
 }
 
 }  // namespace gbsub

@@ -6,11 +6,18 @@
 
 namespace gbsub {
 
-// One candidate source: everything the SNR step needs, 32 bytes (two 16-byte loads).
-struct Cand {
-  long long src;  // index in the catalog
-  double a2;      // A^2
-  double lo, hi;  // sweep endpoints in bin units (sorted)
+// Candidates that can still be resolved (rho_0 > rho_th), structure of arrays.
+struct Cands {
+  long long* src;     // index in the catalog
+  int* ka;            // first bin of the sweep, relative to k_lo (may be < 0)
+  int* nbin;          // bins touched by the sweep (kb - ka + 1)
+  float* a2f;         // A^2 * 2^160 (FP32 screen)
+  float* flo;         // lo - ka (FP32 screen)
+  float* len;         // hi - lo (FP32 screen)
+  double* a2;         // A^2 (exact path)
+  double* lo;         // sweep endpoints in bin units (exact path)
+  double* hi;
+  unsigned char* res; // 1 once resolved
 };
 
 // Loop state kept on the device for one run.
@@ -19,11 +26,12 @@ struct RunState {
   int final_pass;        // 1: max_iter reached, one more estimate of S_gal without SNR
   int converged;         // 1: stopped because nothing crossed rho_th (or rtol met)
   int stopped;           // 1: the loop is over
-  unsigned long long ncand;
+  unsigned long long ncand;     // sources with rho_0 >= kappa rho_th (paper's candidates)
+  unsigned long long nlive;     // candidates kept (rho_0 > rho_th, and >= kappa rho_th)
   unsigned long long nres;
   unsigned long long count_new;
-  unsigned long long max_p_bits;    // max of the estimator input, as bits of a double >= 0
-  unsigned long long max_m_bits;    // max of the median output (median-then-mean)
+  unsigned long long nexact;    // SNR decisions that needed the exact FP64 recomputation
+  unsigned long long max_p_bits;    // scratch maximum (estimate on a given spectrum)
   unsigned long long relchg_bits;   // max relative change of S_n (conv_rtol)
   unsigned err;
   unsigned pad;
@@ -34,6 +42,18 @@ struct Grid {
   double T, T2, t5;      // T_obs, T_obs^2, T_obs / 5
   long long k_lo;        // first DFT index in band
   long long nb;          // bins in band
+  unsigned long long mT; // T_obs = mT 2^eT, mT the 53-bit integer mantissa
+  int eT;
+  float T2f;             // T_obs^2 in FP32
+};
+
+// Per-bin tables, built once per context.
+struct Tables {
+  const double* S;       // S_instr
+  const double* R;       // R
+  const double* gq;      // 2^96 (T/5) R / S: fixed-point units per unit of A^2 w
+  const float* Gf;       // 4 (T/5) R / S * 2^-160: rho_0^2 per unit of A^2 w * 2^160
+  const float* invSf;    // 1 / (S * 2^150)
 };
 
 struct SmoothPlan {
@@ -47,53 +67,97 @@ struct SmoothPlan {
   int slide_threads;
 };
 
+// Source of an estimator's input: the run's fixed-point spectrum (P_k = S_k Q_k 2^-96) or
+// a plain array of doubles.
+struct SpecIn {
+  const unsigned long long* acc;  // 4 words per bin (three used), or null
+  const double* S;                // S_instr when acc is set
+  const double* x;                // input doubles when acc is null
+};
+
+// Chunks whose input changed since the previous iteration.  Two byte arrays of nch
+// entries alternate: iteration i reads set (i-1) & 1 and the removals of iteration i mark
+// set i & 1 (rs->iter = i - 1 while iteration i runs).  A null base means every chunk
+// has changed (first estimate, or an estimate of a given spectrum).
+struct Dirty {
+  unsigned char* base;
+  int nch;
+  const RunState* rs;
+  __device__ __forceinline__ bool any(long long c, int radius) const {
+    if (!base) return true;
+    const unsigned char* cur = base + (size_t)(rs->iter & 1) * nch;
+    long long a = c - radius, b = c + radius;
+    if (a < 0) a = 0;
+    if (b > nch - 1) b = nch - 1;
+    for (long long i = a; i <= b; ++i)
+      if (cur[i]) return true;
+    return false;
+  }
+  __device__ __forceinline__ void mark_next(long long c) const {
+    if (base) base[(size_t)((rs->iter + 1) & 1) * nch + c] = 1;
+  }
+};
+
+// Output epilogue of the kernel that writes S_gal.
+struct SgOut {
+  double* out;           // S_gal (or the median of median-then-mean)
+  float* inv_f;          // 1 / (1 + S_gal / S_instr) in FP32, or null
+  const double* S;       // S_instr (for inv_f and the rtol test)
+  const float* invSf;
+  int rtol_on;
+  RunState* rs;
+};
+
 // Raise the dynamic shared-memory limits of the kernels that need more than 48 KB.
 void configure_kernels();
 
-void launch_tables(const Grid& g, int tdi2, double* S, double* R, double* gq, cudaStream_t st);
+void launch_tables(const Grid& g, int tdi2, double* S, double* R, double* gq, float* Gf,
+                   float* invSf, cudaStream_t st);
 
 void launch_prepass(const double* A, const double* f, const double* fdot, long long N,
-                    const Grid& g, const double* gq, double thr_q, unsigned long long* acc_lo,
-                    unsigned long long* acc_hi, Cand* cand, RunState* rs, int nsm,
-                    cudaStream_t st);
+                    const Grid& g, const Tables& tb, double thr_kappa, double thr_live,
+                    unsigned long long* acc, Cands cd, RunState* rs, int nsm, cudaStream_t st);
 
-void launch_q2p(const unsigned long long* acc_lo, const unsigned long long* acc_hi,
-                const double* S, long long nb, double* P, RunState* rs, int final_only,
-                cudaStream_t st);
+// P[j] = S_j Q_j 2^-96 for every bin.
+void launch_power_out(const unsigned long long* acc, const double* S, long long n, double* P,
+                      cudaStream_t st);
 
 // *max_bits = max(*max_bits, bits of max x) over x[0 .. n) (x >= 0).
 void launch_max_bits(const double* x, long long n, unsigned long long* max_bits, cudaStream_t st);
 
-void launch_chunk_sort(const double* x, long long n, const SmoothPlan& pl, unsigned long long* skey,
-                       uint16_t* srank, uint32_t* snap, const RunState* rs, cudaStream_t st);
+// Sort every chunk of the input whose values changed (keys, ranks, active-set snapshots).
+void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
+                       uint16_t* srank, uint32_t* snap, Dirty d, cudaStream_t st);
 
-// out = C * running median of x.  max_bits_out (may be null) receives the max of out.
-// When rtol_on, relative change of S_instr + out against its previous content is
-// folded into rs->relchg_bits before out is overwritten.
+// out = C * running median, recomputed in the output chunks whose windows changed.
 void launch_median_slide(const unsigned long long* skey, const uint16_t* srank,
-                         const uint32_t* snap, long long n, const SmoothPlan& pl, double* out,
-                         unsigned long long* max_bits_out, const double* S, int rtol_on,
-                         RunState* rs, cudaStream_t st);
+                         const uint32_t* snap, long long n, const SmoothPlan& pl, SgOut o,
+                         Dirty d, cudaStream_t st);
 
-// Exact 128-bit prefix sums of x inside each chunk; uflow[b] = 1 when an input > 0 of
-// chunk b is below one fixed-point unit.
-void launch_chunk_prefix(const double* x, long long n, const SmoothPlan& pl,
-                         const unsigned long long* max_bits, unsigned long long* pre_lo,
-                         unsigned long long* pre_hi, unsigned* uflow, const RunState* rs,
-                         cudaStream_t st);
+// Exact 128-bit prefix sums of the input inside each chunk at a per-chunk scale sig[b];
+// uflow[b] = 1 when an input > 0 of chunk b is below one unit.  x_out (may be null)
+// receives the input values.
+// (in_radius: the input of chunk b changed when a chunk within in_radius of b is dirty.)
+void launch_chunk_prefix(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* pre_lo,
+                         unsigned long long* pre_hi, int* sig, unsigned* uflow, double* x_out,
+                         Dirty d, int in_radius, cudaStream_t st);
 
 void launch_window_mean(const double* x, long long n, const SmoothPlan& pl,
-                        const unsigned long long* max_bits, const unsigned long long* pre_lo,
-                        const unsigned long long* pre_hi, const unsigned* uflow, double* out,
-                        const double* S, int rtol_on, RunState* rs, cudaStream_t st);
+                        const unsigned long long* pre_lo, const unsigned long long* pre_hi,
+                        const int* sig, const unsigned* uflow, SgOut o, Dirty d, int out_radius,
+                        cudaStream_t st);
 
-void launch_snr_resolve(const Cand* cand, long long ncand_cap, const Grid& g, const double* S,
-                        const double* R, const double* gq, const double* Sg, double th2,
-                        double rtol, unsigned char* cres, unsigned char* resolved,
-                        unsigned long long* acc_lo, unsigned long long* acc_hi, RunState* rs,
-                        int nsm, cudaStream_t st);
+// sg_radius: S_gal of chunk c changed when a chunk within sg_radius of c is dirty; only
+// candidates with a bin in such a chunk are tested again.
+void launch_snr_resolve(Cands cd, long long ncap, const Grid& g, const Tables& tb,
+                        const double* Sg, const float* inv_f, double th2, double rtol, int mixed,
+                        unsigned char* resolved, unsigned long long* acc, RunState* rs,
+                        Dirty d, int Kc, int sg_radius, int nsm, cudaStream_t st);
+
+// Loop control; it also clears the dirty set the finished iteration read.
 
 void launch_control(RunState* rs, int max_iter, double rtol, int* new_hist,
-                    unsigned long long cond_handle, int use_cond, cudaStream_t st);
+                    unsigned long long cond_handle, int use_cond, unsigned char* dirty, int nch,
+                    cudaStream_t st);
 
 }  // namespace gbsub

@@ -12,9 +12,8 @@
 // it (about 21 MB) until the process exits.  Every call shares it and it keeps the
 // last call's contents, so calls whose work overlaps on the GPU (different streams,
 // or different host threads) race with each other and must be serialised by the
-// caller.  The window maximum that fixes the fixed-point scale is cleared at the
-// start of every call; the prefix sums and underflow flags are fully rewritten for
-// the bins a call uses.
+// caller.  Nothing in it has to start at zero: every call rewrites the prefix sums,
+// the per-chunk scales and the underflow flags of all the bins and chunks it reads.
 
 #include <cstdio>
 #include <mutex>
@@ -38,8 +37,9 @@ constexpr long long kNoAllocMaxWindow = SUB_NOALLOC_MAX_WINDOW;
 // chunk cells: at most one chunk beyond the bins, chunks of >= 32 and <= max window
 constexpr long long kCells = kNoAllocMaxBins + kNoAllocMaxWindow + 32;
 constexpr long long kChunks = kNoAllocMaxBins / 32 + 2;
-// layout in 8-byte words: pre_lo[kCells] | pre_hi[kCells] | uflow (u32)[kChunks] | max bits
-constexpr long long kWords = 2 * kCells + (kChunks + 1) / 2 + 1;
+// layout in 8-byte words: pre_lo[kCells] | pre_hi[kCells] | scale (i32)[kChunks] |
+// underflow flag (u32)[kChunks]
+constexpr long long kWords = 2 * kCells + kChunks;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kWords];
 
@@ -106,16 +106,27 @@ extern "C" int sub_running_mean_noalloc(const double* x, double* out, int64_t n,
   pl.slide_threads = 0;
   unsigned long long* pre_lo = base;
   unsigned long long* pre_hi = base + kCells;
-  unsigned* uflow = (unsigned*)(base + 2 * kCells);
-  unsigned long long* max_bits = base + kWords - 1;
+  int* sig = (int*)(base + 2 * kCells);
+  unsigned* uflow = (unsigned*)(sig + kChunks);
   cudaStream_t st = (cudaStream_t)stream;
-  e = cudaMemsetAsync(max_bits, 0, sizeof(unsigned long long), st);
-  if (e == cudaSuccess) {
-    launch_max_bits(x, n, max_bits, st);
-    launch_chunk_prefix(x, n, pl, max_bits, pre_lo, pre_hi, uflow, nullptr, st);
-    launch_window_mean(x, n, pl, max_bits, pre_lo, pre_hi, uflow, out, nullptr, 0, nullptr, st);
-    e = cudaGetLastError();
-  }
+  SpecIn in;
+  in.acc = nullptr;
+  in.S = nullptr;
+  in.x = x;
+  SgOut o;
+  o.out = out;
+  o.inv_f = nullptr;
+  o.S = nullptr;
+  o.invSf = nullptr;
+  o.rtol_on = 0;
+  o.rs = nullptr;
+  Dirty all;  // every chunk is computed
+  all.base = nullptr;
+  all.nch = pl.nch;
+  all.rs = nullptr;
+  launch_chunk_prefix(in, n, pl, pre_lo, pre_hi, sig, uflow, nullptr, all, 0, st);
+  launch_window_mean(x, n, pl, pre_lo, pre_hi, sig, uflow, o, all, 0, st);
+  e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(msg, sizeof(msg), "sub_running_mean_noalloc: launch failed: %s",
              cudaGetErrorString(e));

@@ -20,7 +20,7 @@ from . import build as _build
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ETIMEOUT, EBUDGET, ERANGE, ESTATE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
 MEAN, MEDIAN, MEDIAN_MEAN = 0, 1, 2
-FP64, MIXED = 0, 1
+FP64, MIXED, FP64_STRICT = 0, 1, 2
 HOST, DEVICE = 0, 1
 YEAR = 365.25 * 86400.0
 
@@ -52,6 +52,7 @@ class sub_stats(ctypes.Structure):
         ("n_sources", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
         ("n_resolved", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("k_lo", ctypes.c_int64),
         ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("n_live", ctypes.c_int64), ("n_exact", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -63,8 +64,8 @@ _lock = threading.Lock()
 EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_run", "sub_get_stats",
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
            "sub_get_tables", "sub_get_timing", "sub_profile", "sub_device_bytes", "sub_destroy",
-           "sub_last_error", "sub_running_mean_noalloc")
-KERNELS = ("prepass", "q2p", "sort", "slide", "prefix", "mean", "snr", "control")
+           "sub_last_error", "sub_running_mean_noalloc", "sub_get_power")
+KERNELS = ("prepass", "sort", "slide", "prefix", "mean", "snr", "control")
 
 
 def library_path() -> str:
@@ -95,6 +96,7 @@ def lib(build_if_missing: bool = True):
             "sub_get_resolved_mask": (i32, [P, P, i64, i32]),
             "sub_estimate": (i32, [P, P, P, i64, i32]),
             "sub_get_tables": (i32, [P, P, P, i64, i32]),
+            "sub_get_power": (i32, [P, P, i64, i32]),
             "sub_get_timing": (i32, [P, P, P, P]),
             "sub_profile": (i32, [P, P, P, ctypes.POINTER(sub_stats)]),
             "sub_device_bytes": (i64, [P]),
@@ -225,6 +227,15 @@ def sub_estimate(ctx, P, out=None):
     return out
 
 
+def sub_get_power(ctx, out=None):
+    nb, _ = n_bins_of(ctx)
+    if out is None:
+        out = np.empty(nb)
+    p, w, n = _ptr(out, np.float64)
+    _check(ctx, lib().sub_get_power(ctx, p, n, w))
+    return out
+
+
 def sub_get_tables(ctx):
     nb, _ = n_bins_of(ctx)
     S = np.empty(nb)
@@ -289,6 +300,9 @@ class Subtraction:
 
     def tables(self):
         return sub_get_tables(self.ctx)
+
+    def power(self, out=None):
+        return sub_get_power(self.ctx, out)
 
     def timing(self):
         return sub_get_timing(self.ctx)

@@ -3,7 +3,11 @@
 Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
 written from its published definition.  Every number a catalog needs is a pure
 function of (seed, source index, stream), so any slice of a catalog can be
-regenerated independently and the same catalog is produced on any machine.
+regenerated independently.  The same catalog is produced bit for bit on any
+machine: the elementary functions used below (log, exp, pow) are written here
+with IEEE basic operations only (+, -, *, /, sqrt, exact scalings), so they do not
+depend on the platform's math library, and normal deviates come from Marsaglia's
+polar method (no trigonometric function).
 
 Distributions (the synthetic stand-in for the paper's population catalogs):
   f     : truncated power law p(f) ~ f^-gamma on [1e-4, 1e-2] Hz, by inverse CDF
@@ -65,20 +69,62 @@ def u32(a):
 # Stream identifiers (third counter word).
 _STREAM_FM = 0          # f and chirp mass
 _STREAM_GAMMA = 1       # Gamma attempts use streams 1..16
-_MAX_GAMMA_TRIES = 16
+_MAX_GAMMA_TRIES = 24
 _STREAM_POP = 0xFFFFFFF0  # per-catalog population parameters
+
+
+# ------------------------------------------------------------------ portable elementary functions
+# Natural log: x = m 2^e with m in [sqrt(1/2), sqrt(2)), log m = 2 atanh((m-1)/(m+1)) by its
+# series; exp: x = k ln2 + r with |r| <= ln2/2, exp r by its Taylor series, then scaled by 2^k.
+# ln 2 is split in a part with a short mantissa (exact products with k) and a correction.
+_LN2_HI = 6.93147180369123816490e-01
+_LN2_LO = 1.90821492927058770002e-10
+_SQRT_HALF = 0.70710678118654752440
+
+
+def plog(x):
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)
+    small = m < _SQRT_HALF
+    m = np.where(small, m * 2.0, m)
+    e = (e - small.astype(np.int64)).astype(np.float64)
+    t = (m - 1.0) / (m + 1.0)
+    t2 = t * t
+    acc = np.full(t.shape, 1.0 / 27.0)
+    for k in range(25, 0, -2):
+        acc = acc * t2 + 1.0 / k
+    return e * _LN2_HI + (e * _LN2_LO + 2.0 * t * acc)
+
+
+def pexp(x):
+    x = np.asarray(x, dtype=np.float64)
+    k = np.rint(x / (_LN2_HI + _LN2_LO))
+    r = (x - k * _LN2_HI) - k * _LN2_LO
+    acc = np.full(r.shape, 1.0 / math.factorial(18))
+    for i in range(17, -1, -1):
+        acc = acc * r + 1.0 / math.factorial(i)
+    return np.ldexp(acc, k.astype(np.int64))
+
+
+_LOG_1E3 = float(plog(1e-3))
+
+
+def ppow(x, y):
+    """x^y for x > 0 (y scalar or array)."""
+    return pexp(np.asarray(y, dtype=np.float64) * plog(x))
 
 
 def _power_law_icdf(u, gamma, fmin=F_MIN, fmax=F_MAX):
     if abs(gamma - 1.0) < 1e-12:
-        return fmin * np.exp(u * math.log(fmax / fmin))
+        return fmin * pexp(u * float(plog(fmax / fmin)))
     e = 1.0 - gamma
-    a, b = fmin ** e, fmax ** e
-    return (a + u * (b - a)) ** (1.0 / e)
+    a, b = float(ppow(fmin, e)), float(ppow(fmax, e))
+    return ppow(a + u * (b - a), 1.0 / e)
 
 
 def _gamma(k: float, idx: np.ndarray, k0: int, k1: int):
-    """Gamma(k, 1), k >= 1, by Marsaglia-Tsang with counter-based attempts."""
+    """Gamma(k, 1), k >= 1, by Marsaglia-Tsang with counter-based attempts; the normal
+    deviate of each attempt comes from Marsaglia's polar method."""
     if k < 1.0:
         raise ValueError("shape must be >= 1")
     d = k - 1.0 / 3.0
@@ -91,13 +137,17 @@ def _gamma(k: float, idx: np.ndarray, k0: int, k1: int):
         if todo.size == 0:
             break
         x0, x1, x2, x3 = philox4x32_10(lo[todo], hi[todo], _STREAM_GAMMA + t, 0, k0, k1)
-        u1 = u53(x0, x1)
-        z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u32(x2))
+        p = 2.0 * u32(x0) - 1.0
+        q = 2.0 * u32(x1) - 1.0
+        s2 = p * p + q * q
+        inside = (s2 < 1.0) & (s2 > 0.0)
+        s2 = np.where(inside, s2, 0.5)
+        z = p * np.sqrt(-2.0 * plog(s2) / s2)
         v = 1.0 + c * z
-        ok = v > 0.0
+        ok = inside & (v > 0.0)
         v = np.where(ok, v * v * v, 1.0)
-        ua = u32(x3)
-        acc = ok & (np.log(ua) < 0.5 * z * z + d - d * v + d * np.log(v))
+        ua = u53(x2, x3)
+        acc = ok & (plog(ua) < 0.5 * z * z + d - d * v + d * plog(v))
         out[todo[acc]] = d * v[acc]
         todo = todo[~acc]
     return out
@@ -117,7 +167,7 @@ def catalog(n: int, seed: int, pop: Population | None = None, start: int = 0,
     A = np.empty(n)
     f = np.empty(n)
     fdot = np.empty(n)
-    pref = 96.0 / 5.0 * math.pi ** (8.0 / 3.0)
+    pref = 96.0 / 5.0 * float(ppow(math.pi, 8.0 / 3.0))
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
         idx = np.arange(start + s, start + e, dtype=np.int64)
@@ -127,9 +177,10 @@ def catalog(n: int, seed: int, pop: Population | None = None, start: int = 0,
         fs = _power_law_icdf(u53(x0, x1), pop.gamma)
         mc = (0.2 + 0.6 * u53(x2, x3)) * GMSUN_C3
         X = _gamma(pop.shape, idx, k0, k1)
+        lf = plog(fs)
         f[s:e] = fs
-        fdot[s:e] = pref * mc ** (5.0 / 3.0) * fs ** (11.0 / 3.0)
-        A[s:e] = 1e-23 * X * (fs / 1e-3) ** (2.0 / 3.0)
+        fdot[s:e] = pref * pexp(5.0 / 3.0 * plog(mc) + 11.0 / 3.0 * lf)
+        A[s:e] = 1e-23 * X * pexp(2.0 / 3.0 * (lf - _LOG_1E3))
     return A, f, fdot
 
 
@@ -147,8 +198,8 @@ def job_draw(seed: int, index: int, n_range=(1e5, 3e7), years=(1, 2, 4)):
     x0, x1, x2, x3 = philox4x32_10(index & 0xFFFFFFFF, index >> 32, _STREAM_POP + 1, 0,
                                    seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
     un, ut = float(u53(x0, x1)), float(u32(x2))
-    lo, hi = math.log(n_range[0]), math.log(n_range[1])
-    n = int(round(math.exp(lo + un * (hi - lo))))
+    lo, hi = float(plog(n_range[0])), float(plog(n_range[1]))
+    n = int(round(float(pexp(lo + un * (hi - lo)))))
     T = years[min(len(years) - 1, int(ut * len(years)))] * YEAR
     return n, T, float(u32(x3))
 
