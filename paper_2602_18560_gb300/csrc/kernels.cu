@@ -81,7 +81,8 @@ void launch_tables(const Grid& g, int tdi2, double* S, double* R, double* gq, fl
 
 __device__ __forceinline__ void deposit_q(unsigned long long* acc, long long j, double q,
                                           unsigned* err) {
-  if (!(q < kQLimit)) {
+  // q >= 0: compare the bits with those of 2^127 (no FP64 instruction)
+  if ((u64)__double_as_longlong(q) >= 0x47E0000000000000ull) {
     atomicOr(err, ERR_RANGE);
     return;
   }
@@ -94,7 +95,7 @@ __device__ __forceinline__ void deposit_q(unsigned long long* acc, long long j, 
 }
 
 __device__ __forceinline__ void remove_q(unsigned long long* acc, long long j, double q) {
-  if (!(q < kQLimit)) return;  // never deposited
+  if ((u64)__double_as_longlong(q) >= 0x47E0000000000000ull) return;  // never deposited
   u64 c0, c1, c2;
   q_parts(q, &c0, &c1, &c2);
   u64* a = acc + 4 * j;
@@ -134,6 +135,53 @@ void launch_power_out(const unsigned long long* acc, const double* S, long long 
 
 // ============================================================================ prepass
 
+// FP64 path of the catalog pass: the sweep of one source, its pieces deposited; returns
+// the sum of its contributions.  Kept out of line so that none of it is speculated into
+// the common path.
+__device__ __noinline__ double prepass_slow(double a2, double fs, double fds, const Grid g,
+                                            const Tables tb, unsigned long long* acc,
+                                            unsigned* err) {
+  Sweep sw = make_sweep(fs, fds, g.T, g.T2);
+  double r = 0.0;
+  if (sw.ka == sw.kb) {
+    long long j = sw.ka - g.k_lo;
+    if (j >= 0 && j < g.nb) {
+      double q = __dmul_rn(a2, tb.gq[j]);
+      deposit_q(acc, j, q, err);
+      r = q;
+    }
+  } else {
+    long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
+    long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
+    for (long long k = k0; k <= k1; ++k) {
+      double w = sweep_weight(sw, k);
+      if (w > 0.0) {
+        long long j = k - g.k_lo;
+        double q = __dmul_rn(__dmul_rn(a2, w), tb.gq[j]);
+        deposit_q(acc, j, q, err);
+        r = __dadd_rn(r, q);
+      }
+    }
+  }
+  return r;
+}
+
+// Record of a kept candidate (rare; out of line).
+__device__ __noinline__ void emit_candidate(Cands cd, long long c, long long s, double a2,
+                                            double fs, double fds, const Grid g) {
+  Sweep sw = make_sweep(fs, fds, g.T, g.T2);
+  cd.src[c] = s;
+  cd.ka[c] = (int)(sw.ka - g.k_lo);
+  cd.nbin[c] = (int)(sw.kb - sw.ka + 1);
+  cd.a2f[c] = dbl_to_f32_scaled(a2, 160);
+  cd.flo[c] = (float)(sw.lo - (double)sw.ka);
+  cd.len[c] = (float)(sw.hi - sw.lo);
+  cd.a2[c] = a2;
+  cd.lo[c] = sw.lo;
+  cd.hi[c] = sw.hi;
+  cd.res[c] = 0;
+}
+
 __global__ void __launch_bounds__(256) k_prepass(
     const double* __restrict__ A, const double* __restrict__ f, const double* __restrict__ fdot,
     long long N, Grid g, Tables tb, double thr_kappa, double thr_live,
@@ -148,15 +196,12 @@ __global__ void __launch_bounds__(256) k_prepass(
   for (long long base = warp0; base < N; base += stride) {
     long long s = base + lane;
     bool live = false;
-    double a2 = 0.0;
-    Sweep sw;
-    sw.lo = sw.hi = 0.0;
-    sw.ka = sw.kb = 0;
+    double a2 = 0.0, fs = 0.0, fds = 0.0;
     if (s < N) {
       double a = A[s];
-      double fs = f[s], fds = fdot[s];
+      fs = f[s];
+      fds = fdot[s];
       a2 = __dmul_rn(a, a);
-      double r = 0.0;  // sum of q: rho_0^2 = 4 r 2^-96
       // Common case without FP64: bin of f T + 1/2 exactly, and an FP32 bound on the sweep
       // fdot T^2 proving that f T + fdot T^2 + 1/2 stays in the same bin (the FP64 path
       // takes every case the bound cannot settle).
@@ -171,8 +216,8 @@ __global__ void __launch_bounds__(256) k_prepass(
         float x = __fadd_rn(phi, du);
         single = (x >= m) && (x < __fsub_rn(1.0f, m));
       }
+      double r = 0.0;  // sum of q: rho_0^2 = 4 r 2^-96
       if (single) {
-        sw.ka = sw.kb = k0;
         long long j = k0 - g.k_lo;
         if (j >= 0 && j < g.nb) {
           double q = __dmul_rn(a2, tb.gq[j]);
@@ -180,32 +225,11 @@ __global__ void __launch_bounds__(256) k_prepass(
           r = q;
         }
       } else {
-        sw = make_sweep(fs, fds, g.T, g.T2);
-        if (sw.ka == sw.kb) {
-          long long j = sw.ka - g.k_lo;
-          if (j >= 0 && j < g.nb) {
-            double q = __dmul_rn(a2, tb.gq[j]);
-            deposit_q(acc, j, q, &rs->err);
-            r = q;
-          }
-        } else {
-          long long k0b = sw.ka > g.k_lo ? sw.ka : g.k_lo;
-          long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
-          for (long long k = k0b; k <= k1; ++k) {
-            double w = sweep_weight(sw, k);
-            if (w > 0.0) {
-              long long j = k - g.k_lo;
-              double q = __dmul_rn(__dmul_rn(a2, w), tb.gq[j]);
-              deposit_q(acc, j, q, &rs->err);
-              r = __dadd_rn(r, q);
-            }
-          }
-        }
+        r = prepass_slow(a2, fs, fds, g, tb, acc, &rs->err);
       }
       u64 rb = (u64)__double_as_longlong(r);
       if (rb >= tk_bits) ++nkappa;
       live = (rb > tl_bits) && (rb >= tk_bits);
-      if (live && single) sw = make_sweep(fs, fds, g.T, g.T2);  // endpoints for the record
     }
     unsigned m = __ballot_sync(0xFFFFFFFFu, live);
     if (m) {
@@ -215,16 +239,7 @@ __global__ void __launch_bounds__(256) k_prepass(
       b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
       if (live) {
         long long c = (long long)b0 + __popc(m & ((1u << lane) - 1u));
-        cd.src[c] = s;
-        cd.ka[c] = (int)(sw.ka - g.k_lo);
-        cd.nbin[c] = (int)(sw.kb - sw.ka + 1);
-        cd.a2f[c] = dbl_to_f32_scaled(a2, 160);
-        cd.flo[c] = (float)(sw.lo - (double)sw.ka);
-        cd.len[c] = (float)(sw.hi - sw.lo);
-        cd.a2[c] = a2;
-        cd.lo[c] = sw.lo;
-        cd.hi[c] = sw.hi;
-        cd.res[c] = 0;
+        emit_candidate(cd, c, s, a2, fs, fds, g);
       }
     }
   }
@@ -616,6 +631,7 @@ __global__ void __launch_bounds__(256) k_median_slide_smem(
   u64* sk = (u64*)sm_raw;                                   // [3][Kc]
   uint16_t* sr = (uint16_t*)(sk + 3 * (size_t)Kc);          // [3][Kc]
   uint32_t* sb = (uint32_t*)(sr + 3 * (size_t)Kc);          // [2][nw][T]
+  uint16_t* sp = (uint16_t*)(sb + 2 * (size_t)nw * T);      // [2][nw + 1][T] word prefixes
   const long long c0 = c - 1;  // chunk held in slot 0
   for (int slot = 0; slot < 3; ++slot) {
     long long ch = c0 + slot;
@@ -686,6 +702,27 @@ __global__ void __launch_bounds__(256) k_median_slide_smem(
     }
     int cnt = (int)(e_cur - s_cur + 1);
     int kq = cnt / 2 + 1;
+    // word prefixes of the active counts (valid until the first slide step), so that the
+    // count of active elements below a sorted index is one lookup and one popcount
+    uint16_t* pA = sp + tid;
+    uint16_t* pB = sp + (size_t)(nw + 1) * T + tid;
+    {
+      int ra = 0, rb = 0;
+      for (int w = 0; w < nw; ++w) {
+        pA[w * T] = (uint16_t)ra;
+        pB[w * T] = (uint16_t)rb;
+        ra += __popc(A.bs[w * T]);
+        rb += __popc(B.bs[w * T]);
+      }
+      pA[nw * T] = (uint16_t)ra;
+      pB[nw * T] = (uint16_t)rb;
+    }
+    auto cnt_below = [&](const uint32_t* bs, const uint16_t* pf, int x) {
+      int w = x >> 5;
+      int r = pf[w * T];
+      if (x & 31) r += __popc(bs[w * T] & ((1u << (x & 31)) - 1u));
+      return r;
+    };
     // initial cut: smallest merged position with kq active elements before it
     int lo = kq, hi = A.len + B.len;
     while (lo < hi) {
@@ -697,7 +734,7 @@ __global__ void __launch_bounds__(256) k_median_slide_smem(
         bool ok = (y >= B.len) || (A.key[x - 1] <= B.key[y]);
         if (ok) lo2 = x; else hi2 = x - 1;
       }
-      int k2 = popc_prefix(A.bs, T, lo2) + popc_prefix(B.bs, T, P - lo2);
+      int k2 = cnt_below(A.bs, pA, lo2) + cnt_below(B.bs, pB, P - lo2);
       if (k2 >= kq) hi = P; else lo = P + 1;
     }
     int cA, cB;
@@ -824,15 +861,17 @@ __global__ void __launch_bounds__(256) k_median_slide_smem(
   if (o.rtol_on) warp_max_atomic((u64)__double_as_longlong(relmax), &o.rs->relchg_bits);
 }
 
-// Threads per chunk for the shared-memory slide, and whether its staging fits.
+// Threads per chunk for the shared-memory slide (each takes Kc / T consecutive outputs:
+// short chains of dependent steps), and its shared-memory size.
 static int smem_slide_threads(const SmoothPlan& pl) {
-  int t = pl.Kc / 16;
+  int t = pl.Kc / 8;
   if (t < 32) t = 32;
   if (t > 128) t = 128;
   return t;
 }
 static size_t smem_slide_bytes(const SmoothPlan& pl, int T) {
-  return (size_t)3 * pl.Kc * (sizeof(u64) + sizeof(uint16_t)) + (size_t)2 * pl.nw * T * 4;
+  return (size_t)3 * pl.Kc * (sizeof(u64) + sizeof(uint16_t)) + (size_t)2 * pl.nw * T * 4 +
+         (size_t)2 * (pl.nw + 1) * T * 2;
 }
 
 void launch_median_slide(const unsigned long long* skey, const uint16_t* srank,
