@@ -132,15 +132,14 @@ def kernels_per_iteration(est):
     return {0: 4, 1: 4, 2: 6}[est]
 
 
-def algorithmic_bytes(kernel, N, nb, nlive, est, plan_chunks, kc, nsnap):
+def algorithmic_bytes(kernel, N, nb, nlive, est):
     """Bytes a kernel must move per launch: reads of its inputs plus writes of its outputs."""
-    snap = plan_chunks * nsnap * (kc // 32) * 4
     if kernel == "prepass":   # catalog, cleared spectrum (4 words/bin), kept candidates
         return 24 * N + 32 * nb + 53 * nlive
-    if kernel == "sort":      # spectrum words + S_instr -> keys, ranks, snapshots
-        return 32 * nb + 8 * nb + 2 * nb + snap
-    if kernel == "slide":     # keys, ranks, snapshots -> median (+ inv_f when it is S_gal)
-        return 10 * nb + snap + 8 * nb + (4 * nb if est == 1 else 0)
+    if kernel == "sort":      # spectrum words + S_instr -> sorted keys, ranks
+        return 32 * nb + 8 * nb + 8 * nb + 2 * nb
+    if kernel == "median":    # sorted keys, ranks -> median (+ inv_f when it is S_gal)
+        return 10 * nb + 8 * nb + (4 * nb if est == 1 else 0)
     if kernel == "prefix":    # input (spectrum words + S, or the median) -> prefix sums
         return (40 * nb + 8 * nb if est == 0 else 8 * nb) + 16 * nb
     if kernel == "mean":      # two prefix sums per output -> S_gal + inv_f
@@ -293,18 +292,15 @@ def main():
     kernels = {k: {"ms_per_run": v[0] / prof_runs, "launches_per_run": v[1] / prof_runs}
                for k, v in acc.items() if v[1] > 0}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_run"])
-    plan_kc = ((args.window + 31) // 32) * 32
     nb = st.n_bins
-    nch = (nb + plan_kc - 1) // plan_kc
-    nsnap = plan_kc // 32 + 1
     per_launch_ms = kernels[dom]["ms_per_run"] / kernels[dom]["launches_per_run"]
     nlive = st.n_live
-    algo = algorithmic_bytes(dom, N, nb, nlive, est, nch, plan_kc, nsnap)
+    algo = algorithmic_bytes(dom, N, nb, nlive, est)
     hbm, hbm_kind = peaks()
     achieved = algo / (per_launch_ms * 1e-3) / 1e9
     # the catalog pass separately (timed inside the graph of the last timed step)
-    pre_algo = algorithmic_bytes("prepass", N, nb, nlive, est, nch, plan_kc, nsnap)
-    per_iter = sum(algorithmic_bytes(k, N, nb, nlive, est, nch, plan_kc, nsnap)
+    pre_algo = algorithmic_bytes("prepass", N, nb, nlive, est)
+    per_iter = sum(algorithmic_bytes(k, N, nb, nlive, est)
                    for k in kernels if k not in ("prepass", "control"))
     whole_bytes = pre_algo + st.iterations * per_iter + N
     traffic = None

@@ -185,8 +185,8 @@ int sub_get_timing(sub_ctx* ctx, float* prepass_ms, float* loop_ms, float* total
 
 /* Kernels of the path, in the order of SUB_K_* below. */
 #define SUB_K_PREPASS 0   /* catalog pass: sweep, deposit, rho_0, candidates  */
-#define SUB_K_SORT 1      /* per-chunk sort + active-set snapshots (median)    */
-#define SUB_K_SLIDE 2     /* sliding median                                    */
+#define SUB_K_SORT 1      /* per-chunk sort (median)                           */
+#define SUB_K_MEDIAN 2    /* running median (merged ranks, wavelet selection)  */
 #define SUB_K_PREFIX 3    /* exact per-chunk prefix sums (mean)                */
 #define SUB_K_MEAN 4      /* window means                                      */
 #define SUB_K_SNR 5       /* SNR, threshold, removal                           */

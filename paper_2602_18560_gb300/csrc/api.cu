@@ -49,7 +49,6 @@ struct sub_ctx {
   unsigned char* dirty = nullptr;  // two sets of one byte per chunk
   unsigned long long* skey = nullptr;
   uint16_t* srank = nullptr;
-  uint32_t* snap = nullptr;
   unsigned long long *pre_lo = nullptr, *pre_hi = nullptr;
   unsigned* uflow = nullptr;
   // catalog and per-source buffers
@@ -188,16 +187,9 @@ static SmoothPlan make_plan(int W, int64_t n) {
   pl.Kc = kc;
   pl.nw = kc / 32;
   pl.nch = (int)((n + kc - 1) / kc);
-  pl.nsnap = kc / kSnapStride + 1;
   int kp = 1;
   while (kp < kc) kp <<= 1;
   pl.kpad = kp;
-  pl.L = 32;
-  int t = (96 * 1024) / (8 * pl.nw);
-  t = (t / 32) * 32;
-  if (t > 128) t = 128;
-  if (t < 32) t = 32;
-  pl.slide_threads = t;
   return pl;
 }
 
@@ -271,7 +263,6 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   if (p->estimator != SUB_MEAN) {
     rc = dalloc(c, (void**)&c->skey, (size_t)ncell * 8);
     if (!rc) rc = dalloc(c, (void**)&c->srank, (size_t)ncell * 2);
-    if (!rc) rc = dalloc(c, (void**)&c->snap, (size_t)pl.nch * pl.nsnap * pl.nw * 4);
     if (!rc && p->estimator == SUB_MEDIAN_MEAN) rc = dalloc(c, (void**)&c->M, (size_t)n * 8);
     if (rc) return fail(rc);
   }
@@ -432,8 +423,8 @@ static void enqueue_estimate(sub_ctx* c, cudaStream_t st, SpecIn in, int rtol_on
       break;
     }
     case SUB_MEDIAN: {
-      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(in, n, pl, c->skey, c->srank, c->snap, d, st); }
-      { KTimer t(c, st, SUB_K_SLIDE); launch_median_slide(c->skey, c->srank, c->snap, n, pl, o, d, st); }
+      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(in, n, pl, c->skey, c->srank, d, st); }
+      { KTimer t(c, st, SUB_K_MEDIAN); launch_running_median(c->skey, c->srank, n, pl, o, d, st); }
       break;
     }
     default: {
@@ -445,8 +436,8 @@ static void enqueue_estimate(sub_ctx* c, cudaStream_t st, SpecIn in, int rtol_on
       mi.acc = nullptr;
       mi.S = nullptr;
       mi.x = c->M;
-      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(in, n, pl, c->skey, c->srank, c->snap, d, st); }
-      { KTimer t(c, st, SUB_K_SLIDE); launch_median_slide(c->skey, c->srank, c->snap, n, pl, om, d, st); }
+      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(in, n, pl, c->skey, c->srank, d, st); }
+      { KTimer t(c, st, SUB_K_MEDIAN); launch_running_median(c->skey, c->srank, n, pl, om, d, st); }
       { KTimer t(c, st, SUB_K_PREFIX); launch_chunk_prefix(mi, n, pl, c->pre_lo, c->pre_hi, c->sig, c->uflow, nullptr, d, 1, st); }
       { KTimer t(c, st, SUB_K_MEAN); launch_window_mean(c->M, n, pl, c->pre_lo, c->pre_hi, c->sig, c->uflow, o, d, 2, st); }
       break;

@@ -21,7 +21,6 @@ constexpr double kMedianBias = 729.0 / 512.0;
 constexpr double kQScale = 79228162514264337593543950336.0;                   // 2^96
 constexpr double kQLimit = 170141183460469231731687303715884105728.0;          // 2^127
 constexpr int kMaxWindow = 8192;
-constexpr int kSnapStride = 32;   // positions between stored active-set snapshots
 
 // Error bits raised on the device.
 enum : unsigned { ERR_RANGE = 1u, ERR_WINDOW = 2u, ERR_CAND = 4u };
@@ -200,37 +199,6 @@ __device__ __forceinline__ double sweep_weight(const Sweep& s, i64 k) {
   double b = fmin(s.hi, __dadd_rn((double)k, 0.5));
   if (!(b > a)) return 0.0;
   return __ddiv_rn(__dsub_rn(b, a), __dsub_rn(s.hi, s.lo));
-}
-
-// ---------------------------------------------------------------- bitsets
-// Smallest set bit index >= i in words[0 .. nw), stride-addressed (word w at
-// words[w * stride]); returns limit if none below limit.
-__device__ __forceinline__ int bs_next(const uint32_t* words, int stride, int nw, int i, int limit) {
-  if (i >= limit) return limit;
-  int w = i >> 5;
-  uint32_t bits = words[w * stride] & (0xFFFFFFFFu << (i & 31));
-  while (bits == 0u) {
-    ++w;
-    if (w >= nw) return limit;
-    bits = words[w * stride];
-  }
-  int r = (w << 5) + __ffs(bits) - 1;
-  return r < limit ? r : limit;
-}
-
-// Largest set bit index < i; -1 if none.
-__device__ __forceinline__ int bs_prev(const uint32_t* words, int stride, int i) {
-  if (i <= 0) return -1;
-  int w = (i - 1) >> 5;
-  int sh = (i - 1) & 31;
-  uint32_t mask = (sh == 31) ? 0xFFFFFFFFu : ((2u << sh) - 1u);
-  uint32_t bits = words[w * stride] & mask;
-  while (bits == 0u) {
-    --w;
-    if (w < 0) return -1;
-    bits = words[w * stride];
-  }
-  return (w << 5) + 31 - __clz(bits);
 }
 
 }  // namespace gbsub

@@ -303,18 +303,16 @@ __device__ __forceinline__ double sg_store(const SgOut& o, long long j, double v
 // ============================================================================ chunk sort
 // Chunks of Kc >= W consecutive bins: any window of at most W bins lies in at most two
 // consecutive chunks.  Each chunk is sorted once (keys: the bits of the non-negative
-// doubles, whose integer order is their value order; ties broken by position), and
-// for every kSnapStride-th position t the set of sorted indices whose position is >= t
-// is stored as a bitset ("snapshot") so that a thread can build the active set of any
-// window quickly.
+// doubles, whose integer order is their value order; ties broken by position); srank
+// maps a position to its sorted index.
 
 __global__ void k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
                              unsigned long long* __restrict__ skey, uint16_t* __restrict__ srank,
-                             uint32_t* __restrict__ snap, Dirty d) {
+                             Dirty d) {
   extern __shared__ unsigned long long sm_keys[];
   uint16_t* sm_idx = (uint16_t*)(sm_keys + pl.kpad);
   const int b = blockIdx.x;
-  if (!d.any(b, 0)) return;  // unchanged input: keys, ranks and snapshots still hold
+  if (!d.any(b, 0)) return;  // unchanged input: keys and ranks still hold
   const long long base = (long long)b * pl.Kc;
   const int len = (int)((n - base) < pl.Kc ? (n - base) : pl.Kc);
   for (int i = threadIdx.x; i < pl.kpad; i += blockDim.x) {
@@ -352,544 +350,220 @@ __global__ void k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
     skey[base + s] = sm_keys[s];
     srank[base + sm_idx[s]] = (uint16_t)s;
   }
-  // snapshots: word w of snapshot m has bit i set iff sorted index 32w+i < len and its
-  // position is >= m * kSnapStride.
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  for (int w = warp; w < pl.nw; w += nwarp) {
-    int s = w * 32 + lane;
-    int pos = (s < len) ? (int)sm_idx[s] : -1;
-    uint32_t* dst = snap + (size_t)b * pl.nsnap * pl.nw + w;
-    for (int m = 0; m < pl.nsnap; ++m) {
-      unsigned bits = __ballot_sync(0xFFFFFFFFu, pos >= m * kSnapStride);
-      if (lane == 0) dst[(size_t)m * pl.nw] = bits;
-    }
-  }
 }
 
 void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
-                       uint16_t* srank, uint32_t* snap, Dirty d, cudaStream_t st) {
+                       uint16_t* srank, Dirty d, cudaStream_t st) {
   size_t smem = (size_t)pl.kpad * (sizeof(u64) + sizeof(uint16_t));
   int th = pl.kpad >= 1024 ? 1024 : (pl.kpad < 64 ? 64 : pl.kpad);
-  k_chunk_sort<<<pl.nch, th, smem, st>>>(in, n, pl, skey, srank, snap, d);
+  k_chunk_sort<<<pl.nch, th, smem, st>>>(in, n, pl, skey, srank, d);
 }
 
-// ============================================================================ median slide
-// Each thread produces L consecutive outputs.  The window of output j is
-// [s(j), e(j)] = [max(0, j - W/2), min(n-1, j - W/2 + W - 1)] and lies in chunk A (the
-// chunk of s(j)) and chunk B = A + 1.  The thread keeps, for A and B, a bitset over
-// sorted indices marking the elements inside the window, and a "merge cut" (cA, cB):
-// the first cA sorted elements of A and first cB of B are exactly the elements that
-// precede the cut in the merged order of A and B (ties: A first, then by position).
-// pc counts the active elements before the cut; it is kept at c/2 + 1 (c = window
-// size), so the last active element before the cut is the upper median.  Sliding the
-// window by one bin clears one bit and sets one bit, and moves the cut by O(1) active
-// elements.  The initial cut comes from a binary search over the merged order.
+// ============================================================================ running median
+// Tile u (u = 0 .. nch) produces the outputs j in [(u-1) Kc + h, u Kc + h), h = W/2.
+// Their windows [s(j), e(j)] = [max(0, j - h), min(n-1, j - h + W - 1)] lie in the 2 Kc
+// bins of chunks u-1 and u (W <= Kc): the tile's span.  One CTA per tile
+//  1. merges the two sorted chunks, so that every position p of the span gets its rank
+//     v(p) in the merged order (key, then position): a permutation of 0 .. 2Kc-1, bins
+//     outside the band taking the top ranks (they are never inside a window);
+//  2. builds a wavelet matrix of v over the positions: level l (l = 0 .. LV-1) stores bit
+//     LV-1-l of the ranks in the order the stable partitions (zeros first) of the levels
+//     above left them, as bitset words with exclusive prefix counts of their ones;
+//  3. answers, one thread per output, "k-th smallest rank among positions [s, e]" by LV
+//     descents of two rank lookups each, for k = c/2 (the upper median of c bins) and
+//     k = c/2 - 1 (the lower one, used when c is even).
+// Both results are elements of the window, so the median (App. D, Eq. running median)
+// is a selection, exact whatever the order of the arithmetic; the ranks only say which
+// element is selected.  Every output costs O(log Kc) independent of its neighbours, so
+// a tile's latency is a few thousand cycles even when a single chunk has changed.
 
-struct SlideSide {
-  const u64* key;        // sorted keys of the chunk
-  const uint16_t* rank;  // position -> sorted index
-  const uint32_t* snap;  // snapshots of the chunk
-  uint32_t* bs;          // bitset words (strided)
-  int len;               // elements in the chunk (0 if none)
-  long long base;        // first bin of the chunk
-};
+__device__ __forceinline__ int wm_levels(int M) { return 32 - __clz(M - 1); }
 
-__device__ __forceinline__ void side_bind(SlideSide& sd, const u64* skey, const uint16_t* srank,
-                                          const uint32_t* snap, const SmoothPlan& pl, long long n,
-                                          long long chunk) {
-  sd.base = chunk * pl.Kc;
-  long long rem = n - sd.base;
-  sd.len = rem <= 0 ? 0 : (rem < pl.Kc ? (int)rem : pl.Kc);
-  if (chunk >= pl.nch) chunk = pl.nch - 1;  // unused when len == 0
-  sd.key = skey + chunk * (long long)pl.Kc;
-  sd.rank = srank + chunk * (long long)pl.Kc;
-  sd.snap = snap + chunk * (long long)pl.nsnap * pl.nw;
-}
-
-__device__ __forceinline__ void bs_set(uint32_t* bs, int stride, int s) {
-  bs[(s >> 5) * stride] |= (1u << (s & 31));
-}
-__device__ __forceinline__ void bs_clear(uint32_t* bs, int stride, int s) {
-  bs[(s >> 5) * stride] &= ~(1u << (s & 31));
-}
-
-// Active positions [p0, p1) of a chunk as a bitset over sorted indices.
-__device__ void side_fill(SlideSide& sd, int stride, int nw, int p0, int p1) {
-  if (sd.len == 0 || p1 <= p0) {
-    for (int w = 0; w < nw; ++w) sd.bs[w * stride] = 0u;
-    return;
-  }
-  int m0 = p0 / kSnapStride, m1 = p1 / kSnapStride;
-  const uint32_t* s0 = sd.snap + (size_t)m0 * nw;
-  const uint32_t* s1 = sd.snap + (size_t)m1 * nw;
-  for (int w = 0; w < nw; ++w) sd.bs[w * stride] = __ldg(s0 + w) & ~__ldg(s1 + w);
-  for (int p = m0 * kSnapStride; p < p0; ++p) bs_clear(sd.bs, stride, __ldg(sd.rank + p));
-  int q0 = m1 * kSnapStride > p0 ? m1 * kSnapStride : p0;
-  for (int p = q0; p < p1; ++p) bs_set(sd.bs, stride, __ldg(sd.rank + p));
-}
-
-__device__ __forceinline__ int popc_prefix(const uint32_t* bs, int stride, int c) {
-  int r = 0;
-  int w = c >> 5;
-  for (int i = 0; i < w; ++i) r += __popc(bs[i * stride]);
-  if (c & 31) r += __popc(bs[w * stride] & ((1u << (c & 31)) - 1u));
-  return r;
-}
-
-// Number of A elements among the first P of the merged order.
-__device__ __forceinline__ int merge_path(const SlideSide& A, const SlideSide& B, int P) {
-  int lo = P - B.len > 0 ? P - B.len : 0;
-  int hi = P < A.len ? P : A.len;
-  while (lo < hi) {
-    int x = (lo + hi + 1) >> 1;  // try taking x elements of A
-    int y = P - x;
-    bool ok = (y >= B.len) || (__ldg(A.key + x - 1) <= __ldg(B.key + y));
-    if (ok) lo = x; else hi = x - 1;
-  }
-  return lo;
-}
-
-__global__ void __launch_bounds__(128) k_median_slide(
+__global__ void __launch_bounds__(512, 2) k_median_wm(
     const unsigned long long* __restrict__ skey, const uint16_t* __restrict__ srank,
-    const uint32_t* __restrict__ snap, long long n, SmoothPlan pl, SgOut o, Dirty d) {
-  extern __shared__ uint32_t sm_bits[];
-  const int T = blockDim.x;
-  const int tid = threadIdx.x;
-  const int nw = pl.nw;
-  uint32_t* bsX = sm_bits + tid;               // word w at bsX[w * T]
-  uint32_t* bsY = sm_bits + (size_t)nw * T + tid;
-  const long long g = blockIdx.x * (long long)T + tid;
-  const long long j0 = g * pl.L;
-  double relmax = 0.0;
-  // the outputs of this thread lie in one chunk (L divides Kc); their windows read chunks
-  // within one of it
-  if (j0 < n && d.any(j0 / pl.Kc, 1)) {
-    const long long j1 = (j0 + pl.L < n) ? j0 + pl.L : n;
-    const int h = pl.W / 2;
-    long long s_cur = j0 - h > 0 ? j0 - h : 0;
-    long long e_cur = j0 - h + pl.W - 1 < n - 1 ? j0 - h + pl.W - 1 : n - 1;
-    long long chA = s_cur / pl.Kc;
-    SlideSide A, B;
-    side_bind(A, skey, srank, snap, pl, n, chA);
-    side_bind(B, skey, srank, snap, pl, n, chA + 1);
-    A.bs = bsX;
-    B.bs = bsY;
-    {
-      int pa0 = (int)(s_cur - A.base);
-      long long ea = e_cur - A.base + 1;
-      int pa1 = (int)(ea < A.len ? ea : A.len);
-      side_fill(A, T, nw, pa0, pa1);
-      long long eb = e_cur - B.base + 1;
-      int pb1 = eb <= 0 ? 0 : (int)(eb < B.len ? eb : B.len);
-      side_fill(B, T, nw, 0, pb1);
-    }
-    int c = (int)(e_cur - s_cur + 1);
-    int kq = c / 2 + 1;
-    // initial cut: smallest merged position with kq active elements before it
-    int lo = kq, hi = A.len + B.len;
-    while (lo < hi) {
-      int P = (lo + hi) >> 1;
-      int x = merge_path(A, B, P);
-      int cnt = popc_prefix(A.bs, T, x) + popc_prefix(B.bs, T, P - x);
-      if (cnt >= kq) hi = P; else lo = P + 1;
-    }
-    int cA = merge_path(A, B, lo);
-    int cB = lo - cA;
-    int pc = kq;
-
-    for (long long j = j0; j < j1; ++j) {
-      if (j > j0) {
-        long long sj = j - h > 0 ? j - h : 0;
-        long long ej = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
-        if (sj > s_cur) {
-          int sx = __ldg(A.rank + (s_cur - A.base));
-          bs_clear(A.bs, T, sx);
-          --c;
-          if (sx < cA) --pc;
-          s_cur = sj;
-          if (s_cur >= A.base + A.len && B.len > 0) {
-            // chunk A is empty: B becomes A, the next chunk becomes B
-            uint32_t* freed = A.bs;
-            A = B;
-            cA = cB;
-            ++chA;
-            side_bind(B, skey, srank, snap, pl, n, chA + 1);
-            B.bs = freed;  // all zero: every element of the old A has left
-            // cB = number of B elements preceding A[cA] (B after A on ties)
-            int lo2 = 0, hi2 = B.len;
-            if (cA < A.len) {
-              u64 ka = __ldg(A.key + cA);
-              while (lo2 < hi2) {
-                int mid = (lo2 + hi2) >> 1;
-                if (__ldg(B.key + mid) < ka) lo2 = mid + 1; else hi2 = mid;
-              }
-              cB = lo2;
-            } else {
-              cB = B.len;
-            }
-          }
-        }
-        if (ej > e_cur) {
-          e_cur = ej;
-          if (ej < A.base + A.len) {
-            int sx = __ldg(A.rank + (ej - A.base));
-            bs_set(A.bs, T, sx);
-            ++c;
-            if (sx < cA) ++pc;
-          } else {
-            int sx = __ldg(B.rank + (ej - B.base));
-            bs_set(B.bs, T, sx);
-            ++c;
-            if (sx < cB) ++pc;
-          }
-        }
-        kq = c / 2 + 1;
-        while (pc < kq) {
-          // advance over the next active element of the merged order
-          int nA = bs_next(A.bs, T, nw, cA, A.len);
-          int nB = bs_next(B.bs, T, nw, cB, B.len);
-          bool takeA = (nB >= B.len) || (nA < A.len && __ldg(A.key + nA) <= __ldg(B.key + nB));
-          if (takeA) {
-            u64 ka = __ldg(A.key + nA);
-            cA = nA + 1;
-            while (cB < B.len && __ldg(B.key + cB) < ka) ++cB;
-          } else {
-            u64 kb = __ldg(B.key + nB);
-            cB = nB + 1;
-            while (cA < A.len && __ldg(A.key + cA) <= kb) ++cA;
-          }
-          ++pc;
-        }
-        while (pc > kq) {
-          // retreat over the last active element before the cut
-          int pA = bs_prev(A.bs, T, cA);
-          int pB = bs_prev(B.bs, T, cB);
-          bool takeB = (pA < 0) || (pB >= 0 && __ldg(B.key + pB) >= __ldg(A.key + pA));
-          if (takeB) {
-            u64 kb = __ldg(B.key + pB);
-            cB = pB;
-            while (cA > 0 && __ldg(A.key + cA - 1) > kb) --cA;
-          } else {
-            u64 ka = __ldg(A.key + pA);
-            cA = pA;
-            while (cB > 0 && __ldg(B.key + cB - 1) >= ka) --cB;
-          }
-          --pc;
-        }
-      }
-      // the upper median is the last active element before the cut
-      int pA = bs_prev(A.bs, T, cA);
-      int pB = bs_prev(B.bs, T, cB);
-      u64 khi, klo = 0;
-      bool hiB = (pA < 0) || (pB >= 0 && __ldg(B.key + pB) >= __ldg(A.key + pA));
-      if (hiB) khi = __ldg(B.key + pB); else khi = __ldg(A.key + pA);
-      double med;
-      if (c & 1) {
-        med = __longlong_as_double((i64)khi);
-      } else {
-        // lower median: the larger of the other side's last active and this side's previous
-        int q1, q2;
-        u64 k1 = 0, k2 = 0;
-        bool h1 = false, h2 = false;
-        if (hiB) {
-          q1 = pA;
-          q2 = bs_prev(B.bs, T, pB);
-          if (q1 >= 0) { k1 = __ldg(A.key + q1); h1 = true; }
-          if (q2 >= 0) { k2 = __ldg(B.key + q2); h2 = true; }
-        } else {
-          q1 = pB;
-          q2 = bs_prev(A.bs, T, pA);
-          if (q1 >= 0) { k1 = __ldg(B.key + q1); h1 = true; }
-          if (q2 >= 0) { k2 = __ldg(A.key + q2); h2 = true; }
-        }
-        klo = (h1 && h2) ? (k1 > k2 ? k1 : k2) : (h1 ? k1 : k2);
-        med = __dmul_rn(__dadd_rn(__longlong_as_double((i64)klo), __longlong_as_double((i64)khi)),
-                        0.5);
-      }
-      double v = __dmul_rn(kMedianBias, med);
-      double rel = sg_store(o, j, v);
-      relmax = rel > relmax ? rel : relmax;
-    }
-  }
-  if (o.rtol_on) warp_max_atomic((u64)__double_as_longlong(relmax), &o.rs->relchg_bits);
-}
-
-// Same algorithm with the sorted keys and ranks of the three chunks a window of output
-// chunk c can touch (c-1, c, c+1) staged in shared memory: one CTA per output chunk, so
-// the dependent loads of each thread's merge-cut walk hit shared memory.  Snapshots are
-// read from global memory (a few independent loads per thread at set-up).
-__global__ void __launch_bounds__(256) k_median_slide_smem(
-    const unsigned long long* __restrict__ skey, const uint16_t* __restrict__ srank,
-    const uint32_t* __restrict__ snap, long long n, SmoothPlan pl, SgOut o, Dirty d) {
+    long long n, SmoothPlan pl, SgOut o, Dirty d) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int T = blockDim.x;
-  const int tid = threadIdx.x;
-  const int nw = pl.nw;
-  const int Kc = pl.Kc;
-  const long long c = blockIdx.x;
-  if (!d.any(c, 1)) return;  // no window of this chunk changed
-  u64* sk = (u64*)sm_raw;                                   // [3][Kc]
-  uint16_t* sr = (uint16_t*)(sk + 3 * (size_t)Kc);          // [3][Kc]
-  uint32_t* sb = (uint32_t*)(sr + 3 * (size_t)Kc);          // [2][nw][T]
-  uint16_t* sp = (uint16_t*)(sb + 2 * (size_t)nw * T);      // [2][nw + 1][T] word prefixes
-  const long long c0 = c - 1;  // chunk held in slot 0
-  for (int slot = 0; slot < 3; ++slot) {
-    long long ch = c0 + slot;
-    if (ch < 0 || ch >= pl.nch) continue;
-    long long base = ch * (long long)Kc;
-    int len = (int)((n - base) < Kc ? (n - base) : Kc);
-    const ulonglong2* gk = reinterpret_cast<const ulonglong2*>(skey + base);
-    ulonglong2* dk = reinterpret_cast<ulonglong2*>(sk + (size_t)slot * Kc);
-    for (int i = tid; i < (len + 1) / 2; i += T) dk[i] = gk[i];
-    for (int i = tid; i < len; i += T) sr[(size_t)slot * Kc + i] = srank[base + i];
+  __shared__ int zeros[16];
+  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Kc = pl.Kc, M = 2 * Kc, LV = wm_levels(M);
+  const int nwm = M >> 5, ws = nwm + 1;  // words per level (one zero word of padding)
+  const long long u = blockIdx.x;
+  const int h = pl.W / 2;
+  long long j_lo = (u - 1) * Kc + h, j_hi = u * Kc + h;
+  if (j_lo < 0) j_lo = 0;
+  if (j_hi > n) j_hi = n;
+  if (j_lo >= j_hi) return;
+  if (!d.any_between(u - 1, u)) return;  // no window of this tile changed
+  const long long span = (u - 1) * (long long)Kc;
+  int len0 = 0, len1 = 0;
+  if (u >= 1) len0 = (n - span) < Kc ? (int)(n - span) : Kc;
+  if (u < pl.nch) len1 = (n - span - Kc) < Kc ? (int)(n - span - Kc) : Kc;
+  u64* sk = (u64*)sm_raw;                                    // [M] sorted keys (step 1)
+  uint16_t* seq1 = (uint16_t*)sm_raw;                        // [M] (steps 2-3, over sk)
+  uint16_t* src = seq1 + M;                                  // [M] rank -> element
+  uint16_t* seq0 = (uint16_t*)(sm_raw + (size_t)16 * Kc);    // [M]
+  uint32_t* bits = (uint32_t*)(seq0 + M);                    // [LV][ws]
+  uint16_t* pre = (uint16_t*)(bits + (size_t)LV * ws);       // [LV][ws]
+
+  // 1. merged ranks.  Chunk u-1 precedes chunk u on equal keys (its positions are lower).
+  for (int i = tid; i < len0; i += T) sk[i] = skey[span + i];
+  for (int i = tid; i < len1; i += T) sk[Kc + i] = skey[span + Kc + i];
+  __syncthreads();
+  for (int p = tid; p < M; p += T) {
+    const int X = p >= Kc, q = p - X * Kc;
+    const int lenX = X ? len1 : len0;
+    int v;
+    if (q < lenX) {
+      const int si = srank[span + p];
+      const u64 key = sk[p - q + si];
+      const u64* oth = X ? sk : sk + Kc;
+      int lo = 0, hi = X ? len0 : len1;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        u64 km = oth[mid];
+        bool before = X ? (km <= key) : (km < key);
+        if (before) lo = mid + 1; else hi = mid;
+      }
+      v = si + lo;
+    } else {
+      v = len0 + len1 + (X ? (Kc - len0) + (q - len1) : (q - len0));
+    }
+    seq0[p] = (uint16_t)v;
   }
   __syncthreads();
-  uint32_t* bsX = sb + tid;
-  uint32_t* bsY = sb + (size_t)nw * T + tid;
-  const long long j0 = c * Kc + (long long)tid * pl.L;
+  for (int p = tid; p < M; p += T) {
+    const int X = p >= Kc, q = p - X * Kc;
+    if (q < (X ? len1 : len0)) src[seq0[p]] = (uint16_t)((X << 15) | srank[span + p]);
+  }
+
+  // 2. wavelet matrix (T is a multiple of 32 and M of 64: every warp covers whole words)
+  const int nit = (M + T - 1) / T;
+  uint16_t* cur = seq0;
+  uint16_t* nxt = seq1;
+  for (int l = 0; l < LV; ++l) {
+    const int sh = LV - 1 - l;
+    uint32_t* bl = bits + (size_t)l * ws;
+    uint16_t* pf = pre + (size_t)l * ws;
+    for (int it = 0; it < nit; ++it) {
+      const int i = it * T + tid;
+      const int b = (i < M) ? ((cur[i] >> sh) & 1) : 0;
+      const unsigned w = __ballot_sync(0xFFFFFFFFu, b);
+      if (lane == 0 && i < M) bl[i >> 5] = w;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int run = 0;
+      for (int w0 = 0; w0 < nwm; w0 += 32) {
+        const int w = w0 + lane;
+        const int c = (w < nwm) ? __popc(bl[w]) : 0;
+        int incl = c;
+        for (int s = 1; s < 32; s <<= 1) {
+          int t = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+          if (lane >= s) incl += t;
+        }
+        if (w < nwm) pf[w] = (uint16_t)(run + incl - c);
+        run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+      }
+      if (lane == 0) {
+        pf[nwm] = (uint16_t)run;
+        bl[nwm] = 0u;
+        zeros[l] = M - run;
+      }
+    }
+    __syncthreads();
+    if (l + 1 < LV) {
+      const int Z = zeros[l];
+      for (int it = 0; it < nit; ++it) {
+        const int i = it * T + tid;
+        if (i < M) {
+          const int x = cur[i];
+          const int ob = pf[i >> 5] + __popc(bl[i >> 5] & ((1u << lane) - 1u));
+          nxt[((x >> sh) & 1) ? Z + ob : i - ob] = (uint16_t)x;
+        }
+      }
+      __syncthreads();
+      uint16_t* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+  }
+
+  // 3. selections
   double relmax = 0.0;
-  if (j0 < n) {
-    long long jend = (c + 1) * (long long)Kc;
-    long long j1 = j0 + pl.L < jend ? j0 + pl.L : jend;
-    if (j1 > n) j1 = n;
-    const int h = pl.W / 2;
-    long long s_cur = j0 - h > 0 ? j0 - h : 0;
-    long long e_cur = j0 - h + pl.W - 1 < n - 1 ? j0 - h + pl.W - 1 : n - 1;
-    long long chA = s_cur / Kc;
-    auto bind = [&](SlideSide& sd, long long ch) {
-      sd.base = ch * Kc;
-      long long rem = n - sd.base;
-      sd.len = rem <= 0 ? 0 : (rem < Kc ? (int)rem : Kc);
-      long long slot = ch - c0;
-      if (slot < 0) slot = 0;
-      if (slot > 2) slot = 2;
-      sd.key = sk + slot * Kc;
-      sd.rank = sr + slot * Kc;
-      long long chs = ch < pl.nch ? ch : pl.nch - 1;
-      sd.snap = snap + chs * (long long)pl.nsnap * nw;
-    };
-    SlideSide A, B;
-    bind(A, chA);
-    bind(B, chA + 1);
-    A.bs = bsX;
-    B.bs = bsY;
-    {
-      int pa0 = (int)(s_cur - A.base);
-      long long ea = e_cur - A.base + 1;
-      int pa1 = (int)(ea < A.len ? ea : A.len);
-      int m0 = pa0 / kSnapStride, m1 = pa1 / kSnapStride;
-      if (A.len == 0 || pa1 <= pa0) {
-        for (int w = 0; w < nw; ++w) A.bs[w * T] = 0u;
+  const int nout = (int)(j_hi - j_lo);
+  for (int t = tid; t < nout; t += T) {
+    const long long j = j_lo + t;
+    const long long s = j - h > 0 ? j - h : 0;
+    const long long e = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
+    const int cnt = (int)(e - s + 1);
+    // two descents side by side: a = upper median (k = c/2), b = lower (k = c/2 - 1)
+    int la = (int)(s - span), ra = (int)(e + 1 - span), ka = cnt >> 1, va = 0;
+    int lb = la, rb = ra, kb = ka > 0 ? ka - 1 : 0, vb = 0;
+    for (int l = 0; l < LV; ++l) {
+      const uint32_t* bl = bits + (size_t)l * ws;
+      const uint16_t* pf = pre + (size_t)l * ws;
+      const int Z = zeros[l];
+      const int oal = pf[la >> 5] + __popc(bl[la >> 5] & ((1u << (la & 31)) - 1u));
+      const int oar = pf[ra >> 5] + __popc(bl[ra >> 5] & ((1u << (ra & 31)) - 1u));
+      const int obl = pf[lb >> 5] + __popc(bl[lb >> 5] & ((1u << (lb & 31)) - 1u));
+      const int obr = pf[rb >> 5] + __popc(bl[rb >> 5] & ((1u << (rb & 31)) - 1u));
+      const int za = (ra - oar) - (la - oal), zb = (rb - obr) - (lb - obl);
+      const int bit = 1 << (LV - 1 - l);
+      if (ka < za) {
+        la -= oal;
+        ra -= oar;
       } else {
-        const uint32_t* s0 = A.snap + (size_t)m0 * nw;
-        const uint32_t* s1 = A.snap + (size_t)m1 * nw;
-        for (int w = 0; w < nw; ++w) A.bs[w * T] = __ldg(s0 + w) & ~__ldg(s1 + w);
-        for (int p = m0 * kSnapStride; p < pa0; ++p) bs_clear(A.bs, T, A.rank[p]);
-        int q0 = m1 * kSnapStride > pa0 ? m1 * kSnapStride : pa0;
-        for (int p = q0; p < pa1; ++p) bs_set(A.bs, T, A.rank[p]);
+        ka -= za;
+        la = Z + oal;
+        ra = Z + oar;
+        va |= bit;
       }
-      long long eb = e_cur - B.base + 1;
-      int pb1 = eb <= 0 ? 0 : (int)(eb < B.len ? eb : B.len);
-      if (B.len == 0 || pb1 <= 0) {
-        for (int w = 0; w < nw; ++w) B.bs[w * T] = 0u;
+      if (kb < zb) {
+        lb -= obl;
+        rb -= obr;
       } else {
-        int mb = pb1 / kSnapStride;
-        const uint32_t* s0 = B.snap;
-        const uint32_t* s1 = B.snap + (size_t)mb * nw;
-        for (int w = 0; w < nw; ++w) B.bs[w * T] = __ldg(s0 + w) & ~__ldg(s1 + w);
-        for (int p = mb * kSnapStride; p < pb1; ++p) bs_set(B.bs, T, B.rank[p]);
+        kb -= zb;
+        lb = Z + obl;
+        rb = Z + obr;
+        vb |= bit;
       }
     }
-    int cnt = (int)(e_cur - s_cur + 1);
-    int kq = cnt / 2 + 1;
-    // word prefixes of the active counts (valid until the first slide step), so that the
-    // count of active elements below a sorted index is one lookup and one popcount
-    uint16_t* pA = sp + tid;
-    uint16_t* pB = sp + (size_t)(nw + 1) * T + tid;
-    {
-      int ra = 0, rb = 0;
-      for (int w = 0; w < nw; ++w) {
-        pA[w * T] = (uint16_t)ra;
-        pB[w * T] = (uint16_t)rb;
-        ra += __popc(A.bs[w * T]);
-        rb += __popc(B.bs[w * T]);
-      }
-      pA[nw * T] = (uint16_t)ra;
-      pB[nw * T] = (uint16_t)rb;
+    const int ea = src[va];
+    const u64 khi = skey[span + (ea >> 15) * Kc + (ea & 0x7FFF)];
+    double med;
+    if (cnt & 1) {
+      med = __longlong_as_double((i64)khi);
+    } else {
+      const int eb = src[vb];
+      const u64 klo = skey[span + (eb >> 15) * Kc + (eb & 0x7FFF)];
+      med = __dmul_rn(__dadd_rn(__longlong_as_double((i64)klo), __longlong_as_double((i64)khi)),
+                      0.5);
     }
-    auto cnt_below = [&](const uint32_t* bs, const uint16_t* pf, int x) {
-      int w = x >> 5;
-      int r = pf[w * T];
-      if (x & 31) r += __popc(bs[w * T] & ((1u << (x & 31)) - 1u));
-      return r;
-    };
-    // initial cut: smallest merged position with kq active elements before it
-    int lo = kq, hi = A.len + B.len;
-    while (lo < hi) {
-      int P = (lo + hi) >> 1;
-      int lo2 = P - B.len > 0 ? P - B.len : 0, hi2 = P < A.len ? P : A.len;
-      while (lo2 < hi2) {
-        int x = (lo2 + hi2 + 1) >> 1;
-        int y = P - x;
-        bool ok = (y >= B.len) || (A.key[x - 1] <= B.key[y]);
-        if (ok) lo2 = x; else hi2 = x - 1;
-      }
-      int k2 = cnt_below(A.bs, pA, lo2) + cnt_below(B.bs, pB, P - lo2);
-      if (k2 >= kq) hi = P; else lo = P + 1;
-    }
-    int cA, cB;
-    {
-      int P = lo;
-      int lo2 = P - B.len > 0 ? P - B.len : 0, hi2 = P < A.len ? P : A.len;
-      while (lo2 < hi2) {
-        int x = (lo2 + hi2 + 1) >> 1;
-        int y = P - x;
-        bool ok = (y >= B.len) || (A.key[x - 1] <= B.key[y]);
-        if (ok) lo2 = x; else hi2 = x - 1;
-      }
-      cA = lo2;
-      cB = P - lo2;
-    }
-    int pc = kq;
-    for (long long j = j0; j < j1; ++j) {
-      if (j > j0) {
-        long long sj = j - h > 0 ? j - h : 0;
-        long long ej = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
-        if (sj > s_cur) {
-          int sx = A.rank[s_cur - A.base];
-          bs_clear(A.bs, T, sx);
-          --cnt;
-          if (sx < cA) --pc;
-          s_cur = sj;
-          if (s_cur >= A.base + A.len && B.len > 0) {
-            uint32_t* freed = A.bs;
-            A = B;
-            cA = cB;
-            ++chA;
-            bind(B, chA + 1);
-            B.bs = freed;
-            if (cA < A.len) {
-              u64 ka = A.key[cA];
-              int lo3 = 0, hi3 = B.len;
-              while (lo3 < hi3) {
-                int mid = (lo3 + hi3) >> 1;
-                if (B.key[mid] < ka) lo3 = mid + 1; else hi3 = mid;
-              }
-              cB = lo3;
-            } else {
-              cB = B.len;
-            }
-          }
-        }
-        if (ej > e_cur) {
-          e_cur = ej;
-          if (ej < A.base + A.len) {
-            int sx = A.rank[ej - A.base];
-            bs_set(A.bs, T, sx);
-            ++cnt;
-            if (sx < cA) ++pc;
-          } else {
-            int sx = B.rank[ej - B.base];
-            bs_set(B.bs, T, sx);
-            ++cnt;
-            if (sx < cB) ++pc;
-          }
-        }
-        kq = cnt / 2 + 1;
-        while (pc < kq) {
-          int nA = bs_next(A.bs, T, nw, cA, A.len);
-          int nB = bs_next(B.bs, T, nw, cB, B.len);
-          bool takeA = (nB >= B.len) || (nA < A.len && A.key[nA] <= B.key[nB]);
-          if (takeA) {
-            u64 ka = A.key[nA];
-            cA = nA + 1;
-            while (cB < B.len && B.key[cB] < ka) ++cB;
-          } else {
-            u64 kb = B.key[nB];
-            cB = nB + 1;
-            while (cA < A.len && A.key[cA] <= kb) ++cA;
-          }
-          ++pc;
-        }
-        while (pc > kq) {
-          int pA = bs_prev(A.bs, T, cA);
-          int pB = bs_prev(B.bs, T, cB);
-          bool takeB = (pA < 0) || (pB >= 0 && B.key[pB] >= A.key[pA]);
-          if (takeB) {
-            u64 kb = B.key[pB];
-            cB = pB;
-            while (cA > 0 && A.key[cA - 1] > kb) --cA;
-          } else {
-            u64 ka = A.key[pA];
-            cA = pA;
-            while (cB > 0 && B.key[cB - 1] >= ka) --cB;
-          }
-          --pc;
-        }
-      }
-      int pA = bs_prev(A.bs, T, cA);
-      int pB = bs_prev(B.bs, T, cB);
-      bool hiB = (pA < 0) || (pB >= 0 && B.key[pB] >= A.key[pA]);
-      u64 khi = hiB ? B.key[pB] : A.key[pA];
-      double med;
-      if (cnt & 1) {
-        med = __longlong_as_double((i64)khi);
-      } else {
-        int q1, q2;
-        u64 k1 = 0, k2 = 0;
-        bool h1 = false, h2 = false;
-        if (hiB) {
-          q1 = pA;
-          q2 = bs_prev(B.bs, T, pB);
-          if (q1 >= 0) { k1 = A.key[q1]; h1 = true; }
-          if (q2 >= 0) { k2 = B.key[q2]; h2 = true; }
-        } else {
-          q1 = pB;
-          q2 = bs_prev(A.bs, T, pA);
-          if (q1 >= 0) { k1 = B.key[q1]; h1 = true; }
-          if (q2 >= 0) { k2 = A.key[q2]; h2 = true; }
-        }
-        u64 klo = (h1 && h2) ? (k1 > k2 ? k1 : k2) : (h1 ? k1 : k2);
-        med = __dmul_rn(__dadd_rn(__longlong_as_double((i64)klo), __longlong_as_double((i64)khi)),
-                        0.5);
-      }
-      double v = __dmul_rn(kMedianBias, med);
-      double rel = sg_store(o, j, v);
-      relmax = rel > relmax ? rel : relmax;
-    }
+    double v = __dmul_rn(kMedianBias, med);
+    double rel = sg_store(o, j, v);
+    relmax = rel > relmax ? rel : relmax;
   }
   if (o.rtol_on) warp_max_atomic((u64)__double_as_longlong(relmax), &o.rs->relchg_bits);
 }
 
-// Threads per chunk for the shared-memory slide (each takes Kc / T consecutive outputs:
-// short chains of dependent steps), and its shared-memory size.
-static int smem_slide_threads(const SmoothPlan& pl) {
-  int t = pl.Kc / 8;
+static int median_threads(const SmoothPlan& pl) {
+  int t = ((pl.Kc / 2 + 31) / 32) * 32;
   if (t < 32) t = 32;
-  if (t > 128) t = 128;
+  if (t > 512) t = 512;
   return t;
 }
-static size_t smem_slide_bytes(const SmoothPlan& pl, int T) {
-  return (size_t)3 * pl.Kc * (sizeof(u64) + sizeof(uint16_t)) + (size_t)2 * pl.nw * T * 4 +
-         (size_t)2 * (pl.nw + 1) * T * 2;
+
+size_t median_smem_bytes(int Kc) {
+  int M = 2 * Kc, LV = 0;
+  while ((1 << LV) < M) ++LV;
+  size_t ws = (size_t)M / 32 + 1;
+  return (size_t)16 * Kc + (size_t)2 * M + (size_t)LV * ws * (4 + 2);
 }
 
-void launch_median_slide(const unsigned long long* skey, const uint16_t* srank,
-                         const uint32_t* snap, long long n, const SmoothPlan& pl, SgOut o,
-                         Dirty d, cudaStream_t st) {
-  int ts = smem_slide_threads(pl);
-  size_t ss = smem_slide_bytes(pl, ts);
-  if (ss <= 160 * 1024) {
-    SmoothPlan p2 = pl;
-    p2.L = (pl.Kc + ts - 1) / ts;
-    k_median_slide_smem<<<pl.nch, ts, ss, st>>>(skey, srank, snap, n, p2, o, d);
-    return;
-  }
-  int th = pl.slide_threads;
-  long long threads = (n + pl.L - 1) / pl.L;
-  long long bl = (threads + th - 1) / th;
-  size_t smem = (size_t)2 * pl.nw * th * sizeof(uint32_t);
-  k_median_slide<<<(unsigned)bl, th, smem, st>>>(skey, srank, snap, n, pl, o, d);
+void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
+                           const SmoothPlan& pl, SgOut o, Dirty d, cudaStream_t st) {
+  k_median_wm<<<pl.nch + 1, median_threads(pl), median_smem_bytes(pl.Kc), st>>>(skey, srank, n,
+                                                                                pl, o, d);
 }
 
 // ============================================================================ window mean
@@ -1269,8 +943,8 @@ void launch_control(RunState* rs, int max_iter, double rtol, int* new_hist,
 
 void configure_kernels() {
   cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaFuncSetAttribute(k_median_slide, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-  cudaFuncSetAttribute(k_median_slide_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  cudaFuncSetAttribute(k_median_wm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)median_smem_bytes(kMaxWindow));
 }
 
 }  // namespace gbsub

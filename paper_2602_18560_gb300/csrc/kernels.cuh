@@ -61,10 +61,7 @@ struct SmoothPlan {
   int Kc;       // chunk length: multiple of 32, >= W
   int nw;       // 32-bit words per chunk bitset (Kc / 32)
   int nch;      // chunks
-  int nsnap;    // snapshots per chunk (Kc / kSnapStride + 1)
   int kpad;     // power of two >= Kc (sort width)
-  int L;        // outputs per thread in the median slide
-  int slide_threads;
 };
 
 // Source of an estimator's input: the run's fixed-point spectrum (P_k = S_k Q_k 2^-96) or
@@ -84,9 +81,12 @@ struct Dirty {
   int nch;
   const RunState* rs;
   __device__ __forceinline__ bool any(long long c, int radius) const {
+    return any_between(c - radius, c + radius);
+  }
+  // any chunk of [a, b] (clipped to the chunks that exist)
+  __device__ __forceinline__ bool any_between(long long a, long long b) const {
     if (!base) return true;
     const unsigned char* cur = base + (size_t)(rs->iter & 1) * nch;
-    long long a = c - radius, b = c + radius;
     if (a < 0) a = 0;
     if (b > nch - 1) b = nch - 1;
     for (long long i = a; i <= b; ++i)
@@ -125,14 +125,15 @@ void launch_power_out(const unsigned long long* acc, const double* S, long long 
 // *max_bits = max(*max_bits, bits of max x) over x[0 .. n) (x >= 0).
 void launch_max_bits(const double* x, long long n, unsigned long long* max_bits, cudaStream_t st);
 
-// Sort every chunk of the input whose values changed (keys, ranks, active-set snapshots).
+// Sort every chunk of the input whose values changed (sorted keys, position -> rank).
 void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
-                       uint16_t* srank, uint32_t* snap, Dirty d, cudaStream_t st);
+                       uint16_t* srank, Dirty d, cudaStream_t st);
 
-// out = C * running median, recomputed in the output chunks whose windows changed.
-void launch_median_slide(const unsigned long long* skey, const uint16_t* srank,
-                         const uint32_t* snap, long long n, const SmoothPlan& pl, SgOut o,
-                         Dirty d, cudaStream_t st);
+// out = C * running median from the sorted chunks, recomputed in the tiles whose windows
+// changed.
+void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
+                           const SmoothPlan& pl, SgOut o, Dirty d, cudaStream_t st);
+size_t median_smem_bytes(int Kc);
 
 // Exact 128-bit prefix sums of the input inside each chunk at a per-chunk scale sig[b];
 // uflow[b] = 1 when an input > 0 of chunk b is below one unit.  x_out (may be null)

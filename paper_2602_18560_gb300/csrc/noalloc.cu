@@ -100,10 +100,7 @@ extern "C" int sub_running_mean_noalloc(const double* x, double* out, int64_t n,
   if (pl.Kc < 32) pl.Kc = 32;
   pl.nw = pl.Kc / 32;
   pl.nch = (int)((n + pl.Kc - 1) / pl.Kc);
-  pl.nsnap = pl.Kc / kSnapStride + 1;
   pl.kpad = 0;
-  pl.L = 0;
-  pl.slide_threads = 0;
   unsigned long long* pre_lo = base;
   unsigned long long* pre_hi = base + kCells;
   int* sig = (int*)(base + 2 * kCells);

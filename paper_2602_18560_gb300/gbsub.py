@@ -65,7 +65,7 @@ EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_run", "s
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
            "sub_get_tables", "sub_get_timing", "sub_profile", "sub_device_bytes", "sub_destroy",
            "sub_last_error", "sub_running_mean_noalloc", "sub_get_power")
-KERNELS = ("prepass", "sort", "slide", "prefix", "mean", "snr", "control")
+KERNELS = ("prepass", "sort", "median", "prefix", "mean", "snr", "control")
 
 
 def library_path() -> str:
