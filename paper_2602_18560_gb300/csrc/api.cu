@@ -47,6 +47,8 @@ struct sub_ctx {
   float* inv_f = nullptr;
   int* sig = nullptr;
   unsigned char* dirty = nullptr;  // two sets of one byte per chunk
+  int* lists = nullptr;            // work lists of the chunk kernels [kNumLists][nch + 1]
+  int* list_counts = nullptr;      // [kNumLists]
   unsigned long long* skey = nullptr;
   uint16_t* srank = nullptr;
   unsigned long long *pre_lo = nullptr, *pre_hi = nullptr;
@@ -225,6 +227,7 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   if (e != cudaSuccess) { c->err = std::string("cudaGetDevice: ") + cudaGetErrorString(e); return fail(SUB_ECUDA); }
   cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
   if (c->nsm <= 0) c->nsm = 1;
+  c->plan.nsm = c->nsm;
   if (stream) {
     c->stream = (cudaStream_t)stream;
   } else {
@@ -236,6 +239,7 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { c->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e); return fail(SUB_ECUDA); }
   configure_kernels();
+  plan_grids(c->plan);
   {
     cudaEvent_t* evs[] = {&c->ev_start, &c->ev_pre, &c->ev_end, &c->ev_k[0], &c->ev_k[1]};
     for (cudaEvent_t* ev : evs) {
@@ -252,6 +256,8 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
       {(void**)&c->P, (size_t)n * 8}, {(void**)&c->Sg, (size_t)n * 8},
       {(void**)&c->sig, (size_t)pl.nch * 4}, {(void**)&c->estimate_in, (size_t)n * 8},
       {(void**)&c->dirty, (size_t)pl.nch * 2},
+      {(void**)&c->lists, (size_t)kNumLists * (pl.nch + 1) * 4},
+      {(void**)&c->list_counts, (size_t)kNumLists * 4},
       {(void**)&c->pre_lo, (size_t)ncell * 8}, {(void**)&c->pre_hi, (size_t)ncell * 8},
       {(void**)&c->uflow, (size_t)pl.nch * 4},
       {(void**)&c->rs, sizeof(RunState)}, {(void**)&c->new_hist, (size_t)p->max_iter * 4},
@@ -370,6 +376,17 @@ struct KTimer {
   }
 };
 
+// Dirty-chunk tracking of the run (track), or every chunk.
+static Dirty dirty_of(sub_ctx* c, bool track) {
+  Dirty d;
+  d.base = track ? c->dirty : nullptr;
+  d.lists = track ? c->lists : nullptr;
+  d.counts = track ? c->list_counts : nullptr;
+  d.nch = c->plan.nch;
+  d.rs = c->rs;
+  return d;
+}
+
 static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
   const int64_t n = c->grid.nb;
   cudaError_t e;
@@ -378,6 +395,7 @@ static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
   // the first iteration reads set 0: every chunk is new
   if ((e = cudaMemsetAsync(c->dirty, 1, (size_t)c->plan.nch, st))) return e;
   if ((e = cudaMemsetAsync(c->dirty + c->plan.nch, 0, (size_t)c->plan.nch, st))) return e;
+  launch_build_lists(dirty_of(c, true), c->lists, c->list_counts, st);
   if ((e = cudaMemsetAsync(c->new_hist, 0, (size_t)c->p.max_iter * 4, st))) return e;
   if (c->N > 0) {
     if ((e = cudaMemsetAsync(c->resolved, 0, (size_t)c->N, st))) return e;
@@ -392,14 +410,6 @@ static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
 
 // One estimate of S_gal from `in` into c->Sg (and inv_f when with_inv).  With track, only
 // the chunks whose inputs changed since the previous iteration are recomputed.
-static Dirty dirty_of(sub_ctx* c, bool track) {
-  Dirty d;
-  d.base = track ? c->dirty : nullptr;
-  d.nch = c->plan.nch;
-  d.rs = c->rs;
-  return d;
-}
-
 // Chunks around a changed chunk whose S_gal changes: the median and the mean read one chunk
 // on each side, median-then-mean two.
 static int sg_radius_of(const sub_ctx* c) { return c->p.estimator == SUB_MEDIAN_MEAN ? 2 : 1; }
@@ -460,7 +470,7 @@ static cudaError_t enqueue_body(sub_ctx* c, cudaStream_t st, unsigned long long 
                        c->p.conv_rtol, snr_mode(c), c->resolved, c->acc, rs, dirty_of(c, true),
                        c->plan.Kc, sg_radius_of(c), c->nsm, st);
   }
-  { KTimer t(c, st, SUB_K_CONTROL); launch_control(rs, c->p.max_iter, c->p.conv_rtol, c->new_hist, handle, use_cond, c->dirty, c->plan.nch, st); }
+  { KTimer t(c, st, SUB_K_CONTROL); launch_control(rs, c->p.max_iter, c->p.conv_rtol, c->new_hist, handle, use_cond, c->dirty, c->plan.nch, c->lists, c->list_counts, st); }
   return cudaGetLastError();
 }
 

@@ -311,26 +311,29 @@ __global__ void k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
                              Dirty d) {
   extern __shared__ unsigned long long sm_keys[];
   uint16_t* sm_idx = (uint16_t*)(sm_keys + pl.kpad);
-  const int b = blockIdx.x;
-  if (!d.any(b, 0)) return;  // unchanged input: keys and ranks still hold
-  const long long base = (long long)b * pl.Kc;
-  const int len = (int)((n - base) < pl.Kc ? (n - base) : pl.Kc);
-  for (int i = threadIdx.x; i < pl.kpad; i += blockDim.x) {
-    u64 k = ~0ull;
-    if (i < len) {
-      k = (u64)__double_as_longlong(spec_value(in, base + i));
-      if (k >> 63) k = 0ull;  // -0.0 (or a negative value) sorts as zero
+  const int half = pl.kpad >> 1;  // compare-exchange pairs per stage
+  const int nitem = d.count(kListR0, pl.nch);
+  for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+    const int b = d.item(kListR0, it);  // a chunk whose input changed
+    const long long base = (long long)b * pl.Kc;
+    const int len = (int)((n - base) < pl.Kc ? (n - base) : pl.Kc);
+    for (int i = threadIdx.x; i < pl.kpad; i += blockDim.x) {
+      u64 k = ~0ull;
+      if (i < len) {
+        k = (u64)__double_as_longlong(spec_value(in, base + i));
+        if (k >> 63) k = 0ull;  // -0.0 (or a negative value) sorts as zero
+      }
+      sm_keys[i] = k;
+      sm_idx[i] = (uint16_t)i;
     }
-    sm_keys[i] = k;
-    sm_idx[i] = (uint16_t)i;
-  }
-  __syncthreads();
-  // bitonic sort of (key, position)
-  for (int kk = 2; kk <= pl.kpad; kk <<= 1) {
-    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-      for (int i = threadIdx.x; i < pl.kpad; i += blockDim.x) {
-        int ixj = i ^ jj;
-        if (ixj > i) {
+    __syncthreads();
+    // bitonic sort of (key, position): pair q of stage (kk, jj) is (i, i + jj) with i
+    // the q-th index whose bit jj is clear
+    for (int kk = 2; kk <= pl.kpad; kk <<= 1) {
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int q = threadIdx.x; q < half; q += blockDim.x) {
+          const int i = ((q & ~(jj - 1)) << 1) | (q & (jj - 1));
+          const int ixj = i | jj;
           u64 ki = sm_keys[i], kj = sm_keys[ixj];
           uint16_t ii = sm_idx[i], ij = sm_idx[ixj];
           bool gt = (ki > kj) || (ki == kj && ii > ij);
@@ -342,21 +345,50 @@ __global__ void k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
             sm_idx[ixj] = ii;
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
+    for (int s = threadIdx.x; s < len; s += blockDim.x) {
+      skey[base + s] = sm_keys[s];
+      srank[base + sm_idx[s]] = (uint16_t)s;
+    }
+    __syncthreads();  // before the next chunk overwrites the keys
   }
-  for (int s = threadIdx.x; s < len; s += blockDim.x) {
-    skey[base + s] = sm_keys[s];
-    srank[base + sm_idx[s]] = (uint16_t)s;
-  }
+}
+
+// Persistent grid: as many CTAs as fit on the GPU at once (items are dealt out statically,
+// so a CTA that had to wait for a free slot would serialise its share), never more than
+// the work items.
+template <typename K>
+static int resident_ctas(const SmoothPlan& pl, K kernel, int threads, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return pl.nsm * per_sm;
+}
+static int persistent_grid(const SmoothPlan& pl, int items, int resident) {
+  if (pl.nsm <= 0 || resident <= 0) return items;
+  return items < resident ? items : resident;
+}
+
+static int sort_threads(const SmoothPlan& pl) {
+  int th = pl.kpad / 2;
+  if (th > 1024) th = 1024;
+  if (th < 32) th = 32;
+  return th;
+}
+static size_t sort_smem(const SmoothPlan& pl) {
+  return (size_t)pl.kpad * (sizeof(u64) + sizeof(uint16_t));
 }
 
 void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
                        uint16_t* srank, Dirty d, cudaStream_t st) {
-  size_t smem = (size_t)pl.kpad * (sizeof(u64) + sizeof(uint16_t));
-  int th = pl.kpad >= 1024 ? 1024 : (pl.kpad < 64 ? 64 : pl.kpad);
-  k_chunk_sort<<<pl.nch, th, smem, st>>>(in, n, pl, skey, srank, d);
+  size_t smem = sort_smem(pl);
+  int th = sort_threads(pl);
+  k_chunk_sort<<<persistent_grid(pl, pl.nch, pl.res_sort), th, smem, st>>>(in, n, pl, skey, srank,
+                                                                          d);
 }
 
 // ============================================================================ running median
@@ -379,25 +411,24 @@ void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned lo
 
 __device__ __forceinline__ int wm_levels(int M) { return 32 - __clz(M - 1); }
 
-__global__ void __launch_bounds__(512, 2) k_median_wm(
-    const unsigned long long* __restrict__ skey, const uint16_t* __restrict__ srank,
-    long long n, SmoothPlan pl, SgOut o, Dirty d) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ int zeros[16];
+// One tile; returns the largest relative change of S_n among its outputs (conv_rtol).
+__device__ __forceinline__ double median_tile(const unsigned long long* __restrict__ skey,
+                                              const uint16_t* __restrict__ srank, long long n,
+                                              const SmoothPlan& pl, const SgOut& o, long long u,
+                                              unsigned char* sm_raw, int* zeros) {
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Kc = pl.Kc, M = 2 * Kc, LV = wm_levels(M);
   const int nwm = M >> 5, ws = nwm + 1;  // words per level (one zero word of padding)
-  const long long u = blockIdx.x;
   const int h = pl.W / 2;
   long long j_lo = (u - 1) * Kc + h, j_hi = u * Kc + h;
   if (j_lo < 0) j_lo = 0;
   if (j_hi > n) j_hi = n;
-  if (j_lo >= j_hi) return;
-  if (!d.any_between(u - 1, u)) return;  // no window of this tile changed
+  if (j_lo >= j_hi) return 0.0;
   const long long span = (u - 1) * (long long)Kc;
   int len0 = 0, len1 = 0;
   if (u >= 1) len0 = (n - span) < Kc ? (int)(n - span) : Kc;
   if (u < pl.nch) len1 = (n - span - Kc) < Kc ? (int)(n - span - Kc) : Kc;
+  double relmax = 0.0;
   u64* sk = (u64*)sm_raw;                                    // [M] sorted keys (step 1)
   uint16_t* seq1 = (uint16_t*)sm_raw;                        // [M] (steps 2-3, over sk)
   uint16_t* src = seq1 + M;                                  // [M] rank -> element
@@ -489,7 +520,6 @@ __global__ void __launch_bounds__(512, 2) k_median_wm(
   }
 
   // 3. selections
-  double relmax = 0.0;
   const int nout = (int)(j_hi - j_lo);
   for (int t = tid; t < nout; t += T) {
     const long long j = j_lo + t;
@@ -543,6 +573,22 @@ __global__ void __launch_bounds__(512, 2) k_median_wm(
     double rel = sg_store(o, j, v);
     relmax = rel > relmax ? rel : relmax;
   }
+  return relmax;
+}
+
+__global__ void __launch_bounds__(512, 2) k_median_wm(
+    const unsigned long long* __restrict__ skey, const uint16_t* __restrict__ srank,
+    long long n, SmoothPlan pl, SgOut o, Dirty d) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ int zeros[16];
+  double relmax = 0.0;
+  const int nitem = d.count(kListTile, pl.nch + 1);
+  for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+    // a tile whose windows changed
+    double r = median_tile(skey, srank, n, pl, o, d.item(kListTile, it), sm_raw, zeros);
+    relmax = r > relmax ? r : relmax;
+    __syncthreads();  // before the next tile overwrites shared memory
+  }
   if (o.rtol_on) warp_max_atomic((u64)__double_as_longlong(relmax), &o.rs->relchg_bits);
 }
 
@@ -562,8 +608,10 @@ size_t median_smem_bytes(int Kc) {
 
 void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
                            const SmoothPlan& pl, SgOut o, Dirty d, cudaStream_t st) {
-  k_median_wm<<<pl.nch + 1, median_threads(pl), median_smem_bytes(pl.Kc), st>>>(skey, srank, n,
-                                                                                pl, o, d);
+  int th = median_threads(pl);
+  size_t smem = median_smem_bytes(pl.Kc);
+  int bl = persistent_grid(pl, pl.nch + 1, pl.res_median);
+  k_median_wm<<<bl, th, smem, st>>>(skey, srank, n, pl, o, d);
 }
 
 // ============================================================================ window mean
@@ -580,16 +628,13 @@ __device__ __forceinline__ int sigma_from_max(u64 maxbits) {
   return 1136 - e;
 }
 
-__global__ void k_chunk_prefix(SpecIn in, long long n, SmoothPlan pl,
-                               unsigned long long* __restrict__ pre_lo,
-                               unsigned long long* __restrict__ pre_hi, int* __restrict__ sig,
-                               unsigned* __restrict__ uflow, double* __restrict__ x_out, Dirty d,
-                               int in_radius) {
-  __shared__ U128 warp_tot[32];
-  __shared__ u64 warp_max[32];
-  __shared__ int any_uf;
-  const int b = blockIdx.x;
-  if (!d.any(b, in_radius)) return;  // unchanged input: prefix sums still hold
+// Prefix sums of chunk b.
+__device__ __forceinline__ void chunk_prefix(const SpecIn& in, long long n, const SmoothPlan& pl,
+                                             unsigned long long* __restrict__ pre_lo,
+                                             unsigned long long* __restrict__ pre_hi,
+                                             int* __restrict__ sig, unsigned* __restrict__ uflow,
+                                             double* __restrict__ x_out, int b, U128* warp_tot,
+                                             u64* warp_max, int& any_uf) {
   const long long base = (long long)b * pl.Kc;
   const int len = (int)((n - base) < pl.Kc ? (n - base) : pl.Kc);
   const int per = (pl.Kc + blockDim.x - 1) / blockDim.x;
@@ -679,12 +724,30 @@ __global__ void k_chunk_prefix(SpecIn in, long long n, SmoothPlan pl,
   }
 }
 
+__global__ void k_chunk_prefix(SpecIn in, long long n, SmoothPlan pl,
+                               unsigned long long* __restrict__ pre_lo,
+                               unsigned long long* __restrict__ pre_hi, int* __restrict__ sig,
+                               unsigned* __restrict__ uflow, double* __restrict__ x_out, Dirty d,
+                               int in_radius) {
+  __shared__ U128 warp_tot[32];
+  __shared__ u64 warp_max[32];
+  __shared__ int any_uf;
+  // chunks whose input changed (a chunk within in_radius of them is dirty)
+  const int list = kListR0 + in_radius;
+  const int nitem = d.count(list, pl.nch);
+  for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+    chunk_prefix(in, n, pl, pre_lo, pre_hi, sig, uflow, x_out, d.item(list, it), warp_tot,
+                 warp_max, any_uf);
+    __syncthreads();
+  }
+}
+
 void launch_chunk_prefix(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* pre_lo,
                          unsigned long long* pre_hi, int* sig, unsigned* uflow, double* x_out,
                          Dirty d, int in_radius, cudaStream_t st) {
   int th = pl.Kc < 1024 ? pl.Kc : 1024;  // at most 8 values per thread
-  k_chunk_prefix<<<pl.nch, th, 0, st>>>(in, n, pl, pre_lo, pre_hi, sig, uflow, x_out, d,
-                                        in_radius);
+  int bl = persistent_grid(pl, pl.nch, pl.res_prefix);
+  k_chunk_prefix<<<bl, th, 0, st>>>(in, n, pl, pre_lo, pre_hi, sig, uflow, x_out, d, in_radius);
 }
 
 // Sum of x[a .. e] inside one chunk as a double (a, e in the chunk, a <= e).
@@ -714,25 +777,32 @@ __global__ void k_window_mean(const double* __restrict__ x, long long n, SmoothP
                               const unsigned long long* __restrict__ pre_hi,
                               const int* __restrict__ sig, const unsigned* __restrict__ uflow,
                               SgOut o, Dirty d, int out_radius) {
-  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double relmax = 0.0;
-  if (j < n && d.any(j / pl.Kc, out_radius)) {
-    const int h = pl.W / 2;
-    long long s = j - h > 0 ? j - h : 0;
-    long long e = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
-    long long cs = s / pl.Kc, ce = e / pl.Kc;
-    long long cnt = e - s + 1;
-    double sum;
-    if (cs == ce) {
-      sum = part_sum(x, cs * pl.Kc, s, e, pre_lo, pre_hi, sig[cs], uflow[cs]);
-    } else {
-      long long last = cs * pl.Kc + pl.Kc - 1;
-      double s1 = part_sum(x, cs * pl.Kc, s, last, pre_lo, pre_hi, sig[cs], uflow[cs]);
-      double s2 = part_sum(x, ce * pl.Kc, ce * pl.Kc, e, pre_lo, pre_hi, sig[ce], uflow[ce]);
-      sum = __dadd_rn(s1, s2);
+  const int h = pl.W / 2;
+  // output chunks with a dirty chunk within out_radius
+  const int list = kListR0 + out_radius;
+  const int nitem = d.count(list, pl.nch);
+  for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+    const long long b = d.item(list, it);
+    const long long jend = (b + 1) * pl.Kc < n ? (b + 1) * pl.Kc : n;
+    for (long long j = b * pl.Kc + threadIdx.x; j < jend; j += blockDim.x) {
+      long long s = j - h > 0 ? j - h : 0;
+      long long e = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
+      long long cs = s / pl.Kc, ce = e / pl.Kc;
+      long long cnt = e - s + 1;
+      double sum;
+      if (cs == ce) {
+        sum = part_sum(x, cs * pl.Kc, s, e, pre_lo, pre_hi, sig[cs], uflow[cs]);
+      } else {
+        long long last = cs * pl.Kc + pl.Kc - 1;
+        double s1 = part_sum(x, cs * pl.Kc, s, last, pre_lo, pre_hi, sig[cs], uflow[cs]);
+        double s2 = part_sum(x, ce * pl.Kc, ce * pl.Kc, e, pre_lo, pre_hi, sig[ce], uflow[ce]);
+        sum = __dadd_rn(s1, s2);
+      }
+      double v = (cnt == pl.W) ? __dmul_rn(sum, 1.0 / (double)pl.W) : __ddiv_rn(sum, (double)cnt);
+      double rel = sg_store(o, j, v);
+      relmax = rel > relmax ? rel : relmax;
     }
-    double v = (cnt == pl.W) ? __dmul_rn(sum, 1.0 / (double)pl.W) : __ddiv_rn(sum, (double)cnt);
-    relmax = sg_store(o, j, v);
   }
   if (o.rtol_on) warp_max_atomic((u64)__double_as_longlong(relmax), &o.rs->relchg_bits);
 }
@@ -742,8 +812,8 @@ void launch_window_mean(const double* x, long long n, const SmoothPlan& pl,
                         const int* sig, const unsigned* uflow, SgOut o, Dirty d, int out_radius,
                         cudaStream_t st) {
   int th = 256;
-  k_window_mean<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(x, n, pl, pre_lo, pre_hi, sig, uflow,
-                                                               o, d, out_radius);
+  int bl = persistent_grid(pl, pl.nch, pl.res_mean);
+  k_window_mean<<<bl, th, 0, st>>>(x, n, pl, pre_lo, pre_hi, sig, uflow, o, d, out_radius);
 }
 
 // ============================================================================ SNR + resolve
@@ -784,16 +854,21 @@ __device__ double rho2_exact(const Grid& g, const Tables& tb, const double* __re
   return __dmul_rn(4.0, acc);
 }
 
+// One warp per candidate: the lanes share the bins of its sweep (loud high-frequency
+// sources sweep hundreds of bins, and a thread per candidate would leave the launch
+// waiting on the longest one), for the screen sum and for the removal.
 __global__ void __launch_bounds__(256) k_snr_resolve(
     Cands cd, Grid g, Tables tb, const double* __restrict__ Sg, const float* __restrict__ inv_f,
     double th2, double rtol, int mode, unsigned char* __restrict__ resolved,
     unsigned long long* __restrict__ acc, RunState* rs, Dirty d, int Kc, int sg_radius) {
   if (rs->final_pass || rtol_stop(rs, rtol)) return;
   const long long nlive = (long long)rs->nlive;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const float th2f = (float)th2;
   unsigned local_new = 0, local_exact = 0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nlive; c += stride) {
+  for (long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; c < nlive;
+       c += nwarps) {
     if (cd.res[c]) continue;
     const int ka = cd.ka[c];
     const int nbin = cd.nbin[c];
@@ -812,7 +887,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
     float r2 = 0.0f;
     int kcount = 0;
     if (nbin == 1) {
-      if (ka >= 0 && ka < g.nb) {
+      if (lane == 0 && ka >= 0 && ka < g.nb) {
         r2 = __fmul_rn(__fmul_rn(a2f, tb.Gf[ka]), inv_f[ka]);
         kcount = 1;
       }
@@ -820,7 +895,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
       const float flo = cd.flo[c], fhi = __fadd_rn(flo, cd.len[c]), invlen = 1.0f / cd.len[c];
       int t0 = ka < 0 ? -ka : 0;
       int t1 = (long long)ka + nbin > g.nb ? (int)(g.nb - ka) : nbin;
-      for (int t = t0; t < t1; ++t) {
+      for (int t = t0 + lane; t < t1; t += 32) {
         float a = fmaxf(flo, (float)t - 0.5f);
         float b = fminf(fhi, (float)t + 0.5f);
         if (b > a) {
@@ -830,6 +905,11 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
           ++kcount;
         }
       }
+    }
+    // butterfly sums: every lane ends with the same values
+    for (int o = 16; o > 0; o >>= 1) {
+      r2 = __fadd_rn(r2, __shfl_xor_sync(0xFFFFFFFFu, r2, o));
+      kcount += __shfl_xor_sync(0xFFFFFFFFu, kcount, o);
     }
     bool resolve;
     if (mode == 1) {
@@ -841,14 +921,21 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
       } else if (mode == 0 && r2 < th2f * (1.0f - m)) {
         resolve = false;
       } else {
-        ++local_exact;
-        resolve = rho2_exact(g, tb, Sg, cd.a2[c], cd.lo[c], cd.hi[c]) > th2;
+        // the oracle's order of summation, on one lane
+        int ex = 0;
+        if (lane == 0) {
+          ++local_exact;
+          ex = rho2_exact(g, tb, Sg, cd.a2[c], cd.lo[c], cd.hi[c]) > th2;
+        }
+        resolve = __shfl_sync(0xFFFFFFFFu, ex, 0) != 0;
       }
     }
     if (resolve) {
-      cd.res[c] = 1;
-      resolved[cd.src[c]] = 1;
-      ++local_new;
+      if (lane == 0) {
+        cd.res[c] = 1;
+        resolved[cd.src[c]] = 1;
+        ++local_new;
+      }
       // remove exactly the parts the prepass deposited
       Sweep sw;
       sw.lo = cd.lo[c];
@@ -858,14 +945,14 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
       double a2 = cd.a2[c];
       if (sw.ka == sw.kb) {
         long long j = sw.ka - g.k_lo;
-        if (j >= 0 && j < g.nb) {
+        if (lane == 0 && j >= 0 && j < g.nb) {
           remove_q(acc, j, __dmul_rn(a2, tb.gq[j]));
           d.mark_next(j / Kc);
         }
       } else {
         long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
         long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
-        for (long long k = k0; k <= k1; ++k) {
+        for (long long k = k0 + lane; k <= k1; k += 32) {
           double w = sweep_weight(sw, k);
           if (w > 0.0) {
             long long j = k - g.k_lo;
@@ -876,11 +963,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
       }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    local_new += __shfl_xor_sync(0xFFFFFFFFu, local_new, o);
-    local_exact += __shfl_xor_sync(0xFFFFFFFFu, local_exact, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     if (local_new) atomicAdd(&rs->count_new, (unsigned long long)local_new);
     if (local_exact) atomicAdd(&rs->nexact, (unsigned long long)local_exact);
   }
@@ -891,7 +974,7 @@ void launch_snr_resolve(Cands cd, long long ncap, const Grid& g, const Tables& t
                         unsigned char* resolved, unsigned long long* acc, RunState* rs,
                         Dirty d, int Kc, int sg_radius, int nsm, cudaStream_t st) {
   int th = 256;
-  long long want = (ncap + th - 1) / th;
+  long long want = (ncap * 32 + th - 1) / th;
   long long cap = (long long)nsm * 8;
   int bl = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
   k_snr_resolve<<<bl, th, 0, st>>>(cd, g, tb, Sg, inv_f, th2, rtol, mode, resolved, acc, rs, d, Kc,
@@ -900,14 +983,48 @@ void launch_snr_resolve(Cands cd, long long ncap, const Grid& g, const Tables& t
 
 // ============================================================================ loop control
 
+// Work lists from the dirty set `cur` (one CTA).  Their order depends on the atomics,
+// which is harmless: every item is computed on its own.
+__device__ void build_lists_cta(const unsigned char* __restrict__ cur, int nch,
+                                int* __restrict__ lists, int* __restrict__ counts) {
+  __shared__ int cnt[kNumLists];
+  if (threadIdx.x < kNumLists) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const size_t stride = (size_t)nch + 1;
+  for (int b = threadIdx.x; b <= nch; b += blockDim.x) {
+    auto at = [&](int i) { return i >= 0 && i < nch && cur[i] != 0; };
+    const bool d0 = at(b), dm1 = at(b - 1);
+    if (b < nch) {
+      const bool r0 = d0, r1 = r0 || dm1 || at(b + 1), r2 = r1 || at(b - 2) || at(b + 2);
+      if (r0) lists[kListR0 * stride + atomicAdd(&cnt[kListR0], 1)] = b;
+      if (r1) lists[kListR1 * stride + atomicAdd(&cnt[kListR1], 1)] = b;
+      if (r2) lists[kListR2 * stride + atomicAdd(&cnt[kListR2], 1)] = b;
+    }
+    if (d0 || dm1) lists[kListTile * stride + atomicAdd(&cnt[kListTile], 1)] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNumLists) counts[threadIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_build_lists(Dirty d, int* lists, int* counts) {
+  build_lists_cta(d.base + (size_t)(d.rs->iter & 1) * d.nch, d.nch, lists, counts);
+}
+
+void launch_build_lists(Dirty d, int* lists, int* counts, cudaStream_t st) {
+  k_build_lists<<<1, 1024, 0, st>>>(d, lists, counts);
+}
+
 __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist,
                           unsigned long long cond_handle, int use_cond, unsigned char* dirty,
-                          int nch) {
-  // every thread clears part of the dirty set this iteration read (rs->iter still holds
-  // the previous count); the new set was marked by this iteration's removals
+                          int nch, int* lists, int* counts) {
+  // every thread reads the count before thread 0 advances it (after the barriers below)
+  const int it0 = rs->iter;
   if (dirty) {
-    unsigned char* cur = dirty + (size_t)(rs->iter & 1) * nch;
+    // clear the set this iteration read; the removals of this iteration marked the other
+    // one, which the next iteration reads through its work lists
+    unsigned char* cur = dirty + (size_t)(it0 & 1) * nch;
     for (int i = threadIdx.x; i < nch; i += blockDim.x) cur[i] = 0;
+    build_lists_cta(dirty + (size_t)((it0 + 1) & 1) * nch, nch, lists, counts);
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -916,7 +1033,7 @@ __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist
     go = 0u;
   } else {
     bool rstop = rtol_stop(rs, rtol);
-    int it = rs->iter + 1;
+    int it = it0 + 1;
     rs->iter = it;
     unsigned long long nn = rs->count_new;
     if (new_hist && it <= max_iter) new_hist[it - 1] = (int)nn;
@@ -937,8 +1054,18 @@ __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist
 
 void launch_control(RunState* rs, int max_iter, double rtol, int* new_hist,
                     unsigned long long cond_handle, int use_cond, unsigned char* dirty, int nch,
-                    cudaStream_t st) {
-  k_control<<<1, 256, 0, st>>>(rs, max_iter, rtol, new_hist, cond_handle, use_cond, dirty, nch);
+                    int* lists, int* counts, cudaStream_t st) {
+  k_control<<<1, 1024, 0, st>>>(rs, max_iter, rtol, new_hist, cond_handle, use_cond, dirty, nch,
+                                lists, counts);
+}
+
+void plan_grids(SmoothPlan& pl) {
+  pl.res_sort = pl.res_median = pl.res_prefix = pl.res_mean = 0;
+  if (pl.nsm <= 0) return;
+  pl.res_sort = resident_ctas(pl, k_chunk_sort, sort_threads(pl), sort_smem(pl));
+  pl.res_median = resident_ctas(pl, k_median_wm, median_threads(pl), median_smem_bytes(pl.Kc));
+  pl.res_prefix = resident_ctas(pl, k_chunk_prefix, pl.Kc < 1024 ? pl.Kc : 1024, 0);
+  pl.res_mean = resident_ctas(pl, k_window_mean, 256, 0);
 }
 
 void configure_kernels() {

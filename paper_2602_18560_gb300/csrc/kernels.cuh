@@ -62,6 +62,8 @@ struct SmoothPlan {
   int nw;       // 32-bit words per chunk bitset (Kc / 32)
   int nch;      // chunks
   int kpad;     // power of two >= Kc (sort width)
+  int nsm;      // SMs for persistent grids (0: one CTA per work item)
+  int res_sort, res_median, res_prefix, res_mean;  // CTAs resident at once (plan_grids)
 };
 
 // Source of an estimator's input: the run's fixed-point spectrum (P_k = S_k Q_k 2^-96) or
@@ -76,10 +78,19 @@ struct SpecIn {
 // entries alternate: iteration i reads set (i-1) & 1 and the removals of iteration i mark
 // set i & 1 (rs->iter = i - 1 while iteration i runs).  A null base means every chunk
 // has changed (first estimate, or an estimate of a given spectrum).
+//
+// From the set an iteration reads, the loop control builds work lists (ascending order is
+// not kept): the chunks with a changed chunk within 0, 1 or 2 of them, and the median
+// tiles u whose chunks u-1 or u changed.  The chunk kernels run persistent grids over
+// them, so an iteration that changed a few chunks launches a few busy CTAs.
+enum { kListR0 = 0, kListR1 = 1, kListR2 = 2, kListTile = 3, kNumLists = 4 };
+
 struct Dirty {
   unsigned char* base;
   int nch;
   const RunState* rs;
+  const int* lists;   // [kNumLists][nch + 1], null when base is null
+  const int* counts;  // [kNumLists]
   __device__ __forceinline__ bool any(long long c, int radius) const {
     return any_between(c - radius, c + radius);
   }
@@ -96,6 +107,13 @@ struct Dirty {
   __device__ __forceinline__ void mark_next(long long c) const {
     if (base) base[(size_t)((rs->iter + 1) & 1) * nch + c] = 1;
   }
+  // items of work list `which` (all `all` of them when nothing is tracked)
+  __device__ __forceinline__ int count(int which, int all) const {
+    return lists ? counts[which] : all;
+  }
+  __device__ __forceinline__ int item(int which, int i) const {
+    return lists ? lists[(size_t)which * (nch + 1) + i] : i;
+  }
 };
 
 // Output epilogue of the kernel that writes S_gal.
@@ -110,6 +128,9 @@ struct SgOut {
 
 // Raise the dynamic shared-memory limits of the kernels that need more than 48 KB.
 void configure_kernels();
+
+// Persistent-grid sizes of the chunk kernels for pl (after configure_kernels; pl.nsm set).
+void plan_grids(SmoothPlan& pl);
 
 void launch_tables(const Grid& g, int tdi2, double* S, double* R, double* gq, float* Gf,
                    float* invSf, cudaStream_t st);
@@ -155,10 +176,13 @@ void launch_snr_resolve(Cands cd, long long ncap, const Grid& g, const Tables& t
                         unsigned char* resolved, unsigned long long* acc, RunState* rs,
                         Dirty d, int Kc, int sg_radius, int nsm, cudaStream_t st);
 
-// Loop control; it also clears the dirty set the finished iteration read.
+// Work lists of the set the next iteration reads (set rs->iter & 1).
+void launch_build_lists(Dirty d, int* lists, int* counts, cudaStream_t st);
 
+// Loop control; it also clears the dirty set the finished iteration read and builds the
+// work lists of the next one.
 void launch_control(RunState* rs, int max_iter, double rtol, int* new_hist,
                     unsigned long long cond_handle, int use_cond, unsigned char* dirty, int nch,
-                    cudaStream_t st);
+                    int* lists, int* counts, cudaStream_t st);
 
 }  // namespace gbsub

@@ -101,6 +101,8 @@ extern "C" int sub_running_mean_noalloc(const double* x, double* out, int64_t n,
   pl.nw = pl.Kc / 32;
   pl.nch = (int)((n + pl.Kc - 1) / pl.Kc);
   pl.kpad = 0;
+  pl.nsm = 0;  // one CTA per chunk
+  pl.res_sort = pl.res_median = pl.res_prefix = pl.res_mean = 0;
   unsigned long long* pre_lo = base;
   unsigned long long* pre_hi = base + kCells;
   int* sig = (int*)(base + 2 * kCells);
@@ -121,6 +123,8 @@ extern "C" int sub_running_mean_noalloc(const double* x, double* out, int64_t n,
   all.base = nullptr;
   all.nch = pl.nch;
   all.rs = nullptr;
+  all.lists = nullptr;
+  all.counts = nullptr;
   launch_chunk_prefix(in, n, pl, pre_lo, pre_hi, sig, uflow, nullptr, all, 0, st);
   launch_window_mean(x, n, pl, pre_lo, pre_hi, sig, uflow, o, all, 0, st);
   e = cudaGetLastError();
