@@ -42,6 +42,7 @@ struct sub_ctx {
   float *Gf = nullptr, *invSf = nullptr;
   // spectrum and smoothing buffers
   unsigned long long* acc = nullptr;  // 4 words per bin
+  AccReplicas rep = {nullptr, 0};     // private copies of the first bins (catalog pass)
   double *P = nullptr, *M = nullptr, *Sg = nullptr;
   double* estimate_in = nullptr;  // input copy of sub_estimate
   float* inv_f = nullptr;
@@ -189,7 +190,7 @@ static SmoothPlan make_plan(int W, int64_t n) {
   pl.Kc = kc;
   pl.nw = kc / 32;
   pl.nch = (int)((n + kc - 1) / kc);
-  int kp = 1;
+  int kp = 64;  // sort width: a power of two >= Kc, and two elements for each of >= 32 threads
   while (kp < kc) kp <<= 1;
   pl.kpad = kp;
   return pl;
@@ -253,6 +254,7 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
       {(void**)&c->S, (size_t)n * 8}, {(void**)&c->R, (size_t)n * 8}, {(void**)&c->gq, (size_t)n * 8},
       {(void**)&c->Gf, (size_t)n * 4}, {(void**)&c->invSf, (size_t)n * 4},
       {(void**)&c->acc, (size_t)n * 32}, {(void**)&c->inv_f, (size_t)n * 4},
+      {(void**)&c->rep.w, (size_t)kAccReplicas * (n < kAccReplicaBins ? n : kAccReplicaBins) * 16},
       {(void**)&c->P, (size_t)n * 8}, {(void**)&c->Sg, (size_t)n * 8},
       {(void**)&c->sig, (size_t)pl.nch * 4}, {(void**)&c->estimate_in, (size_t)n * 8},
       {(void**)&c->dirty, (size_t)pl.nch * 2},
@@ -266,6 +268,7 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
     rc = dalloc(c, w.p, w.b);
     if (rc) return fail(rc);
   }
+  c->rep.nbins = n < kAccReplicaBins ? n : kAccReplicaBins;
   if (p->estimator != SUB_MEAN) {
     rc = dalloc(c, (void**)&c->skey, (size_t)ncell * 8);
     if (!rc) rc = dalloc(c, (void**)&c->srank, (size_t)ncell * 2);
@@ -391,6 +394,7 @@ static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
   const int64_t n = c->grid.nb;
   cudaError_t e;
   if ((e = cudaMemsetAsync(c->acc, 0, (size_t)n * 32, st))) return e;
+  if ((e = cudaMemsetAsync(c->rep.w, 0, (size_t)kAccReplicas * c->rep.nbins * 16, st))) return e;
   if ((e = cudaMemsetAsync(c->rs, 0, sizeof(RunState), st))) return e;
   // the first iteration reads set 0: every chunk is new
   if ((e = cudaMemsetAsync(c->dirty, 1, (size_t)c->plan.nch, st))) return e;
@@ -403,7 +407,7 @@ static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
   {
     KTimer t(c, st, SUB_K_PREPASS);
     launch_prepass(c->A, c->f, c->fdot, c->N, c->grid, tables_of(c), thr_kappa_of(c),
-                   thr_live_of(c), c->acc, c->cd, c->rs, c->nsm, st);
+                   thr_live_of(c), c->acc, c->rep, c->cd, c->rs, c->nsm, st);
   }
   return cudaGetLastError();
 }
@@ -544,7 +548,10 @@ static int fill_stats(sub_ctx* c, sub_stats* st) {
   CU(cudaStreamSynchronize(c->stream), c);
   const RunState& r = *c->h_rs;
   int status = SUB_OK;
-  if (r.err & ERR_RANGE) {
+  if (r.err & ERR_TIMEOUT) {
+    status = SUB_ETIMEOUT;
+    set_err(c, "a staged copy of the catalog did not arrive in time; the run was abandoned");
+  } else if (r.err & ERR_RANGE) {
     status = SUB_ERANGE;
     set_err(c, "a deposited power exceeded the fixed-point range (P/S_instr >= 2^31 in one bin)");
   } else if (!r.converged) {

@@ -23,7 +23,7 @@ constexpr double kQLimit = 170141183460469231731687303715884105728.0;          /
 constexpr int kMaxWindow = 8192;
 
 // Error bits raised on the device.
-enum : unsigned { ERR_RANGE = 1u, ERR_WINDOW = 2u, ERR_CAND = 4u };
+enum : unsigned { ERR_RANGE = 1u, ERR_WINDOW = 2u, ERR_CAND = 4u, ERR_TIMEOUT = 8u };
 
 // ---------------------------------------------------------------- 128-bit unsigned
 struct U128 {

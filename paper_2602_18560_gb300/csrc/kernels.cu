@@ -135,6 +135,40 @@ void launch_power_out(const unsigned long long* acc, const double* S, long long 
 
 // ============================================================================ prepass
 
+// The catalog is dominated by the low-frequency end of the band (the number of sources
+// falls steeply with f), so the 64-bit atomics of the deposits pile up on the cache lines
+// of the first bins: an L2 line takes one atomic at a time.  The first rep.nbins bins
+// therefore have kAccReplicas private copies (words 1 and 2 of every bin), a source
+// picking one by its index; a fold adds them into the spectrum after the pass.  Integer
+// sums, so the result does not depend on the split.
+__device__ __forceinline__ void deposit_rep(AccReplicas rep, long long j, int r, double q,
+                                            unsigned* err) {
+  if ((u64)__double_as_longlong(q) >= 0x47E0000000000000ull) {
+    atomicOr(err, ERR_RANGE);
+    return;
+  }
+  u64 c0, c1, c2;
+  q_parts(q, &c0, &c1, &c2);
+  u64* a = rep.w + 2 * ((size_t)r * rep.nbins + j);
+  if (c1) atomicAdd(a + 0, c1);
+  if (c2) atomicAdd(a + 1, c2);
+}
+
+__global__ void k_fold_replicas(unsigned long long* __restrict__ acc, AccReplicas rep) {
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= rep.nbins) return;
+  u64 s1 = 0, s2 = 0;
+#pragma unroll
+  for (int r = 0; r < kAccReplicas; ++r) {
+    const ulonglong2 v = reinterpret_cast<const ulonglong2*>(rep.w)[(size_t)r * rep.nbins + j];
+    s1 += v.x;
+    s2 += v.y;
+  }
+  acc[4 * j + 1] += s1;
+  acc[4 * j + 2] += s2;
+}
+
+
 // FP64 path of the catalog pass: the sweep of one source, its pieces deposited; returns
 // the sum of its contributions.  Kept out of line so that none of it is speculated into
 // the common path.
@@ -182,80 +216,250 @@ __device__ __noinline__ void emit_candidate(Cands cd, long long c, long long s, 
   cd.res[c] = 0;
 }
 
-__global__ void __launch_bounds__(256) k_prepass(
-    const double* __restrict__ A, const double* __restrict__ f, const double* __restrict__ fdot,
-    long long N, Grid g, Tables tb, double thr_kappa, double thr_live,
-    unsigned long long* __restrict__ acc, Cands cd, RunState* rs) {
+// The decision for one source once r (its rho_0^2 / 4 in units of 2^-96) is known: count
+// it among the paper's candidates, and keep it when it can still be resolved.
+__device__ __forceinline__ void prepass_decide(double r, u64 tk_bits, u64 tl_bits, bool valid,
+                                               long long s, double a2, double fs, double fds,
+                                               const Grid& g, Cands& cd, RunState* rs,
+                                               unsigned long long& nkappa) {
   const int lane = threadIdx.x & 31;
-  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) - lane;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  // thresholds on r >= 0 compared as the integer bits of non-negative doubles
-  const u64 tk_bits = (u64)__double_as_longlong(thr_kappa);
-  const u64 tl_bits = (u64)__double_as_longlong(thr_live);
-  unsigned long long nkappa = 0;
-  for (long long base = warp0; base < N; base += stride) {
-    long long s = base + lane;
-    bool live = false;
-    double a2 = 0.0, fs = 0.0, fds = 0.0;
-    if (s < N) {
+  u64 rb = (u64)__double_as_longlong(r);
+  bool live = false;
+  if (valid) {
+    if (rb >= tk_bits) ++nkappa;
+    live = (rb > tl_bits) && (rb >= tk_bits);
+  }
+  unsigned m = __ballot_sync(0xFFFFFFFFu, live);
+  if (m) {
+    unsigned long long b0 = 0;
+    int leader = __ffs(m) - 1;
+    if (lane == leader) b0 = atomicAdd(&rs->nlive, (unsigned long long)__popc(m));
+    b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
+    if (live) {
+      long long c = (long long)b0 + __popc(m & ((1u << lane) - 1u));
+      emit_candidate(cd, c, s, a2, fs, fds, g);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- TMA staging
+// The catalog streams through shared memory: one thread issues bulk asynchronous copies
+// (cp.async.bulk, completion counted in bytes on an mbarrier) of whole tiles of A, f and
+// fdot a few tiles ahead, so no thread waits on HBM for its sources.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Wait for phase `parity` of the barrier; false after about a second of polling.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const uint32_t a = smem_addr(bar);
+  for (int i = 0; i < (1 << 20); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    __nanosleep(1000);
+  }
+  return false;
+}
+
+// Sources whose sweep the FP32 bound cannot keep in one bin go through the FP64 path.
+// They are rare (well under 1%), but one such lane would hold its whole warp on the slow
+// FP64 pipe, so each CTA queues them in shared memory and runs them a full CTA at a time.
+constexpr int kPrepassThreads = 256;
+constexpr int kPreTile = 512;                          // sources per staged tile
+constexpr int kPreStages = 3;                          // tiles in flight per CTA
+constexpr int kPrePer = kPreTile / kPrepassThreads;    // sources per thread per tile
+constexpr int kSlowCap = kPrepassThreads + kPreTile;   // queue entries (drained at >= 256)
+constexpr size_t kPrepassSmem = (size_t)kPreStages * kPreTile * 3 * sizeof(double);
+
+__device__ __forceinline__ void prepass_drain(const double* __restrict__ A,
+                                              const double* __restrict__ f,
+                                              const double* __restrict__ fdot, const Grid& g,
+                                              const Tables& tb, u64 tk_bits, u64 tl_bits,
+                                              unsigned long long* __restrict__ acc, Cands& cd,
+                                              RunState* rs, const long long* q, int cnt,
+                                              unsigned long long& nkappa) {
+  // every thread takes entries tid, tid + blockDim.x, ...
+  for (int base = 0; base < cnt; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const bool valid = i < cnt;
+    long long s = valid ? q[i] : 0;
+    double a2 = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
+    if (valid) {
       double a = A[s];
       fs = f[s];
       fds = fdot[s];
       a2 = __dmul_rn(a, a);
-      // Common case without FP64: bin of f T + 1/2 exactly, and an FP32 bound on the sweep
-      // fdot T^2 proving that f T + fdot T^2 + 1/2 stays in the same bin (the FP64 path
-      // takes every case the bound cannot settle).
-      long long k0;
-      unsigned fr24;
-      int fb;
-      bool single = false;
-      if (ft_bin(fs, g.mT, g.eT, &k0, &fr24, &fb)) {
-        float du = __fmul_rn(dbl_to_f32_signed(fds), g.T2f);
-        float phi = __fmul_rn((float)fr24, 5.9604644775390625e-8f);  // 2^-24
-        float m = __fadd_rn(9.5367431640625e-7f, __fmul_rn(4e-7f, fabsf(du)));  // 2^-20 + ...
-        float x = __fadd_rn(phi, du);
-        single = (x >= m) && (x < __fsub_rn(1.0f, m));
-      }
-      double r = 0.0;  // sum of q: rho_0^2 = 4 r 2^-96
-      if (single) {
-        long long j = k0 - g.k_lo;
-        if (j >= 0 && j < g.nb) {
-          double q = __dmul_rn(a2, tb.gq[j]);
-          deposit_q(acc, j, q, &rs->err);
-          r = q;
-        }
-      } else {
-        r = prepass_slow(a2, fs, fds, g, tb, acc, &rs->err);
-      }
-      u64 rb = (u64)__double_as_longlong(r);
-      if (rb >= tk_bits) ++nkappa;
-      live = (rb > tl_bits) && (rb >= tk_bits);
+      r = prepass_slow(a2, fs, fds, g, tb, acc, &rs->err);
     }
-    unsigned m = __ballot_sync(0xFFFFFFFFu, live);
-    if (m) {
-      unsigned long long b0 = 0;
-      int leader = __ffs(m) - 1;
-      if (lane == leader) b0 = atomicAdd(&rs->nlive, (unsigned long long)__popc(m));
-      b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
-      if (live) {
-        long long c = (long long)b0 + __popc(m & ((1u << lane) - 1u));
-        emit_candidate(cd, c, s, a2, fs, fds, g);
+    prepass_decide(r, tk_bits, tl_bits, valid, s, a2, fs, fds, g, cd, rs, nkappa);
+  }
+}
+
+__global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
+    const double* __restrict__ A, const double* __restrict__ f, const double* __restrict__ fdot,
+    long long N, Grid g, Tables tb, double thr_kappa, double thr_live,
+    unsigned long long* __restrict__ acc, AccReplicas rep, Cands cd, RunState* rs) {
+  extern __shared__ __align__(128) double pre_tiles[];  // [stage][A | f | fdot][kPreTile]
+  __shared__ __align__(8) uint64_t bar[kPreStages];
+  __shared__ long long stage_tile[kPreStages];  // tile held by each stage
+  __shared__ long long slow_q[kSlowCap];
+  __shared__ int slow_n;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  // thresholds on r >= 0 compared as the integer bits of non-negative doubles
+  const u64 tk_bits = (u64)__double_as_longlong(thr_kappa);
+  const u64 tl_bits = (u64)__double_as_longlong(thr_live);
+  unsigned long long nkappa = 0;
+  const long long ntiles = (N + kPreTile - 1) / kPreTile;
+  const long long nfull = N / kPreTile;  // full tiles come through TMA, the ragged one directly
+  // Thread 0 takes the next tile from the global counter (CTAs that run faster take more
+  // tiles) and, when it is full, starts its copy into `stage`.
+  auto fetch = [&](int stage) {
+    const long long t = (long long)atomicAdd(&rs->next_tile, 1ull);
+    stage_tile[stage] = t;
+    if (t < nfull) {
+      double* d = pre_tiles + (size_t)stage * 3 * kPreTile;
+      const size_t off = (size_t)t * kPreTile;
+      mbar_expect_tx(&bar[stage], 3u * kPreTile * (unsigned)sizeof(double));
+      bulk_g2s(d, A + off, kPreTile * sizeof(double), &bar[stage]);
+      bulk_g2s(d + kPreTile, f + off, kPreTile * sizeof(double), &bar[stage]);
+      bulk_g2s(d + 2 * kPreTile, fdot + off, kPreTile * sizeof(double), &bar[stage]);
+    }
+  };
+  if (tid == 0) {
+    for (int k = 0; k < kPreStages; ++k) mbar_init(&bar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    slow_n = 0;
+    for (int k = 0; k < kPreStages; ++k) fetch(k);
+  }
+  __syncthreads();
+  bool failed = false;
+  long long i = 0;
+  for (;; ++i) {
+    const int stage = (int)(i % kPreStages);
+    // written by thread 0 at least one barrier ago; tiles only grow, so once a stage holds
+    // a tile past the end no copy is outstanding in any stage
+    const long long t = stage_tile[stage];
+    if (t >= ntiles) break;
+    const bool staged = t < nfull;
+    bool ok = true;
+    if (staged) ok = mbar_wait(&bar[stage], (unsigned)((i / kPreStages) & 1));
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const double* sA = pre_tiles + (size_t)stage * 3 * kPreTile;
+    const double* sF = sA + kPreTile;
+    const double* sD = sF + kPreTile;
+#pragma unroll
+    for (int k = 0; k < kPrePer; ++k) {
+      const int idx = tid + k * kPrepassThreads;
+      const long long s = t * kPreTile + idx;
+      bool valid = false, slow = false;
+      double a2 = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
+      if (s < N) {
+        double a = staged ? sA[idx] : A[s];
+        fs = staged ? sF[idx] : f[s];
+        fds = staged ? sD[idx] : fdot[s];
+        a2 = __dmul_rn(a, a);
+        // Common case without FP64: bin of f T + 1/2 exactly, and an FP32 bound on the
+        // sweep fdot T^2 proving that f T + fdot T^2 + 1/2 stays in the same bin (the FP64
+        // path takes every case the bound cannot settle).
+        long long k0;
+        unsigned fr24;
+        int fb;
+        bool single = false;
+        if (ft_bin(fs, g.mT, g.eT, &k0, &fr24, &fb)) {
+          float du = __fmul_rn(dbl_to_f32_signed(fds), g.T2f);
+          float phi = __fmul_rn((float)fr24, 5.9604644775390625e-8f);  // 2^-24
+          float m = __fadd_rn(9.5367431640625e-7f, __fmul_rn(4e-7f, fabsf(du)));  // 2^-20 + ...
+          float x = __fadd_rn(phi, du);
+          single = (x >= m) && (x < __fsub_rn(1.0f, m));
+        }
+        if (single) {
+          valid = true;
+          long long j = k0 - g.k_lo;
+          if (j >= 0 && j < g.nb) {
+            double q = __dmul_rn(a2, tb.gq[j]);
+            if (j < rep.nbins)
+              deposit_rep(rep, j, (int)(s & (kAccReplicas - 1)), q, &rs->err);
+            else
+              deposit_q(acc, j, q, &rs->err);
+            r = q;
+          }
+        } else {
+          slow = true;
+        }
       }
+      if (slow) slow_q[atomicAdd(&slow_n, 1)] = s;
+      prepass_decide(r, tk_bits, tl_bits, valid, s, a2, fs, fds, g, cd, rs, nkappa);
+    }
+    __syncthreads();  // the stage is consumed; the queue count is final
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      fetch(stage);
+    }
+    const int cnt = slow_n;
+    if (cnt >= kPrepassThreads) {
+      prepass_drain(A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, slow_q, cnt, nkappa);
+      __syncthreads();
+      if (tid == 0) slow_n = 0;
+      __syncthreads();
     }
   }
+  if (failed) {
+    // a copy never arrived: flag it, and wait (bounded) for every copy this CTA started
+    // before its shared memory goes away
+    if (tid == 0) {
+      atomicOr(&rs->err, ERR_TIMEOUT);
+      for (long long k = i; k < i + kPreStages; ++k) {
+        const long long tk = stage_tile[k % kPreStages];
+        if (tk < nfull) mbar_wait(&bar[k % kPreStages], (unsigned)((k / kPreStages) & 1));
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  prepass_drain(A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, slow_q, slow_n, nkappa);
   for (int o = 16; o > 0; o >>= 1) nkappa += __shfl_xor_sync(0xFFFFFFFFu, nkappa, o);
   if (lane == 0 && nkappa) atomicAdd(&rs->ncand, nkappa);
 }
 
 void launch_prepass(const double* A, const double* f, const double* fdot, long long N,
                     const Grid& g, const Tables& tb, double thr_kappa, double thr_live,
-                    unsigned long long* acc, Cands cd, RunState* rs, int nsm, cudaStream_t st) {
+                    unsigned long long* acc, AccReplicas rep, Cands cd, RunState* rs, int nsm,
+                    cudaStream_t st) {
   if (N <= 0) return;
-  int th = 256;
-  long long want = (N + th - 1) / th;
-  long long cap = (long long)nsm * 8;
-  int bl = (int)(want < cap ? want : cap);
-  k_prepass<<<bl, th, 0, st>>>(A, f, fdot, N, g, tb, thr_kappa, thr_live, acc, cd, rs);
+  long long tiles = (N + kPreTile - 1) / kPreTile;
+  long long cap = (long long)nsm * 4;  // resident CTAs (launch bounds, shared memory)
+  int bl = (int)(tiles < cap ? tiles : cap);
+  k_prepass<<<bl, kPrepassThreads, kPrepassSmem, st>>>(A, f, fdot, N, g, tb, thr_kappa, thr_live,
+                                                       acc, rep, cd, rs);
+  if (rep.nbins > 0)
+    k_fold_replicas<<<(unsigned)((rep.nbins + 255) / 256), 256, 0, st>>>(acc, rep);
 }
 
 // ============================================================================ reductions
@@ -306,53 +510,123 @@ __device__ __forceinline__ double sg_store(const SgOut& o, long long j, double v
 // doubles, whose integer order is their value order; ties broken by position); srank
 // maps a position to its sorted index.
 
-__global__ void k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
-                             unsigned long long* __restrict__ skey, uint16_t* __restrict__ srank,
-                             Dirty d) {
+// Bitonic sort of (key, position) with E consecutive elements per thread: stages whose
+// partners are less than E apart run in registers, less than 32 E apart through warp
+// shuffles, and only the longest ones through shared memory (a barrier per stage).
+template <int E>
+__device__ __forceinline__ void cmp_keep(u64& k, int& x, u64 ko, int xo, bool keep_min) {
+  const bool gt = (k > ko) || (k == ko && x > xo);  // this element after the other one
+  if (gt == keep_min) {
+    k = ko;
+    x = xo;
+  }
+}
+
+template <int E>
+__global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
+                                                     unsigned long long* __restrict__ skey,
+                                                     uint16_t* __restrict__ srank, Dirty d) {
   extern __shared__ unsigned long long sm_keys[];
   uint16_t* sm_idx = (uint16_t*)(sm_keys + pl.kpad);
-  const int half = pl.kpad >> 1;  // compare-exchange pairs per stage
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int kpad = pl.kpad;  // = T * E
   const int nitem = d.count(kListR0, pl.nch);
-  for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
-    const int b = d.item(kListR0, it);  // a chunk whose input changed
+  for (int item = blockIdx.x; item < nitem; item += gridDim.x) {
+    const int b = d.item(kListR0, item);  // a chunk whose input changed
     const long long base = (long long)b * pl.Kc;
     const int len = (int)((n - base) < pl.Kc ? (n - base) : pl.Kc);
-    for (int i = threadIdx.x; i < pl.kpad; i += blockDim.x) {
-      u64 k = ~0ull;
+    u64 k[E];
+    int x[E];
+#pragma unroll
+    for (int a = 0; a < E; ++a) {
+      const int i = tid * E + a;
+      u64 kv = ~0ull;
       if (i < len) {
-        k = (u64)__double_as_longlong(spec_value(in, base + i));
-        if (k >> 63) k = 0ull;  // -0.0 (or a negative value) sorts as zero
+        kv = (u64)__double_as_longlong(spec_value(in, base + i));
+        if (kv >> 63) kv = 0ull;  // -0.0 (or a negative value) sorts as zero
       }
-      sm_keys[i] = k;
-      sm_idx[i] = (uint16_t)i;
+      k[a] = kv;
+      x[a] = i;
     }
-    __syncthreads();
-    // bitonic sort of (key, position): pair q of stage (kk, jj) is (i, i + jj) with i
-    // the q-th index whose bit jj is clear
-    for (int kk = 2; kk <= pl.kpad; kk <<= 1) {
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (int q = threadIdx.x; q < half; q += blockDim.x) {
-          const int i = ((q & ~(jj - 1)) << 1) | (q & (jj - 1));
-          const int ixj = i | jj;
-          u64 ki = sm_keys[i], kj = sm_keys[ixj];
-          uint16_t ii = sm_idx[i], ij = sm_idx[ixj];
-          bool gt = (ki > kj) || (ki == kj && ii > ij);
-          bool asc = ((i & kk) == 0);
-          if (gt == asc) {
-            sm_keys[i] = kj;
-            sm_keys[ixj] = ki;
-            sm_idx[i] = ij;
-            sm_idx[ixj] = ii;
-          }
+    bool first_smem = true;
+    for (int kk = 2; kk <= kpad; kk <<= 1) {
+      int jj = kk >> 1;
+      if (jj >= 32 * E) {
+        if (!first_smem) __syncthreads();  // everyone has read the previous round back
+        first_smem = false;
+#pragma unroll
+        for (int a = 0; a < E; ++a) {
+          sm_keys[tid * E + a] = k[a];
+          sm_idx[tid * E + a] = (uint16_t)x[a];
         }
         __syncthreads();
+        for (; jj >= 32 * E; jj >>= 1) {
+          for (int q = tid; q < kpad / 2; q += T) {
+            const int i = ((q & ~(jj - 1)) << 1) | (q & (jj - 1));
+            const int ixj = i | jj;
+            u64 ki = sm_keys[i], kj = sm_keys[ixj];
+            uint16_t ii = sm_idx[i], ij = sm_idx[ixj];
+            bool gt = (ki > kj) || (ki == kj && ii > ij);
+            bool asc = ((i & kk) == 0);
+            if (gt == asc) {
+              sm_keys[i] = kj;
+              sm_keys[ixj] = ki;
+              sm_idx[i] = ij;
+              sm_idx[ixj] = ii;
+            }
+          }
+          __syncthreads();
+        }
+#pragma unroll
+        for (int a = 0; a < E; ++a) {
+          k[a] = sm_keys[tid * E + a];
+          x[a] = sm_idx[tid * E + a];
+        }
+      }
+      for (; jj >= E; jj >>= 1) {
+        const int lm = jj / E;  // partner lane offset (< 32)
+#pragma unroll
+        for (int a = 0; a < E; ++a) {
+          const int i = tid * E + a;
+          const u64 ko = __shfl_xor_sync(0xFFFFFFFFu, k[a], lm);
+          const int xo = __shfl_xor_sync(0xFFFFFFFFu, x[a], lm);
+          const bool lower = (i & jj) == 0, asc = (i & kk) == 0;
+          cmp_keep<E>(k[a], x[a], ko, xo, lower == asc);
+        }
+      }
+      // in-thread stages: distances E/2 .. 1 (those below kk), unrolled so that the
+      // element arrays stay in registers
+#pragma unroll
+      for (int jl = E / 2; jl >= 1; jl >>= 1) {
+        if (jl > (kk >> 1)) continue;
+#pragma unroll
+        for (int a = 0; a < E; ++a) {
+          if ((a & jl) == 0) {
+            const int c = a | jl;
+            const int i = tid * E + a;
+            const bool asc = (i & kk) == 0;
+            const u64 ka = k[a], kc = k[c];
+            const int xa = x[a], xc = x[c];
+            const bool gt = (ka > kc) || (ka == kc && xa > xc);
+            if (gt == asc) {
+              k[a] = kc;
+              k[c] = ka;
+              x[a] = xc;
+              x[c] = xa;
+            }
+          }
+        }
       }
     }
-    for (int s = threadIdx.x; s < len; s += blockDim.x) {
-      skey[base + s] = sm_keys[s];
-      srank[base + sm_idx[s]] = (uint16_t)s;
+#pragma unroll
+    for (int a = 0; a < E; ++a) {
+      const int sidx = tid * E + a;
+      if (sidx < len) {
+        skey[base + sidx] = k[a];
+        srank[base + x[a]] = (uint16_t)sidx;
+      }
     }
-    __syncthreads();  // before the next chunk overwrites the keys
+    if (!first_smem) __syncthreads();  // before the next chunk overwrites shared memory
   }
 }
 
@@ -373,22 +647,26 @@ static int persistent_grid(const SmoothPlan& pl, int items, int resident) {
   return items < resident ? items : resident;
 }
 
-static int sort_threads(const SmoothPlan& pl) {
-  int th = pl.kpad / 2;
-  if (th > 1024) th = 1024;
-  if (th < 32) th = 32;
-  return th;
-}
+static int sort_per_thread(const SmoothPlan& pl) { return pl.kpad <= 2048 ? 2 : pl.kpad / 1024; }
+static int sort_threads(const SmoothPlan& pl) { return pl.kpad / sort_per_thread(pl); }
 static size_t sort_smem(const SmoothPlan& pl) {
   return (size_t)pl.kpad * (sizeof(u64) + sizeof(uint16_t));
+}
+template <typename F>
+static void with_sort_kernel(const SmoothPlan& pl, F fn) {
+  switch (sort_per_thread(pl)) {
+    case 2: fn(k_chunk_sort<2>); break;
+    case 4: fn(k_chunk_sort<4>); break;
+    default: fn(k_chunk_sort<8>); break;
+  }
 }
 
 void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
                        uint16_t* srank, Dirty d, cudaStream_t st) {
-  size_t smem = sort_smem(pl);
-  int th = sort_threads(pl);
-  k_chunk_sort<<<persistent_grid(pl, pl.nch, pl.res_sort), th, smem, st>>>(in, n, pl, skey, srank,
-                                                                          d);
+  const size_t smem = sort_smem(pl);
+  const int th = sort_threads(pl);
+  const int bl = persistent_grid(pl, pl.nch, pl.res_sort);
+  with_sort_kernel(pl, [&](auto kern) { kern<<<bl, th, smem, st>>>(in, n, pl, skey, srank, d); });
 }
 
 // ============================================================================ running median
@@ -807,11 +1085,14 @@ __global__ void k_window_mean(const double* __restrict__ x, long long n, SmoothP
   if (o.rtol_on) warp_max_atomic((u64)__double_as_longlong(relmax), &o.rs->relchg_bits);
 }
 
+// One output of the chunk per thread.
+static int mean_threads(const SmoothPlan& pl) { return pl.Kc < 1024 ? pl.Kc : 1024; }
+
 void launch_window_mean(const double* x, long long n, const SmoothPlan& pl,
                         const unsigned long long* pre_lo, const unsigned long long* pre_hi,
                         const int* sig, const unsigned* uflow, SgOut o, Dirty d, int out_radius,
                         cudaStream_t st) {
-  int th = 256;
+  int th = mean_threads(pl);
   int bl = persistent_grid(pl, pl.nch, pl.res_mean);
   k_window_mean<<<bl, th, 0, st>>>(x, n, pl, pre_lo, pre_hi, sig, uflow, o, d, out_radius);
 }
@@ -854,9 +1135,87 @@ __device__ double rho2_exact(const Grid& g, const Tables& tb, const double* __re
   return __dmul_rn(4.0, acc);
 }
 
-// One warp per candidate: the lanes share the bins of its sweep (loud high-frequency
-// sources sweep hundreds of bins, and a thread per candidate would leave the launch
-// waiting on the longest one), for the screen sum and for the removal.
+// FP32 screen sum of candidate c over the bins t0 + off, t0 + off + step, ... < t1 of its
+// sweep (t relative to its first bin ka); kcount counts the terms.
+__device__ __forceinline__ float screen_part(const Cands& cd, long long c, const Grid& g,
+                                             const Tables& tb, const float* __restrict__ inv_f,
+                                             int off, int step, int& kcount) {
+  const int ka = cd.ka[c];
+  const int nbin = cd.nbin[c];
+  const float a2f = cd.a2f[c];
+  float r2 = 0.0f;
+  kcount = 0;
+  if (nbin == 1) {
+    if (off == 0 && ka >= 0 && ka < g.nb) {
+      r2 = __fmul_rn(__fmul_rn(a2f, tb.Gf[ka]), inv_f[ka]);
+      kcount = 1;
+    }
+    return r2;
+  }
+  const float flo = cd.flo[c], fhi = __fadd_rn(flo, cd.len[c]), invlen = 1.0f / cd.len[c];
+  const int t0 = ka < 0 ? -ka : 0;
+  const int t1 = (long long)ka + nbin > g.nb ? (int)(g.nb - ka) : nbin;
+  for (int t = t0 + off; t < t1; t += step) {
+    float a = fmaxf(flo, (float)t - 0.5f);
+    float b = fminf(fhi, (float)t + 0.5f);
+    if (b > a) {
+      float w = __fmul_rn(__fsub_rn(b, a), invlen);
+      int k = ka + t;
+      r2 = __fadd_rn(r2, __fmul_rn(__fmul_rn(__fmul_rn(a2f, w), tb.Gf[k]), inv_f[k]));
+      ++kcount;
+    }
+  }
+  return r2;
+}
+
+// Decision from the FP32 value: 1 resolve, 0 keep, -1 too close to rho_th to tell (the
+// caller then computes rho^2 exactly).
+__device__ __forceinline__ int screen_decide(float r2, int kcount, float th2f, int mode) {
+  if (mode == 1) return r2 > th2f ? 1 : 0;
+  float m = 1e-5f + 4e-7f * (float)kcount;
+  if (mode == 0 && r2 > th2f * (1.0f + m)) return 1;
+  if (mode == 0 && r2 < th2f * (1.0f - m)) return 0;
+  return -1;
+}
+
+// Remove the parts of candidate c that the catalog pass deposited: bins k0 + off,
+// k0 + off + step, ... of its sweep.
+__device__ __forceinline__ void remove_part(const Cands& cd, long long c, const Grid& g,
+                                            const Tables& tb, unsigned long long* acc,
+                                            const Dirty& d, int Kc, int off, int step) {
+  Sweep sw;
+  sw.lo = cd.lo[c];
+  sw.hi = cd.hi[c];
+  sw.ka = (i64)floor(__dadd_rn(sw.lo, 0.5));
+  sw.kb = (i64)floor(__dadd_rn(sw.hi, 0.5));
+  const double a2 = cd.a2[c];
+  if (sw.ka == sw.kb) {
+    long long j = sw.ka - g.k_lo;
+    if (off == 0 && j >= 0 && j < g.nb) {
+      remove_q(acc, j, __dmul_rn(a2, tb.gq[j]));
+      d.mark_next(j / Kc);
+    }
+    return;
+  }
+  long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
+  long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
+  for (long long k = k0 + off; k <= k1; k += step) {
+    double w = sweep_weight(sw, k);
+    if (w > 0.0) {
+      long long j = k - g.k_lo;
+      remove_q(acc, j, __dmul_rn(__dmul_rn(a2, w), tb.gq[j]));
+      d.mark_next(j / Kc);
+    }
+  }
+}
+
+// Every lane screens one candidate of a group of 32: still unresolved, and S_n changed on
+// a bin of its sweep (else rho is the value already found below rho_th).  Candidates of a
+// few bins are then done by their own lane; longer sweeps (loud high-frequency sources
+// cover up to hundreds of bins) by the whole warp, the lanes sharing the bins, so that no
+// launch waits on one thread walking a long sweep.
+constexpr int kSnrLaneBins = 4;
+
 __global__ void __launch_bounds__(256) k_snr_resolve(
     Cands cd, Grid g, Tables tb, const double* __restrict__ Sg, const float* __restrict__ inv_f,
     double th2, double rtol, int mode, unsigned char* __restrict__ resolved,
@@ -867,101 +1226,71 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const float th2f = (float)th2;
   unsigned local_new = 0, local_exact = 0;
-  for (long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; c < nlive;
-       c += nwarps) {
-    if (cd.res[c]) continue;
-    const int ka = cd.ka[c];
-    const int nbin = cd.nbin[c];
-    {
-      // S_n unchanged on every bin of the sweep: rho is the value already found below rho_th
+  for (long long cbase = ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5) * 32;
+       cbase < nlive; cbase += nwarps * 32) {
+    bool todo = false, wide = false;
+    const long long c = cbase + lane;
+    if (c < nlive && !cd.res[c]) {
+      const int ka = cd.ka[c];
+      const int nbin = cd.nbin[c];
       long long c0 = ka < 0 ? 0 : ka / Kc;
       long long kl = (long long)ka + nbin - 1;
       if (kl > g.nb - 1) kl = g.nb - 1;
-      if (kl < 0) continue;
-      long long c1 = kl / Kc;
-      bool changed = false;
-      for (long long cc = c0; cc <= c1 && !changed; ++cc) changed = d.any(cc, sg_radius);
-      if (!changed) continue;
-    }
-    const float a2f = cd.a2f[c];
-    float r2 = 0.0f;
-    int kcount = 0;
-    if (nbin == 1) {
-      if (lane == 0 && ka >= 0 && ka < g.nb) {
-        r2 = __fmul_rn(__fmul_rn(a2f, tb.Gf[ka]), inv_f[ka]);
-        kcount = 1;
+      if (kl >= 0) {
+        long long c1 = kl / Kc;
+        for (long long cc = c0; cc <= c1 && !todo; ++cc) todo = d.any(cc, sg_radius);
       }
-    } else {
-      const float flo = cd.flo[c], fhi = __fadd_rn(flo, cd.len[c]), invlen = 1.0f / cd.len[c];
-      int t0 = ka < 0 ? -ka : 0;
-      int t1 = (long long)ka + nbin > g.nb ? (int)(g.nb - ka) : nbin;
-      for (int t = t0 + lane; t < t1; t += 32) {
-        float a = fmaxf(flo, (float)t - 0.5f);
-        float b = fminf(fhi, (float)t + 0.5f);
-        if (b > a) {
-          float w = __fmul_rn(__fsub_rn(b, a), invlen);
-          int k = ka + t;
-          r2 = __fadd_rn(r2, __fmul_rn(__fmul_rn(__fmul_rn(a2f, w), tb.Gf[k]), inv_f[k]));
-          ++kcount;
-        }
+      wide = todo && nbin > kSnrLaneBins;
+    }
+    if (todo && !wide) {
+      int kcount;
+      const float r2 = screen_part(cd, c, g, tb, inv_f, 0, 1, kcount);
+      int dec = screen_decide(r2, kcount, th2f, mode);
+      if (dec < 0) {
+        ++local_exact;
+        dec = rho2_exact(g, tb, Sg, cd.a2[c], cd.lo[c], cd.hi[c]) > th2;
+      }
+      if (dec) {
+        cd.res[c] = 1;
+        resolved[cd.src[c]] = 1;
+        ++local_new;
+        remove_part(cd, c, g, tb, acc, d, Kc, 0, 1);
       }
     }
-    // butterfly sums: every lane ends with the same values
-    for (int o = 16; o > 0; o >>= 1) {
-      r2 = __fadd_rn(r2, __shfl_xor_sync(0xFFFFFFFFu, r2, o));
-      kcount += __shfl_xor_sync(0xFFFFFFFFu, kcount, o);
-    }
-    bool resolve;
-    if (mode == 1) {
-      resolve = r2 > th2f;
-    } else {
-      float m = 1e-5f + 4e-7f * (float)kcount;
-      if (mode == 0 && r2 > th2f * (1.0f + m)) {
-        resolve = true;
-      } else if (mode == 0 && r2 < th2f * (1.0f - m)) {
-        resolve = false;
-      } else {
+    unsigned pending = __ballot_sync(0xFFFFFFFFu, wide);
+    while (pending) {
+      const long long cw = cbase + (__ffs(pending) - 1);
+      pending &= pending - 1;
+      int kcount;
+      float r2 = screen_part(cd, cw, g, tb, inv_f, lane, 32, kcount);
+      // butterfly sums: every lane ends with the same values
+      for (int o = 16; o > 0; o >>= 1) {
+        r2 = __fadd_rn(r2, __shfl_xor_sync(0xFFFFFFFFu, r2, o));
+        kcount += __shfl_xor_sync(0xFFFFFFFFu, kcount, o);
+      }
+      int dec = screen_decide(r2, kcount, th2f, mode);
+      if (dec < 0) {
         // the oracle's order of summation, on one lane
         int ex = 0;
         if (lane == 0) {
           ++local_exact;
-          ex = rho2_exact(g, tb, Sg, cd.a2[c], cd.lo[c], cd.hi[c]) > th2;
+          ex = rho2_exact(g, tb, Sg, cd.a2[cw], cd.lo[cw], cd.hi[cw]) > th2;
         }
-        resolve = __shfl_sync(0xFFFFFFFFu, ex, 0) != 0;
+        dec = __shfl_sync(0xFFFFFFFFu, ex, 0);
+      }
+      if (dec) {
+        if (lane == 0) {
+          cd.res[cw] = 1;
+          resolved[cd.src[cw]] = 1;
+          ++local_new;
+        }
+        remove_part(cd, cw, g, tb, acc, d, Kc, lane, 32);
       }
     }
-    if (resolve) {
-      if (lane == 0) {
-        cd.res[c] = 1;
-        resolved[cd.src[c]] = 1;
-        ++local_new;
-      }
-      // remove exactly the parts the prepass deposited
-      Sweep sw;
-      sw.lo = cd.lo[c];
-      sw.hi = cd.hi[c];
-      sw.ka = (i64)floor(__dadd_rn(sw.lo, 0.5));
-      sw.kb = (i64)floor(__dadd_rn(sw.hi, 0.5));
-      double a2 = cd.a2[c];
-      if (sw.ka == sw.kb) {
-        long long j = sw.ka - g.k_lo;
-        if (lane == 0 && j >= 0 && j < g.nb) {
-          remove_q(acc, j, __dmul_rn(a2, tb.gq[j]));
-          d.mark_next(j / Kc);
-        }
-      } else {
-        long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
-        long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
-        for (long long k = k0 + lane; k <= k1; k += 32) {
-          double w = sweep_weight(sw, k);
-          if (w > 0.0) {
-            long long j = k - g.k_lo;
-            remove_q(acc, j, __dmul_rn(__dmul_rn(a2, w), tb.gq[j]));
-            d.mark_next(j / Kc);
-          }
-        }
-      }
-    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    local_new += __shfl_xor_sync(0xFFFFFFFFu, local_new, o);
+    local_exact += __shfl_xor_sync(0xFFFFFFFFu, local_exact, o);
   }
   if (lane == 0) {
     if (local_new) atomicAdd(&rs->count_new, (unsigned long long)local_new);
@@ -973,8 +1302,8 @@ void launch_snr_resolve(Cands cd, long long ncap, const Grid& g, const Tables& t
                         const double* Sg, const float* inv_f, double th2, double rtol, int mode,
                         unsigned char* resolved, unsigned long long* acc, RunState* rs,
                         Dirty d, int Kc, int sg_radius, int nsm, cudaStream_t st) {
-  int th = 256;
-  long long want = (ncap * 32 + th - 1) / th;
+  int th = 256;  // 8 warps, each screening 32 candidates at a time
+  long long want = (ncap + th - 1) / th;
   long long cap = (long long)nsm * 8;
   int bl = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
   k_snr_resolve<<<bl, th, 0, st>>>(cd, g, tb, Sg, inv_f, th2, rtol, mode, resolved, acc, rs, d, Kc,
@@ -1062,14 +1391,19 @@ void launch_control(RunState* rs, int max_iter, double rtol, int* new_hist,
 void plan_grids(SmoothPlan& pl) {
   pl.res_sort = pl.res_median = pl.res_prefix = pl.res_mean = 0;
   if (pl.nsm <= 0) return;
-  pl.res_sort = resident_ctas(pl, k_chunk_sort, sort_threads(pl), sort_smem(pl));
+  with_sort_kernel(pl, [&](auto kern) {
+    pl.res_sort = resident_ctas(pl, kern, sort_threads(pl), sort_smem(pl));
+  });
   pl.res_median = resident_ctas(pl, k_median_wm, median_threads(pl), median_smem_bytes(pl.Kc));
   pl.res_prefix = resident_ctas(pl, k_chunk_prefix, pl.Kc < 1024 ? pl.Kc : 1024, 0);
-  pl.res_mean = resident_ctas(pl, k_window_mean, 256, 0);
+  pl.res_mean = resident_ctas(pl, k_window_mean, mean_threads(pl), 0);
 }
 
 void configure_kernels() {
-  cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(k_prepass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepassSmem);
+  cudaFuncSetAttribute(k_chunk_sort<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(k_chunk_sort<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(k_chunk_sort<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   cudaFuncSetAttribute(k_median_wm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)median_smem_bytes(kMaxWindow));
 }

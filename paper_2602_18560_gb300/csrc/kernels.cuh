@@ -33,6 +33,7 @@ struct RunState {
   unsigned long long nexact;    // SNR decisions that needed the exact FP64 recomputation
   unsigned long long max_p_bits;    // scratch maximum (estimate on a given spectrum)
   unsigned long long relchg_bits;   // max relative change of S_n (conv_rtol)
+  unsigned long long next_tile;  // catalog tiles handed out so far (catalog pass)
   unsigned err;
   unsigned pad;
 };
@@ -135,9 +136,19 @@ void plan_grids(SmoothPlan& pl);
 void launch_tables(const Grid& g, int tdi2, double* S, double* R, double* gq, float* Gf,
                    float* invSf, cudaStream_t st);
 
+// Private copies of words 1 and 2 of the first nbins bins, kAccReplicas of them, zeroed
+// before the catalog pass; the pass folds them into the spectrum.
+constexpr int kAccReplicas = 16;
+constexpr long long kAccReplicaBins = 65536;
+struct AccReplicas {
+  unsigned long long* w;  // [kAccReplicas][nbins][2]
+  long long nbins;
+};
+
 void launch_prepass(const double* A, const double* f, const double* fdot, long long N,
                     const Grid& g, const Tables& tb, double thr_kappa, double thr_live,
-                    unsigned long long* acc, Cands cd, RunState* rs, int nsm, cudaStream_t st);
+                    unsigned long long* acc, AccReplicas rep, Cands cd, RunState* rs, int nsm,
+                    cudaStream_t st);
 
 // P[j] = S_j Q_j 2^-96 for every bin.
 void launch_power_out(const unsigned long long* acc, const double* S, long long n, double* P,
