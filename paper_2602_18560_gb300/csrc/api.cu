@@ -193,6 +193,9 @@ static SmoothPlan make_plan(int W, int64_t n) {
   int kp = 64;  // sort width: a power of two >= Kc, and two elements for each of >= 32 threads
   while (kp < kc) kp <<= 1;
   pl.kpad = kp;
+  pl.nsm = 0;
+  pl.fp32_keys = 0;
+  pl.key_scale = 1.0;
   return pl;
 }
 
@@ -219,6 +222,7 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
     c->grid.T2f = (float)(p->T_obs * p->T_obs);
   }
   c->plan = make_plan(p->window, n);
+  c->plan.fp32_keys = p->precision == SUB_MIXED ? 1 : 0;  // FP32 median selection
   auto fail = [&](int code) {
     g_create_err = c->err;
     sub_destroy(c);
@@ -280,9 +284,24 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   std::memset(c->h_rs, 0, sizeof(RunState));
   launch_tables(c->grid, p->tdi2, c->S, c->R, c->gq, c->Gf, c->invSf, c->stream);
   e = cudaMemsetAsync(c->Sg, 0, (size_t)n * 8, c->stream);
+  // The FP32 keys of the mixed-precision median are the powers times 2^e: the spectrum
+  // holds at most 2^31 S_instr per bin, so with e = 59 - ilogb(max S_instr) every power
+  // is below 2^91, and the smallest non-zero power (2^-64 S_instr) stays far above the
+  // FP32 normal range over any band whose S_instr spans less than 2^60.
+  if (e == cudaSuccess) e = cudaMemsetAsync(&c->rs->max_p_bits, 0, 8, c->stream);
+  if (e == cudaSuccess) launch_max_bits(c->S, n, &c->rs->max_p_bits, c->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_rs, c->rs, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) { c->err = std::string("table build: ") + cudaGetErrorString(e); return fail(SUB_ECUDA); }
+  {
+    double smax;
+    unsigned long long b = c->h_rs->max_p_bits;
+    std::memcpy(&smax, &b, 8);
+    int ex = smax > 0.0 ? std::ilogb(smax) : 0;
+    c->plan.key_scale = std::ldexp(1.0, 59 - ex);
+  }
   *out = c;
   return SUB_OK;
 }
@@ -298,8 +317,7 @@ extern "C" int sub_load_catalog(sub_ctx* c, const double* A, const double* f, co
   if (n > c->cap_N || c->A == nullptr) {
     drop_graph(c);
     dfree(c, c->A); dfree(c, c->f); dfree(c, c->fdot); dfree(c, c->resolved);
-    void* cds[] = {c->cd.src, c->cd.ka, c->cd.nbin, c->cd.a2f, c->cd.flo, c->cd.len,
-                   c->cd.a2, c->cd.lo, c->cd.hi, c->cd.res};
+    void* cds[] = {c->cd.src, c->cd.pk, c->cd.len, c->cd.a2, c->cd.lo, c->cd.hi, c->cd.res};
     for (void* q : cds) dfree(c, q);
     c->A = c->f = c->fdot = nullptr;
     c->resolved = nullptr;
@@ -311,9 +329,8 @@ extern "C" int sub_load_catalog(sub_ctx* c, const double* A, const double* f, co
     // Candidate arrays hold every source in the worst case (a catalog of bright sources).
     if ((rc = dalloc(c, (void**)&c->A, m * 8)) || (rc = dalloc(c, (void**)&c->f, m * 8)) ||
         (rc = dalloc(c, (void**)&c->fdot, m * 8)) || (rc = dalloc(c, (void**)&c->resolved, m)) ||
-        (rc = dalloc(c, (void**)&c->cd.src, m * 8)) || (rc = dalloc(c, (void**)&c->cd.ka, m * 4)) ||
-        (rc = dalloc(c, (void**)&c->cd.nbin, m * 4)) || (rc = dalloc(c, (void**)&c->cd.a2f, m * 4)) ||
-        (rc = dalloc(c, (void**)&c->cd.flo, m * 4)) || (rc = dalloc(c, (void**)&c->cd.len, m * 4)) ||
+        (rc = dalloc(c, (void**)&c->cd.src, m * 8)) || (rc = dalloc(c, (void**)&c->cd.pk, m * 16)) ||
+        (rc = dalloc(c, (void**)&c->cd.len, m * 4)) ||
         (rc = dalloc(c, (void**)&c->cd.a2, m * 8)) || (rc = dalloc(c, (void**)&c->cd.lo, m * 8)) ||
         (rc = dalloc(c, (void**)&c->cd.hi, m * 8)) || (rc = dalloc(c, (void**)&c->cd.res, m))) {
       return rc;

@@ -205,10 +205,9 @@ __device__ __noinline__ void emit_candidate(Cands cd, long long c, long long s, 
                                             double fs, double fds, const Grid g) {
   Sweep sw = make_sweep(fs, fds, g.T, g.T2);
   cd.src[c] = s;
-  cd.ka[c] = (int)(sw.ka - g.k_lo);
-  cd.nbin[c] = (int)(sw.kb - sw.ka + 1);
-  cd.a2f[c] = dbl_to_f32_scaled(a2, 160);
-  cd.flo[c] = (float)(sw.lo - (double)sw.ka);
+  cd.pk[c] = make_int4((int)(sw.ka - g.k_lo), (int)(sw.kb - sw.ka + 1),
+                       __float_as_int(dbl_to_f32_scaled(a2, 160)),
+                       __float_as_int((float)(sw.lo - (double)sw.ka)));
   cd.len[c] = (float)(sw.hi - sw.lo);
   cd.a2[c] = a2;
   cd.lo[c] = sw.lo;
@@ -510,11 +509,39 @@ __device__ __forceinline__ double sg_store(const SgOut& o, long long j, double v
 // doubles, whose integer order is their value order; ties broken by position); srank
 // maps a position to its sorted index.
 
+// Sort key of a value x >= 0 (a negative value or -0.0 sorts as zero): the bits of the
+// double (FP64 path), or of the float nearest to x * scale (mixed precision; scale is a
+// power of two that brings the powers, ~1e-50 .. 1e-30, into the FP32 range).  For
+// non-negative numbers the integer order of the bits is their value order.
+template <typename K>
+__device__ __forceinline__ K sort_key(double x, double scale);
+template <>
+__device__ __forceinline__ u64 sort_key<u64>(double x, double) {
+  u64 k = (u64)__double_as_longlong(x);
+  return (k >> 63) ? 0ull : k;
+}
+template <>
+__device__ __forceinline__ uint32_t sort_key<uint32_t>(double x, double scale) {
+  uint32_t k = __float_as_uint(__double2float_rn(__dmul_rn(x, scale)));
+  return (k >> 31) ? 0u : k;
+}
+// The value a key stands for (inv_scale = 1 / scale, exact).
+template <typename K>
+__device__ __forceinline__ double key_value(K k, double inv_scale);
+template <>
+__device__ __forceinline__ double key_value<u64>(u64 k, double) {
+  return __longlong_as_double((i64)k);
+}
+template <>
+__device__ __forceinline__ double key_value<uint32_t>(uint32_t k, double inv_scale) {
+  return __dmul_rn((double)__uint_as_float(k), inv_scale);
+}
+
 // Bitonic sort of (key, position) with E consecutive elements per thread: stages whose
 // partners are less than E apart run in registers, less than 32 E apart through warp
 // shuffles, and only the longest ones through shared memory (a barrier per stage).
-template <int E>
-__device__ __forceinline__ void cmp_keep(u64& k, int& x, u64 ko, int xo, bool keep_min) {
+template <typename K>
+__device__ __forceinline__ void cmp_keep(K& k, int& x, K ko, int xo, bool keep_min) {
   const bool gt = (k > ko) || (k == ko && x > xo);  // this element after the other one
   if (gt == keep_min) {
     k = ko;
@@ -522,11 +549,12 @@ __device__ __forceinline__ void cmp_keep(u64& k, int& x, u64 ko, int xo, bool ke
   }
 }
 
-template <int E>
+template <int E, typename K>
 __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
-                                                     unsigned long long* __restrict__ skey,
+                                                     K* __restrict__ skey,
                                                      uint16_t* __restrict__ srank, Dirty d) {
-  extern __shared__ unsigned long long sm_keys[];
+  extern __shared__ __align__(16) unsigned char sort_raw[];
+  K* sm_keys = (K*)sort_raw;
   uint16_t* sm_idx = (uint16_t*)(sm_keys + pl.kpad);
   const int T = blockDim.x, tid = threadIdx.x;
   const int kpad = pl.kpad;  // = T * E
@@ -535,16 +563,13 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
     const int b = d.item(kListR0, item);  // a chunk whose input changed
     const long long base = (long long)b * pl.Kc;
     const int len = (int)((n - base) < pl.Kc ? (n - base) : pl.Kc);
-    u64 k[E];
+    K k[E];
     int x[E];
 #pragma unroll
     for (int a = 0; a < E; ++a) {
       const int i = tid * E + a;
-      u64 kv = ~0ull;
-      if (i < len) {
-        kv = (u64)__double_as_longlong(spec_value(in, base + i));
-        if (kv >> 63) kv = 0ull;  // -0.0 (or a negative value) sorts as zero
-      }
+      K kv = (K)~(K)0;
+      if (i < len) kv = sort_key<K>(spec_value(in, base + i), pl.key_scale);
       k[a] = kv;
       x[a] = i;
     }
@@ -564,7 +589,7 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
           for (int q = tid; q < kpad / 2; q += T) {
             const int i = ((q & ~(jj - 1)) << 1) | (q & (jj - 1));
             const int ixj = i | jj;
-            u64 ki = sm_keys[i], kj = sm_keys[ixj];
+            K ki = sm_keys[i], kj = sm_keys[ixj];
             uint16_t ii = sm_idx[i], ij = sm_idx[ixj];
             bool gt = (ki > kj) || (ki == kj && ii > ij);
             bool asc = ((i & kk) == 0);
@@ -588,10 +613,10 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
 #pragma unroll
         for (int a = 0; a < E; ++a) {
           const int i = tid * E + a;
-          const u64 ko = __shfl_xor_sync(0xFFFFFFFFu, k[a], lm);
+          const K ko = __shfl_xor_sync(0xFFFFFFFFu, k[a], lm);
           const int xo = __shfl_xor_sync(0xFFFFFFFFu, x[a], lm);
           const bool lower = (i & jj) == 0, asc = (i & kk) == 0;
-          cmp_keep<E>(k[a], x[a], ko, xo, lower == asc);
+          cmp_keep<K>(k[a], x[a], ko, xo, lower == asc);
         }
       }
       // in-thread stages: distances E/2 .. 1 (those below kk), unrolled so that the
@@ -605,7 +630,7 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
             const int c = a | jl;
             const int i = tid * E + a;
             const bool asc = (i & kk) == 0;
-            const u64 ka = k[a], kc = k[c];
+            const K ka = k[a], kc = k[c];
             const int xa = x[a], xc = x[c];
             const bool gt = (ka > kc) || (ka == kc && xa > xc);
             if (gt == asc) {
@@ -647,18 +672,34 @@ static int persistent_grid(const SmoothPlan& pl, int items, int resident) {
   return items < resident ? items : resident;
 }
 
+// Launch one k_chunk_sort instantiation with the key buffer cast to its key type.
+template <typename K>
+static void launch_sort_as(void (*kern)(SpecIn, long long, SmoothPlan, K*, uint16_t*, Dirty),
+                           int bl, int th, size_t smem, cudaStream_t st, SpecIn in, long long n,
+                           const SmoothPlan& pl, unsigned long long* skey, uint16_t* srank,
+                           Dirty d) {
+  kern<<<bl, th, smem, st>>>(in, n, pl, (K*)skey, srank, d);
+}
+
 static int sort_per_thread(const SmoothPlan& pl) { return pl.kpad <= 2048 ? 2 : pl.kpad / 1024; }
 static int sort_threads(const SmoothPlan& pl) { return pl.kpad / sort_per_thread(pl); }
 static size_t sort_smem(const SmoothPlan& pl) {
-  return (size_t)pl.kpad * (sizeof(u64) + sizeof(uint16_t));
+  return (size_t)pl.kpad * ((pl.fp32_keys ? 4 : 8) + sizeof(uint16_t));
+}
+template <typename K, typename F>
+static void with_sort_kernel_k(const SmoothPlan& pl, F fn) {
+  switch (sort_per_thread(pl)) {
+    case 2: fn(k_chunk_sort<2, K>); break;
+    case 4: fn(k_chunk_sort<4, K>); break;
+    default: fn(k_chunk_sort<8, K>); break;
+  }
 }
 template <typename F>
 static void with_sort_kernel(const SmoothPlan& pl, F fn) {
-  switch (sort_per_thread(pl)) {
-    case 2: fn(k_chunk_sort<2>); break;
-    case 4: fn(k_chunk_sort<4>); break;
-    default: fn(k_chunk_sort<8>); break;
-  }
+  if (pl.fp32_keys)
+    with_sort_kernel_k<uint32_t>(pl, fn);
+  else
+    with_sort_kernel_k<u64>(pl, fn);
 }
 
 void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
@@ -666,7 +707,9 @@ void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned lo
   const size_t smem = sort_smem(pl);
   const int th = sort_threads(pl);
   const int bl = persistent_grid(pl, pl.nch, pl.res_sort);
-  with_sort_kernel(pl, [&](auto kern) { kern<<<bl, th, smem, st>>>(in, n, pl, skey, srank, d); });
+  with_sort_kernel(pl, [&](auto kern) {
+    launch_sort_as(kern, bl, th, smem, st, in, n, pl, skey, srank, d);
+  });
 }
 
 // ============================================================================ running median
@@ -690,7 +733,8 @@ void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned lo
 __device__ __forceinline__ int wm_levels(int M) { return 32 - __clz(M - 1); }
 
 // One tile; returns the largest relative change of S_n among its outputs (conv_rtol).
-__device__ __forceinline__ double median_tile(const unsigned long long* __restrict__ skey,
+template <typename K>
+__device__ __forceinline__ double median_tile(const K* __restrict__ skey,
                                               const uint16_t* __restrict__ srank, long long n,
                                               const SmoothPlan& pl, const SgOut& o, long long u,
                                               unsigned char* sm_raw, int* zeros) {
@@ -702,15 +746,16 @@ __device__ __forceinline__ double median_tile(const unsigned long long* __restri
   if (j_lo < 0) j_lo = 0;
   if (j_hi > n) j_hi = n;
   if (j_lo >= j_hi) return 0.0;
+  const double inv_scale = 1.0 / pl.key_scale;  // exact: a power of two
   const long long span = (u - 1) * (long long)Kc;
   int len0 = 0, len1 = 0;
   if (u >= 1) len0 = (n - span) < Kc ? (int)(n - span) : Kc;
   if (u < pl.nch) len1 = (n - span - Kc) < Kc ? (int)(n - span - Kc) : Kc;
   double relmax = 0.0;
-  u64* sk = (u64*)sm_raw;                                    // [M] sorted keys (step 1)
+  K* sk = (K*)sm_raw;                                        // [M] sorted keys (step 1)
   uint16_t* seq1 = (uint16_t*)sm_raw;                        // [M] (steps 2-3, over sk)
   uint16_t* src = seq1 + M;                                  // [M] rank -> element
-  uint16_t* seq0 = (uint16_t*)(sm_raw + (size_t)16 * Kc);    // [M]
+  uint16_t* seq0 = (uint16_t*)(sm_raw + sizeof(K) * (size_t)M);  // [M]
   uint32_t* bits = (uint32_t*)(seq0 + M);                    // [LV][ws]
   uint16_t* pre = (uint16_t*)(bits + (size_t)LV * ws);       // [LV][ws]
 
@@ -724,12 +769,12 @@ __device__ __forceinline__ double median_tile(const unsigned long long* __restri
     int v;
     if (q < lenX) {
       const int si = srank[span + p];
-      const u64 key = sk[p - q + si];
-      const u64* oth = X ? sk : sk + Kc;
+      const K key = sk[p - q + si];
+      const K* oth = X ? sk : sk + Kc;
       int lo = 0, hi = X ? len0 : len1;
       while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        u64 km = oth[mid];
+        K km = oth[mid];
         bool before = X ? (km <= key) : (km < key);
         if (before) lo = mid + 1; else hi = mid;
       }
@@ -837,14 +882,14 @@ __device__ __forceinline__ double median_tile(const unsigned long long* __restri
       }
     }
     const int ea = src[va];
-    const u64 khi = skey[span + (ea >> 15) * Kc + (ea & 0x7FFF)];
+    const K khi = skey[span + (ea >> 15) * Kc + (ea & 0x7FFF)];
     double med;
     if (cnt & 1) {
-      med = __longlong_as_double((i64)khi);
+      med = key_value<K>(khi, inv_scale);
     } else {
       const int eb = src[vb];
-      const u64 klo = skey[span + (eb >> 15) * Kc + (eb & 0x7FFF)];
-      med = __dmul_rn(__dadd_rn(__longlong_as_double((i64)klo), __longlong_as_double((i64)khi)),
+      const K klo = skey[span + (eb >> 15) * Kc + (eb & 0x7FFF)];
+      med = __dmul_rn(__dadd_rn(key_value<K>(klo, inv_scale), key_value<K>(khi, inv_scale)),
                       0.5);
     }
     double v = __dmul_rn(kMedianBias, med);
@@ -854,8 +899,9 @@ __device__ __forceinline__ double median_tile(const unsigned long long* __restri
   return relmax;
 }
 
+template <typename K>
 __global__ void __launch_bounds__(512, 2) k_median_wm(
-    const unsigned long long* __restrict__ skey, const uint16_t* __restrict__ srank,
+    const K* __restrict__ skey, const uint16_t* __restrict__ srank,
     long long n, SmoothPlan pl, SgOut o, Dirty d) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int zeros[16];
@@ -863,7 +909,7 @@ __global__ void __launch_bounds__(512, 2) k_median_wm(
   const int nitem = d.count(kListTile, pl.nch + 1);
   for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
     // a tile whose windows changed
-    double r = median_tile(skey, srank, n, pl, o, d.item(kListTile, it), sm_raw, zeros);
+    double r = median_tile<K>(skey, srank, n, pl, o, d.item(kListTile, it), sm_raw, zeros);
     relmax = r > relmax ? r : relmax;
     __syncthreads();  // before the next tile overwrites shared memory
   }
@@ -877,19 +923,22 @@ static int median_threads(const SmoothPlan& pl) {
   return t;
 }
 
-size_t median_smem_bytes(int Kc) {
+size_t median_smem_bytes(int Kc, int key_bytes) {
   int M = 2 * Kc, LV = 0;
   while ((1 << LV) < M) ++LV;
   size_t ws = (size_t)M / 32 + 1;
-  return (size_t)16 * Kc + (size_t)2 * M + (size_t)LV * ws * (4 + 2);
+  return (size_t)key_bytes * M + (size_t)2 * M + (size_t)LV * ws * (4 + 2);
 }
 
 void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
                            const SmoothPlan& pl, SgOut o, Dirty d, cudaStream_t st) {
   int th = median_threads(pl);
-  size_t smem = median_smem_bytes(pl.Kc);
+  size_t smem = median_smem_bytes(pl.Kc, pl.fp32_keys ? 4 : 8);
   int bl = persistent_grid(pl, pl.nch + 1, pl.res_median);
-  k_median_wm<<<bl, th, smem, st>>>(skey, srank, n, pl, o, d);
+  if (pl.fp32_keys)
+    k_median_wm<uint32_t><<<bl, th, smem, st>>>((const uint32_t*)skey, srank, n, pl, o, d);
+  else
+    k_median_wm<u64><<<bl, th, smem, st>>>(skey, srank, n, pl, o, d);
 }
 
 // ============================================================================ window mean
@@ -1137,12 +1186,13 @@ __device__ double rho2_exact(const Grid& g, const Tables& tb, const double* __re
 
 // FP32 screen sum of candidate c over the bins t0 + off, t0 + off + step, ... < t1 of its
 // sweep (t relative to its first bin ka); kcount counts the terms.
-__device__ __forceinline__ float screen_part(const Cands& cd, long long c, const Grid& g,
-                                             const Tables& tb, const float* __restrict__ inv_f,
-                                             int off, int step, int& kcount) {
-  const int ka = cd.ka[c];
-  const int nbin = cd.nbin[c];
-  const float a2f = cd.a2f[c];
+__device__ __forceinline__ float screen_part(const Cands& cd, long long c, const int4 pk,
+                                             const Grid& g, const Tables& tb,
+                                             const float* __restrict__ inv_f, int off, int step,
+                                             int& kcount) {
+  const int ka = pk.x;
+  const int nbin = pk.y;
+  const float a2f = __int_as_float(pk.z);
   float r2 = 0.0f;
   kcount = 0;
   if (nbin == 1) {
@@ -1152,7 +1202,8 @@ __device__ __forceinline__ float screen_part(const Cands& cd, long long c, const
     }
     return r2;
   }
-  const float flo = cd.flo[c], fhi = __fadd_rn(flo, cd.len[c]), invlen = 1.0f / cd.len[c];
+  const float flo = __int_as_float(pk.w), len = cd.len[c];
+  const float fhi = __fadd_rn(flo, len), invlen = 1.0f / len;
   const int t0 = ka < 0 ? -ka : 0;
   const int t1 = (long long)ka + nbin > g.nb ? (int)(g.nb - ka) : nbin;
   for (int t = t0 + off; t < t1; t += step) {
@@ -1230,9 +1281,11 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
        cbase < nlive; cbase += nwarps * 32) {
     bool todo = false, wide = false;
     const long long c = cbase + lane;
+    int4 pk = make_int4(0, 0, 0, 0);
     if (c < nlive && !cd.res[c]) {
-      const int ka = cd.ka[c];
-      const int nbin = cd.nbin[c];
+      pk = cd.pk[c];
+      const int ka = pk.x;
+      const int nbin = pk.y;
       long long c0 = ka < 0 ? 0 : ka / Kc;
       long long kl = (long long)ka + nbin - 1;
       if (kl > g.nb - 1) kl = g.nb - 1;
@@ -1244,7 +1297,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
     }
     if (todo && !wide) {
       int kcount;
-      const float r2 = screen_part(cd, c, g, tb, inv_f, 0, 1, kcount);
+      const float r2 = screen_part(cd, c, pk, g, tb, inv_f, 0, 1, kcount);
       int dec = screen_decide(r2, kcount, th2f, mode);
       if (dec < 0) {
         ++local_exact;
@@ -1262,7 +1315,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
       const long long cw = cbase + (__ffs(pending) - 1);
       pending &= pending - 1;
       int kcount;
-      float r2 = screen_part(cd, cw, g, tb, inv_f, lane, 32, kcount);
+      float r2 = screen_part(cd, cw, cd.pk[cw], g, tb, inv_f, lane, 32, kcount);
       // butterfly sums: every lane ends with the same values
       for (int o = 16; o > 0; o >>= 1) {
         r2 = __fadd_rn(r2, __shfl_xor_sync(0xFFFFFFFFu, r2, o));
@@ -1394,18 +1447,32 @@ void plan_grids(SmoothPlan& pl) {
   with_sort_kernel(pl, [&](auto kern) {
     pl.res_sort = resident_ctas(pl, kern, sort_threads(pl), sort_smem(pl));
   });
-  pl.res_median = resident_ctas(pl, k_median_wm, median_threads(pl), median_smem_bytes(pl.Kc));
+  if (pl.fp32_keys)
+    pl.res_median = resident_ctas(pl, k_median_wm<uint32_t>, median_threads(pl),
+                                  median_smem_bytes(pl.Kc, 4));
+  else
+    pl.res_median = resident_ctas(pl, k_median_wm<u64>, median_threads(pl),
+                                  median_smem_bytes(pl.Kc, 8));
   pl.res_prefix = resident_ctas(pl, k_chunk_prefix, pl.Kc < 1024 ? pl.Kc : 1024, 0);
   pl.res_mean = resident_ctas(pl, k_window_mean, mean_threads(pl), 0);
 }
 
 void configure_kernels() {
   cudaFuncSetAttribute(k_prepass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepassSmem);
-  cudaFuncSetAttribute(k_chunk_sort<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaFuncSetAttribute(k_chunk_sort<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaFuncSetAttribute(k_chunk_sort<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaFuncSetAttribute(k_median_wm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)median_smem_bytes(kMaxWindow));
+  SmoothPlan p64 = {}, p32 = {};
+  p32.fp32_keys = 1;
+  for (int kp : {64, 4096, 8192}) {
+    p64.kpad = p32.kpad = kp;
+    auto set = [](auto kern) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    };
+    with_sort_kernel(p64, set);
+    with_sort_kernel(p32, set);
+  }
+  cudaFuncSetAttribute(k_median_wm<u64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)median_smem_bytes(kMaxWindow, 8));
+  cudaFuncSetAttribute(k_median_wm<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)median_smem_bytes(kMaxWindow, 4));
 }
 
 }  // namespace gbsub

@@ -9,11 +9,11 @@ namespace gbsub {
 // Candidates that can still be resolved (rho_0 > rho_th), structure of arrays.
 struct Cands {
   long long* src;     // index in the catalog
-  int* ka;            // first bin of the sweep, relative to k_lo (may be < 0)
-  int* nbin;          // bins touched by the sweep (kb - ka + 1)
-  float* a2f;         // A^2 * 2^160 (FP32 screen)
-  float* flo;         // lo - ka (FP32 screen)
-  float* len;         // hi - lo (FP32 screen)
+  int4* pk;           // the screen's 16-byte record, read in one load:
+                      //   x = ka, first bin of the sweep relative to k_lo (may be < 0)
+                      //   y = nbin, bins touched by the sweep (kb - ka + 1)
+                      //   z = bits of A^2 * 2^160 (FP32), w = bits of lo - ka (FP32)
+  float* len;         // hi - lo (FP32 screen of sweeps over more than one bin)
   double* a2;         // A^2 (exact path)
   double* lo;         // sweep endpoints in bin units (exact path)
   double* hi;
@@ -64,6 +64,8 @@ struct SmoothPlan {
   int nch;      // chunks
   int kpad;     // power of two >= Kc (sort width)
   int nsm;      // SMs for persistent grids (0: one CTA per work item)
+  int fp32_keys;  // median on the FP32-rounded values (mixed precision): 4-byte keys
+  double key_scale;  // power of two the values are scaled by before rounding to FP32
   int res_sort, res_median, res_prefix, res_mean;  // CTAs resident at once (plan_grids)
 };
 
@@ -165,7 +167,7 @@ void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned lo
 // changed.
 void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
                            const SmoothPlan& pl, SgOut o, Dirty d, cudaStream_t st);
-size_t median_smem_bytes(int Kc);
+size_t median_smem_bytes(int Kc, int key_bytes);
 
 // Exact 128-bit prefix sums of the input inside each chunk at a per-chunk scale sig[b];
 // uflow[b] = 1 when an input > 0 of chunk b is below one unit.  x_out (may be null)

@@ -102,6 +102,8 @@ extern "C" int sub_running_mean_noalloc(const double* x, double* out, int64_t n,
   pl.nch = (int)((n + pl.Kc - 1) / pl.Kc);
   pl.kpad = 0;
   pl.nsm = 0;  // one CTA per chunk
+  pl.fp32_keys = 0;
+  pl.key_scale = 1.0;
   pl.res_sort = pl.res_median = pl.res_prefix = pl.res_mean = 0;
   unsigned long long* pre_lo = base;
   unsigned long long* pre_hi = base + kCells;

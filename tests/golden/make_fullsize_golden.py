@@ -3,16 +3,21 @@ workload (3e7 sources, T_obs = 4 yr, band 0.1-10 mHz, W = 1000, rho_th = 7), for
 median-then-mean and the mean estimators.
 
 Calls only the oracle and the seeded input generator.  Stored: iterations, candidate and
-resolved counts, a SHA-256 of the sorted resolved indices, and S_gal at 4096 bins drawn
-with a fixed seed (as exact hex floats).  Takes a few minutes (the oracle is one thread).
+resolved counts, a SHA-256 of the sorted resolved indices, the indices themselves (gaps
+between sorted indices as little-endian int32, zlib-compressed, base64 text) and S_gal at
+4096 bins drawn with a fixed seed (as exact hex floats).  Takes a few minutes (the oracle
+is one thread).
 
     python tests/golden/make_fullsize_golden.py
 """
+import base64
 import hashlib
 import json
 import os
 import sys
 import time
+
+import zlib
 
 import numpy as np
 
@@ -28,6 +33,17 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fullsize_nb3e7_4
 def resolved_digest(mask):
     idx = np.nonzero(mask)[0].astype(np.int64)
     return hashlib.sha256(idx.tobytes()).hexdigest()
+
+
+def encode_indices(mask):
+    idx = np.nonzero(mask)[0].astype(np.int64)
+    gaps = np.diff(np.concatenate([[0], idx])).astype("<i4")
+    return base64.b64encode(zlib.compress(gaps.tobytes(), 9)).decode("ascii")
+
+
+def decode_indices(text):
+    gaps = np.frombuffer(zlib.decompress(base64.b64decode(text)), dtype="<i4").astype(np.int64)
+    return np.cumsum(gaps)
 
 
 def main():
@@ -47,6 +63,7 @@ def main():
             "iterations": r["iterations"], "converged": r["converged"],
             "n_candidates": r["n_candidates"], "n_resolved": r["n_resolved"],
             "resolved_sha256": resolved_digest(r["resolved"]),
+            "resolved_gaps_b64z": encode_indices(r["resolved"]),
             "S_gal_sample": [float(x).hex() for x in r["S_gal"][sample]],
             "oracle_seconds": time.time() - t,
         }

@@ -298,3 +298,46 @@ def test_errors_are_reported():
         with pytest.raises(gbsub.SubError) as ei:
             s.load(np.zeros(10_000_000), np.zeros(10_000_000), np.zeros(10_000_000))
         assert ei.value.code == gbsub.EBUDGET
+
+
+def mixed_vs_oracle(A, f, fdot, T, est, W, f_max=1e-2):
+    """Mixed precision (FP32 SNR decisions, FP32 median selection, exact fixed-point sums)
+    against the FP64 oracle: every source decided differently lies within the FP32 screen's
+    error of rho_th, and S_gal is within 1e-5 away from the bins of those sources."""
+    prm = oracle.make_params(T_obs=T, estimator=est, window=W, f_max=f_max)
+    ref = oracle.run(prm, A, f, fdot)
+    with gbsub.Subtraction(T_obs=T, window=W, estimator=est, f_max=f_max,
+                           precision=gbsub.MIXED) as s:
+        s.load(A, f, fdot)
+        st = s.run()
+        sg = s.spectrum()
+        res = s.resolved().astype(bool)
+    diff = np.nonzero(res != ref["resolved"])[0]
+    if len(diff):
+        k_lo, n = oracle.grid(T, 1e-4, f_max)
+        S, R = oracle.tables(T, k_lo, n, True)
+        r2 = oracle.snr2(T, k_lo, n, S, R, ref["S_gal"], A[diff], f[diff], fdot[diff])
+        assert np.all(np.abs(r2 / 49.0 - 1.0) < 1e-4), r2
+    keep = np.ones(len(sg), dtype=bool)
+    k_lo = ref["k_lo"]
+    for s_ in diff:
+        k = int(np.floor(f[s_] * T + 0.5)) - k_lo
+        keep[max(0, k - 2 * W):k + 2 * W + 1] = False
+    err = rel_err(sg[keep], ref["S_gal"][keep])
+    assert err <= 1e-5, err
+    return st, ref, len(diff), err
+
+
+@pytest.mark.parametrize("est", [gbsub.MEAN, gbsub.MEDIAN, gbsub.MEDIAN_MEAN])
+def test_mixed_precision_dense_catalog(dense, est):
+    A, f, fdot = dense
+    st, ref, ndiff, err = mixed_vs_oracle(A, f, fdot, synth.YEAR, est, 30, f_max=2e-3)
+    assert ndiff <= max(1, 1e-4 * ref["n_resolved"])
+
+
+def test_mixed_precision_1e6_workload():
+    w = synth.workload("nb1e6_4yr")
+    A, f, fdot = synth.catalog(w.n_sources, w.seed, w.pop)
+    st, ref, ndiff, err = mixed_vs_oracle(A, f, fdot, w.T_obs, gbsub.MEDIAN_MEAN, 1000)
+    assert ndiff == 0
+    assert st.iterations == ref["iterations"]
