@@ -229,6 +229,110 @@ int sub_running_mean_noalloc(const double* x, double* out, int64_t n, int32_t wi
 /* Bytes of device memory the context holds now. */
 int64_t sub_device_bytes(const sub_ctx* ctx);
 
+/* ------------------------------------------------------------------ batches
+ * Many catalogs in one launch.  The per-iteration kernels of a single catalog leave most
+ * of the GPU idle (only the few chunks that changed are recomputed), so a batch launches
+ * every context's whole run (catalog pass and device loop, App. D) as independent
+ * branches of one CUDA graph; their kernels overlap on the SMs.  Results are the same
+ * bits as each context run alone.
+ *   ctxs : n >= 1 distinct contexts on one device, each with its own parameters
+ *          (T_obs, window, estimator, precision ...) and, before sub_batch_run, a catalog.
+ *          The batch borrows them: destroy the batch before any of its contexts.
+ * The graph is built on the first run and rebuilt when a context's catalog size changes.
+ * Errors: SUB_EINVAL (bad list; message in sub_last_error(NULL)), SUB_ECUDA. */
+typedef struct sub_batch sub_batch;
+int sub_batch_create(sub_ctx* const* ctxs, int32_t n, sub_batch** out);
+
+/* Run the batch and wait for it.  stats (may be null) receives n sub_stats, in the order
+ * of ctxs; each context's results are then read with sub_get_spectrum etc.  Returns
+ * SUB_OK, SUB_ENOTCONVERGED if any context stopped at max_iter, or the first error. */
+int sub_batch_run(sub_batch* b, sub_stats* stats);
+
+/* Device time of the last sub_batch_run, in milliseconds (CUDA events around the launch). */
+float sub_batch_last_ms(const sub_batch* b);
+
+/* Reason for the last failure of a call on b; never null. */
+const char* sub_batch_last_error(const sub_batch* b);
+
+/* Free the batch (its contexts stay). */
+void sub_batch_destroy(sub_batch* b);
+
+/* Run the context's chunk kernels, catalog pass and SNR on persistent grids of 1/div of
+ * the GPU's resident CTAs (div in 1 .. 64; 1 = the whole GPU, the default).  Smaller grids
+ * suit batches, where many catalogs share the GPU; results do not depend on div.
+ * Errors: SUB_EINVAL. */
+int sub_set_grid_div(sub_ctx* ctx, int32_t div);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop for subtraction jobs as a sampler emits them.  Jobs are queued in
+ * arrival order and admitted while fewer than max_inflight run and a device-memory budget
+ * allows; each admitted job runs on a pooled context (one per T_obs and catalog size
+ * class, created on demand, the least recently used idle ones destroyed when the budget
+ * needs room) on its own stream, so jobs overlap on the GPU (continuous batching).  A
+ * job's latency runs from sub_server_submit to its results being in the caller's
+ * buffers.  All jobs of a server share the parameters below; T_obs is per job. */
+typedef struct {
+  uint64_t hbm_budget;   /* bytes of device memory for all contexts; 0 = unlimited     */
+  int32_t max_inflight;  /* jobs on the GPU at once, 1 .. 256 (default 16)             */
+  int32_t window;        /* as sub_params                                              */
+  int32_t estimator;
+  int32_t precision;
+  int32_t max_iter;
+  int32_t tdi2;
+  int32_t grid_div;      /* persistent-grid divisor of every context (sub_set_grid_div) */
+  int32_t reserved;
+  double f_min, f_max;
+  double rho_th, kappa;
+} sub_server_params;
+
+typedef struct {
+  int64_t job_id;
+  int32_t status;        /* SUB_OK, SUB_ENOTCONVERGED, or the error that ended the job  */
+  int32_t reserved;
+  sub_stats stats;
+  double latency_ms;     /* submit -> results in the caller's buffers                  */
+  double queue_ms;       /* submit -> admitted                                          */
+  double gpu_ms;         /* device time of the run (catalog pass + loop)                */
+} sub_job_result;
+
+typedef struct {
+  int64_t queued;
+  int64_t contexts_created;
+  int64_t device_bytes;       /* held by the pooled contexts now */
+  int64_t peak_device_bytes;
+  int32_t inflight;
+  int32_t contexts;
+} sub_server_stats;
+
+int sub_server_params_default(sub_server_params* p);
+
+/* Start a server (a worker thread on the current device).  Errors: SUB_EINVAL, SUB_ECUDA. */
+typedef struct sub_server sub_server;
+int sub_server_create(const sub_server_params* p, sub_server** out);
+
+/* Queue a job and return at once.  A, f, fdot: host arrays of n sources (pinned memory
+ * makes the copies asynchronous); S_gal: host buffer of cap >= n_bins(T_obs) doubles, or
+ * null; mask: host buffer of n bytes (1 = resolved), or null.  All must stay valid and
+ * untouched until the job's result comes out of sub_server_poll.  A job larger than the
+ * whole budget ends with SUB_EBUDGET.  Errors: SUB_EINVAL, SUB_ESTATE (server stopping). */
+int sub_server_submit(sub_server* s, int64_t job_id, double T_obs, const double* A,
+                      const double* f, const double* fdot, int64_t n, double* S_gal,
+                      int64_t cap, uint8_t* mask);
+
+/* Move up to cap finished jobs into out, waiting up to timeout_ms for the first one
+ * (0: no wait).  Returns how many were written. */
+int32_t sub_server_poll(sub_server* s, sub_job_result* out, int32_t cap, int32_t timeout_ms);
+
+/* Queue, in-flight and memory counters. */
+int sub_server_info(sub_server* s, sub_server_stats* st);
+
+/* Reason for the last rejected submission; never null. */
+const char* sub_server_last_error(sub_server* s);
+
+/* Stop: jobs not yet admitted are dropped, running ones finish; then every context is
+ * freed. */
+void sub_server_destroy(sub_server* s);
+
 /* Free the context and everything it owns; null is allowed. */
 void sub_destroy(sub_ctx* ctx);
 

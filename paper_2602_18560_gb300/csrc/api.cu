@@ -24,59 +24,7 @@
 
 using namespace gbsub;
 
-struct sub_ctx {
-  sub_params p;
-  Grid grid;
-  SmoothPlan plan;
-  cudaStream_t stream = nullptr;   // where work is issued
-  bool own_stream = false;
-  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
-  int nsm = 0;
-  int device = 0;
-  // bookkeeping
-  std::vector<std::pair<void*, int64_t>> allocs;
-  int64_t bytes = 0;
-  std::string err;
-  // tables
-  double *S = nullptr, *R = nullptr, *gq = nullptr;
-  float *Gf = nullptr, *invSf = nullptr;
-  // spectrum and smoothing buffers
-  unsigned long long* acc = nullptr;  // 4 words per bin
-  AccReplicas rep = {nullptr, 0};     // private copies of the first bins (catalog pass)
-  double *P = nullptr, *M = nullptr, *Sg = nullptr;
-  double* estimate_in = nullptr;  // input copy of sub_estimate
-  float* inv_f = nullptr;
-  int* sig = nullptr;
-  unsigned char* dirty = nullptr;  // two sets of one byte per chunk
-  int* lists = nullptr;            // work lists of the chunk kernels [kNumLists][nch + 1]
-  int* list_counts = nullptr;      // [kNumLists]
-  unsigned long long* skey = nullptr;
-  uint16_t* srank = nullptr;
-  unsigned long long *pre_lo = nullptr, *pre_hi = nullptr;
-  unsigned* uflow = nullptr;
-  // catalog and per-source buffers
-  int64_t N = -1;        // sources loaded (-1: none)
-  int64_t cap_N = 0;     // capacity of the per-source buffers
-  double *A = nullptr, *f = nullptr, *fdot = nullptr;
-  Cands cd = {};
-  unsigned char* resolved = nullptr;
-  // run state
-  RunState* rs = nullptr;
-  int* new_hist = nullptr;
-  RunState* h_rs = nullptr;  // pinned copy
-  bool ran = false;
-  // graph
-  cudaGraphExec_t exec = nullptr;
-  cudaGraph_t graph = nullptr;
-  int64_t graph_N = -1;
-  bool use_graph = true;
-  // timing
-  cudaEvent_t ev_start = nullptr, ev_pre = nullptr, ev_end = nullptr;
-  cudaEvent_t ev_k[2] = {nullptr, nullptr};
-  float prof_ms[SUB_K_COUNT];
-  int prof_n[SUB_K_COUNT];
-  bool profiling = false;
-};
+#include "context.cuh"
 
 static std::string g_create_err = "no error";
 
@@ -245,6 +193,7 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   if (e != cudaSuccess) { c->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e); return fail(SUB_ECUDA); }
   configure_kernels();
   plan_grids(c->plan);
+  c->nsm_run = c->nsm;
   {
     cudaEvent_t* evs[] = {&c->ev_start, &c->ev_pre, &c->ev_end, &c->ev_k[0], &c->ev_k[1]};
     for (cudaEvent_t* ev : evs) {
@@ -424,7 +373,7 @@ static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
   {
     KTimer t(c, st, SUB_K_PREPASS);
     launch_prepass(c->A, c->f, c->fdot, c->N, c->grid, tables_of(c), thr_kappa_of(c),
-                   thr_live_of(c), c->acc, c->rep, c->cd, c->rs, c->nsm, st);
+                   thr_live_of(c), c->acc, c->rep, c->cd, c->rs, c->nsm_run, st);
   }
   return cudaGetLastError();
 }
@@ -489,18 +438,15 @@ static cudaError_t enqueue_body(sub_ctx* c, cudaStream_t st, unsigned long long 
     KTimer t(c, st, SUB_K_SNR);
     launch_snr_resolve(c->cd, c->N > 0 ? c->N : 1, c->grid, tables_of(c), c->Sg, c->inv_f, th2,
                        c->p.conv_rtol, snr_mode(c), c->resolved, c->acc, rs, dirty_of(c, true),
-                       c->plan.Kc, sg_radius_of(c), c->nsm, st);
+                       c->plan.Kc, sg_radius_of(c), c->nsm_run, st);
   }
   { KTimer t(c, st, SUB_K_CONTROL); launch_control(rs, c->p.max_iter, c->p.conv_rtol, c->new_hist, handle, use_cond, c->dirty, c->plan.nch, c->lists, c->list_counts, st); }
   return cudaGetLastError();
 }
 
-static int build_graph(sub_ctx* c) {
-  drop_graph(c);
-  cudaGraph_t g = nullptr, pre = nullptr;
-  cudaError_t e = cudaGraphCreate(&g, 0);
-  if (e) { set_err(c, "cudaGraphCreate: %s", cudaGetErrorString(e)); return SUB_ECUDA; }
-  e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+cudaError_t gbsub::ctx_add_run_nodes(sub_ctx* c, cudaGraph_t g, cudaGraphNode_t* last) {
+  cudaGraph_t pre = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (!e) {
     // external records become event nodes of the graph (timing the run inside the graph)
     cudaError_t e2 = cudaEventRecordWithFlags(c->ev_start, c->cap_stream, cudaEventRecordExternal);
@@ -533,6 +479,17 @@ static int build_graph(sub_ctx* c) {
   }
   cudaGraphNode_t end_node = nullptr;
   if (!e) e = cudaGraphAddEventRecordNode(&end_node, g, &cond_node, 1, c->ev_end);
+  if (!e) *last = end_node;
+  return e;
+}
+
+static int build_graph(sub_ctx* c) {
+  drop_graph(c);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e) { set_err(c, "cudaGraphCreate: %s", cudaGetErrorString(e)); return SUB_ECUDA; }
+  cudaGraphNode_t last = nullptr;
+  e = ctx_add_run_nodes(c, g, &last);
   if (!e) e = cudaGraphInstantiate(&c->exec, g, 0);
   if (e) {
     cudaGetLastError();
@@ -589,6 +546,29 @@ static int fill_stats(sub_ctx* c, sub_stats* st) {
     st->n_exact = (int64_t)r.nexact;
   }
   return status;
+}
+
+
+void gbsub::ctx_set_err(sub_ctx* c, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_create_err = buf;
+}
+
+int gbsub::ctx_fill_stats(sub_ctx* c, sub_stats* st) { return fill_stats(c, st); }
+
+void gbsub::ctx_set_grid_div(sub_ctx* c, int div) {
+  if (div < 1) div = 1;
+  if (div == c->grid_div) return;
+  drop_graph(c);
+  c->grid_div = div;
+  plan_grids(c->plan);
+  int* res[] = {&c->plan.res_sort, &c->plan.res_median, &c->plan.res_prefix, &c->plan.res_mean};
+  for (int* r : res) *r = (*r / div) > 0 ? *r / div : 1;
+  c->nsm_run = c->nsm / div > 0 ? c->nsm / div : 1;
 }
 
 extern "C" int sub_run(sub_ctx* c, sub_stats* st) {

@@ -1,0 +1,541 @@
+// Batches and serving on top of the subtraction contexts.
+//
+// A batch runs many catalogs at once: one CUDA graph holds every context's catalog pass and
+// device loop as independent branches and is launched once.  The per-iteration kernels of
+// one catalog leave most of the GPU idle (a few chunks change per iteration), so catalogs
+// run side by side overlap on the SMs.
+//
+// A server accepts subtraction jobs as they arrive (host catalogs and host result buffers),
+// admits them in arrival order while a device-memory budget and an in-flight limit allow,
+// runs each on a pooled context with its own stream (jobs overlap on the GPU: continuous
+// batching), and hands back each job's statistics with its latency from submission to
+// results in the caller's buffers.  Completion is observed by a host function enqueued
+// behind the result copies, so the latency is not quantised by polling.
+
+#include <algorithm>
+#include <cmath>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "context.cuh"
+
+using namespace gbsub;
+using Clock = std::chrono::steady_clock;
+
+// ============================================================================ batch
+
+struct sub_batch {
+  std::vector<sub_ctx*> ctxs;
+  std::vector<int64_t> sizes;  // catalog sizes the graph was built for
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  float last_ms = 0.0f;
+  std::string err;
+};
+
+static void batch_err(sub_batch* b, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (b) b->err = buf;
+}
+
+static void batch_drop_graph(sub_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->sizes.clear();
+}
+
+static int batch_build(sub_batch* b) {
+  batch_drop_graph(b);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  for (size_t i = 0; !e && i < b->ctxs.size(); ++i) {
+    cudaGraphNode_t last = nullptr;
+    e = ctx_add_run_nodes(b->ctxs[i], g, &last);
+  }
+  if (!e) e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    b->exec = nullptr;
+    batch_err(b, "batch graph build failed: %s", cudaGetErrorString(e));
+    return SUB_ECUDA;
+  }
+  b->graph = g;
+  for (sub_ctx* c : b->ctxs) b->sizes.push_back(c->N);
+  return SUB_OK;
+}
+
+extern "C" int sub_batch_create(sub_ctx* const* ctxs, int32_t n, sub_batch** out) {
+  if (!out) return SUB_EINVAL;
+  *out = nullptr;
+  if (!ctxs || n < 1) {
+    set_global_error("sub_batch_create: need at least one context");
+    return SUB_EINVAL;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    if (!ctxs[i]) {
+      set_global_error("sub_batch_create: null context");
+      return SUB_EINVAL;
+    }
+    for (int32_t k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) {
+        set_global_error("sub_batch_create: a context appears twice");
+        return SUB_EINVAL;
+      }
+    if (ctxs[i]->device != ctxs[0]->device) {
+      set_global_error("sub_batch_create: contexts on different devices");
+      return SUB_EINVAL;
+    }
+  }
+  sub_batch* b = new (std::nothrow) sub_batch;
+  if (!b) return SUB_ENOMEM;
+  b->ctxs.assign(ctxs, ctxs + n);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (!e) e = cudaEventCreate(&b->ev0);
+  if (!e) e = cudaEventCreate(&b->ev1);
+  if (e) {
+    set_global_error("sub_batch_create: stream or event creation failed");
+    sub_batch_destroy(b);
+    return SUB_ECUDA;
+  }
+  *out = b;
+  return SUB_OK;
+}
+
+extern "C" int sub_batch_run(sub_batch* b, sub_stats* stats) {
+  if (!b) return SUB_EINVAL;
+  for (sub_ctx* c : b->ctxs)
+    if (c->N < 0) {
+      batch_err(b, "a context of the batch has no catalog");
+      return SUB_ESTATE;
+    }
+  bool stale = b->exec == nullptr || b->sizes.size() != b->ctxs.size();
+  for (size_t i = 0; !stale && i < b->ctxs.size(); ++i) stale = b->sizes[i] != b->ctxs[i]->N;
+  if (stale) {
+    int rc = batch_build(b);
+    if (rc) return rc;
+  }
+  // each context's own work (catalog copies) is ordered before the batch
+  for (sub_ctx* c : b->ctxs) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e) {
+      batch_err(b, "context stream: %s", cudaGetErrorString(e));
+      return SUB_ECUDA;
+    }
+  }
+  cudaError_t e = cudaEventRecord(b->ev0, b->stream);
+  if (!e) e = cudaGraphLaunch(b->exec, b->stream);
+  if (!e) e = cudaEventRecord(b->ev1, b->stream);
+  if (!e) e = cudaStreamSynchronize(b->stream);
+  if (!e) e = cudaEventElapsedTime(&b->last_ms, b->ev0, b->ev1);
+  if (e) {
+    batch_err(b, "batch launch: %s", cudaGetErrorString(e));
+    return SUB_ECUDA;
+  }
+  int status = SUB_OK;
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    b->ctxs[i]->ran = true;
+    int rc = ctx_fill_stats(b->ctxs[i], stats ? &stats[i] : nullptr);
+    if (rc != SUB_OK && (status == SUB_OK || status == SUB_ENOTCONVERGED)) status = rc;
+  }
+  return status;
+}
+
+extern "C" float sub_batch_last_ms(const sub_batch* b) { return b ? b->last_ms : 0.0f; }
+
+extern "C" const char* sub_batch_last_error(const sub_batch* b) {
+  return b ? b->err.c_str() : "null batch";
+}
+
+extern "C" void sub_batch_destroy(sub_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+extern "C" int sub_set_grid_div(sub_ctx* c, int32_t div) {
+  if (!c) return SUB_EINVAL;
+  if (div < 1 || div > 64) {
+    ctx_set_err(c, "grid divisor %d is outside 1 .. 64", div);
+    return SUB_EINVAL;
+  }
+  ctx_set_grid_div(c, div);
+  return SUB_OK;
+}
+
+// ============================================================================ server
+
+namespace {
+
+struct Job {
+  int64_t id = 0;
+  double T_obs = 0.0;
+  const double *A = nullptr, *f = nullptr, *fdot = nullptr;
+  int64_t n = 0;
+  double* sg_out = nullptr;
+  int64_t cap = 0;
+  uint8_t* mask_out = nullptr;
+  Clock::time_point t_submit, t_admit, t_done;
+};
+
+struct Slot {
+  sub_server* srv = nullptr;
+  sub_ctx* ctx = nullptr;
+  bool busy = false;
+  Job job;
+  uint64_t last_use = 0;
+};
+
+}  // namespace
+
+struct sub_server {
+  sub_server_params p;
+  int device = 0;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job> queue;
+  std::vector<Slot*> slots;
+  std::vector<Slot*> finished;
+  std::vector<sub_job_result> results;
+  bool stop = false;
+  int inflight = 0;
+  int64_t pool_bytes = 0, peak_bytes = 0;
+  uint64_t tick = 0;
+  int64_t contexts_created = 0;
+  std::string err;
+};
+
+static int64_t bins_of(double T_obs, double f_min, double f_max) {
+  int64_t lo = (int64_t)std::ceil(f_min * T_obs), hi = (int64_t)std::floor(f_max * T_obs);
+  return hi >= lo ? hi - lo + 1 : 0;
+}
+
+// Device bytes of a context before it exists: the per-bin buffers (about 130 B/bin), the
+// 16 MB of hot-bin replicas and the per-source buffers (78 B/source), rounded up.
+static int64_t predicted_bytes(const sub_server* s, double T_obs, int64_t n) {
+  const int64_t nb = bins_of(T_obs, s->p.f_min, s->p.f_max);
+  return nb * 136 + ((int64_t)24 << 20) + n * 80;
+}
+
+static void CUDART_CB job_done(void* arg) {
+  Slot* sl = static_cast<Slot*>(arg);
+  sub_server* s = sl->srv;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    sl->job.t_done = Clock::now();
+    s->finished.push_back(sl);
+  }
+  s->cv_work.notify_one();
+}
+
+static double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+static void push_result(sub_server* s, const Job& j, int status, const sub_stats* st,
+                        float gpu_ms) {
+  sub_job_result r;
+  std::memset(&r, 0, sizeof(r));
+  r.job_id = j.id;
+  r.status = status;
+  if (st) r.stats = *st;
+  r.latency_ms = ms_between(j.t_submit, j.t_done);
+  r.queue_ms = ms_between(j.t_submit, j.t_admit);
+  r.gpu_ms = gpu_ms;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->results.push_back(r);
+  s->cv_done.notify_all();
+}
+
+// A context for job j: an idle one with the same T_obs and room for the catalog, else a new
+// one if the budget allows (idle contexts are destroyed, least recently used first, to make
+// room).  Returns null when the job must wait for running jobs to finish.
+static Slot* acquire_slot(sub_server* s, const Job& j, int* fail_status) {
+  *fail_status = SUB_OK;
+  Slot* best = nullptr;
+  for (Slot* sl : s->slots) {
+    if (sl->busy || sl->ctx->p.T_obs != j.T_obs || sl->ctx->cap_N < j.n) continue;
+    if (!best || sl->ctx->cap_N < best->ctx->cap_N) best = sl;
+  }
+  if (best) return best;
+  const int64_t need = predicted_bytes(s, j.T_obs, j.n);
+  const uint64_t budget = s->p.hbm_budget;
+  if (budget && (uint64_t)need > budget) {
+    *fail_status = SUB_EBUDGET;
+    return nullptr;
+  }
+  while (budget && (uint64_t)(s->pool_bytes + need) > budget) {
+    Slot* victim = nullptr;
+    for (Slot* sl : s->slots)
+      if (!sl->busy && (!victim || sl->last_use < victim->last_use)) victim = sl;
+    if (!victim) return nullptr;
+    s->pool_bytes -= sub_device_bytes(victim->ctx);
+    sub_destroy(victim->ctx);
+    s->slots.erase(std::find(s->slots.begin(), s->slots.end(), victim));
+    delete victim;
+  }
+  sub_params prm;
+  sub_params_default(&prm);
+  prm.T_obs = j.T_obs;
+  prm.f_min = s->p.f_min;
+  prm.f_max = s->p.f_max;
+  prm.window = s->p.window;
+  prm.estimator = s->p.estimator;
+  prm.rho_th = s->p.rho_th;
+  prm.kappa = s->p.kappa;
+  prm.max_iter = s->p.max_iter;
+  prm.tdi2 = s->p.tdi2;
+  prm.precision = s->p.precision;
+  sub_ctx* c = nullptr;
+  int rc = sub_create(&prm, nullptr, &c);
+  if (rc) {
+    *fail_status = rc;
+    return nullptr;
+  }
+  if (s->p.grid_div > 1) sub_set_grid_div(c, s->p.grid_div);
+  Slot* sl = new Slot;
+  sl->srv = s;
+  sl->ctx = c;
+  s->slots.push_back(sl);
+  s->pool_bytes += sub_device_bytes(c);
+  s->contexts_created += 1;
+  return sl;
+}
+
+// Enqueue job j on slot sl: catalog in, run, results out, then the completion callback.
+static int launch_job(sub_server* s, Slot* sl, Job& j) {
+  sub_ctx* c = sl->ctx;
+  const int64_t before = sub_device_bytes(c);
+  int rc = sub_load_catalog(c, j.A, j.f, j.fdot, j.n, SUB_HOST);
+  s->pool_bytes += sub_device_bytes(c) - before;
+  if (rc) return rc;
+  rc = sub_run(c, nullptr);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (j.sg_out) e = cudaMemcpyAsync(j.sg_out, c->Sg, (size_t)c->grid.nb * 8,
+                                    cudaMemcpyDeviceToHost, c->stream);
+  if (!e && j.mask_out && j.n > 0)
+    e = cudaMemcpyAsync(j.mask_out, c->resolved, (size_t)j.n, cudaMemcpyDeviceToHost,
+                        c->stream);
+  sl->busy = true;
+  sl->job = j;
+  sl->last_use = ++s->tick;
+  if (!e) e = cudaLaunchHostFunc(c->stream, job_done, sl);
+  if (e) {
+    sl->busy = false;
+    return SUB_ECUDA;
+  }
+  return SUB_OK;
+}
+
+static void finalize(sub_server* s, Slot* sl) {
+  sub_stats st;
+  std::memset(&st, 0, sizeof(st));
+  int status = ctx_fill_stats(sl->ctx, &st);
+  float gpu_ms = 0.0f;
+  float pre = 0.0f, loop = 0.0f;
+  if (sub_get_timing(sl->ctx, &pre, &loop, &gpu_ms) != SUB_OK) gpu_ms = 0.0f;
+  Job j = sl->job;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    sl->busy = false;
+    s->inflight -= 1;
+  }
+  push_result(s, j, status, &st, gpu_ms);
+}
+
+static void worker_main(sub_server* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    std::vector<Slot*> fin;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait_for(lk, std::chrono::microseconds(200), [&] {
+        return s->stop || !s->finished.empty() ||
+               (!s->queue.empty() && s->inflight < s->p.max_inflight);
+      });
+      fin.swap(s->finished);
+      if (s->stop && s->inflight == 0 && fin.empty()) break;
+    }
+    for (Slot* sl : fin) finalize(s, sl);
+    for (;;) {
+      Job j;
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop || s->queue.empty() || s->inflight >= s->p.max_inflight) break;
+        j = s->queue.front();
+      }
+      int fail = SUB_OK;
+      Slot* sl = acquire_slot(s, j, &fail);
+      if (!sl && fail == SUB_OK) break;  // wait for memory to free up
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->queue.pop_front();
+        if (sl) s->inflight += 1;
+      }
+      j.t_admit = Clock::now();
+      if (!sl) {
+        j.t_done = j.t_admit;
+        push_result(s, j, fail, nullptr, 0.0f);
+        continue;
+      }
+      int rc = launch_job(s, sl, j);
+      if (s->pool_bytes > s->peak_bytes) s->peak_bytes = s->pool_bytes;
+      if (rc) {
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          s->inflight -= 1;
+        }
+        cudaStreamSynchronize(sl->ctx->stream);
+        j.t_done = Clock::now();
+        push_result(s, j, rc, nullptr, 0.0f);
+      }
+    }
+  }
+}
+
+extern "C" int sub_server_params_default(sub_server_params* p) {
+  if (!p) return SUB_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  sub_params d;
+  sub_params_default(&d);
+  p->hbm_budget = 0;
+  p->max_inflight = 16;
+  p->window = d.window;
+  p->estimator = d.estimator;
+  p->precision = d.precision;
+  p->max_iter = d.max_iter;
+  p->tdi2 = d.tdi2;
+  p->grid_div = 1;
+  p->f_min = d.f_min;
+  p->f_max = d.f_max;
+  p->rho_th = d.rho_th;
+  p->kappa = d.kappa;
+  return SUB_OK;
+}
+
+extern "C" int sub_server_create(const sub_server_params* p, sub_server** out) {
+  if (!out || !p) return SUB_EINVAL;
+  *out = nullptr;
+  if (p->max_inflight < 1 || p->max_inflight > 256 || p->grid_div < 1 || p->grid_div > 64) {
+    set_global_error("sub_server_create: max_inflight must be 1 .. 256, grid_div 1 .. 64");
+    return SUB_EINVAL;
+  }
+  sub_server* s = new (std::nothrow) sub_server;
+  if (!s) return SUB_ENOMEM;
+  s->p = *p;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    set_global_error("sub_server_create: no CUDA device");
+    return SUB_ECUDA;
+  }
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return SUB_OK;
+}
+
+extern "C" int sub_server_submit(sub_server* s, int64_t job_id, double T_obs, const double* A,
+                                 const double* f, const double* fdot, int64_t n, double* S_gal,
+                                 int64_t cap, uint8_t* mask) {
+  if (!s) return SUB_EINVAL;
+  if (n < 0 || (n > 0 && (!A || !f || !fdot)) || !(T_obs > 0.0)) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = "sub_server_submit: bad catalog or T_obs";
+    return SUB_EINVAL;
+  }
+  if (S_gal && cap < bins_of(T_obs, s->p.f_min, s->p.f_max)) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = "sub_server_submit: S_gal buffer smaller than the number of bins";
+    return SUB_EINVAL;
+  }
+  Job j;
+  j.id = job_id;
+  j.T_obs = T_obs;
+  j.A = A;
+  j.f = f;
+  j.fdot = fdot;
+  j.n = n;
+  j.sg_out = S_gal;
+  j.cap = cap;
+  j.mask_out = mask;
+  j.t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return SUB_ESTATE;
+    s->queue.push_back(j);
+  }
+  s->cv_work.notify_one();
+  return SUB_OK;
+}
+
+extern "C" int32_t sub_server_poll(sub_server* s, sub_job_result* out, int32_t cap,
+                                   int32_t timeout_ms) {
+  if (!s || !out || cap < 1) return 0;
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->results.empty() && timeout_ms > 0)
+    s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                        [&] { return !s->results.empty(); });
+  int32_t k = 0;
+  while (k < cap && !s->results.empty()) {
+    out[k++] = s->results.front();
+    s->results.erase(s->results.begin());
+  }
+  return k;
+}
+
+extern "C" int sub_server_info(sub_server* s, sub_server_stats* st) {
+  if (!s || !st) return SUB_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  st->queued = (int64_t)s->queue.size();
+  st->inflight = s->inflight;
+  st->contexts = (int32_t)s->slots.size();
+  st->device_bytes = s->pool_bytes;
+  st->peak_device_bytes = s->peak_bytes;
+  st->contexts_created = s->contexts_created;
+  return SUB_OK;
+}
+
+extern "C" const char* sub_server_last_error(sub_server* s) {
+  if (!s) return "null server";
+  std::lock_guard<std::mutex> lk(s->mu);
+  return s->err.empty() ? "no error" : s->err.c_str();
+}
+
+extern "C" void sub_server_destroy(sub_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->queue.clear();  // jobs not admitted yet are dropped
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (Slot* sl : s->slots) {
+    sub_destroy(sl->ctx);
+    delete sl;
+  }
+  delete s;
+}

@@ -59,12 +59,43 @@ class sub_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class sub_server_params(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
+        ("window", ctypes.c_int32), ("estimator", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tdi2", ctypes.c_int32),
+        ("grid_div", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("f_min", ctypes.c_double), ("f_max", ctypes.c_double),
+        ("rho_th", ctypes.c_double), ("kappa", ctypes.c_double),
+    ]
+
+
+class sub_job_result(ctypes.Structure):
+    _fields_ = [
+        ("job_id", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("stats", sub_stats), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+        ("gpu_ms", ctypes.c_double),
+    ]
+
+
+class sub_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("queued", ctypes.c_int64), ("contexts_created", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64), ("peak_device_bytes", ctypes.c_int64),
+        ("inflight", ctypes.c_int32), ("contexts", ctypes.c_int32),
+    ]
+
+
 _lib = None
 _lock = threading.Lock()
 EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_run", "sub_get_stats",
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
            "sub_get_tables", "sub_get_timing", "sub_profile", "sub_device_bytes", "sub_destroy",
-           "sub_last_error", "sub_running_mean_noalloc", "sub_get_power")
+           "sub_last_error", "sub_running_mean_noalloc", "sub_get_power", "sub_batch_create",
+           "sub_batch_run", "sub_batch_last_ms", "sub_batch_last_error", "sub_batch_destroy",
+           "sub_set_grid_div", "sub_server_params_default", "sub_server_create",
+           "sub_server_submit", "sub_server_poll", "sub_server_info", "sub_server_last_error",
+           "sub_server_destroy")
 KERNELS = ("prepass", "sort", "median", "prefix", "mean", "snr", "control")
 
 
@@ -103,6 +134,19 @@ def lib(build_if_missing: bool = True):
             "sub_destroy": (None, [P]),
             "sub_last_error": (ctypes.c_char_p, [P]),
             "sub_running_mean_noalloc": (i32, [P, P, i64, i32, P]),
+            "sub_batch_create": (i32, [P, i32, ctypes.POINTER(P)]),
+            "sub_batch_run": (i32, [P, P]),
+            "sub_batch_last_ms": (ctypes.c_float, [P]),
+            "sub_batch_last_error": (ctypes.c_char_p, [P]),
+            "sub_batch_destroy": (None, [P]),
+            "sub_set_grid_div": (i32, [P, i32]),
+            "sub_server_params_default": (i32, [ctypes.POINTER(sub_server_params)]),
+            "sub_server_create": (i32, [ctypes.POINTER(sub_server_params), ctypes.POINTER(P)]),
+            "sub_server_submit": (i32, [P, i64, ctypes.c_double, P, P, P, i64, P, i64, P]),
+            "sub_server_poll": (i32, [P, ctypes.POINTER(sub_job_result), i32, i32]),
+            "sub_server_info": (i32, [P, ctypes.POINTER(sub_server_stats)]),
+            "sub_server_last_error": (ctypes.c_char_p, [P]),
+            "sub_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -318,6 +362,138 @@ class Subtraction:
         if self.ctx:
             sub_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batches
+
+def sub_set_grid_div(ctx, div: int):
+    return _check(ctx, lib().sub_set_grid_div(ctx, int(div)))
+
+
+class Batch:
+    """Several ``Subtraction`` contexts run together in one graph launch
+    (``sub_batch_*``).  The contexts must outlive the batch."""
+
+    def __init__(self, subs):
+        self.subs = list(subs)
+        arr = (ctypes.c_void_p * len(self.subs))(*[s.ctx.value for s in self.subs])
+        self._arr = arr
+        b = ctypes.c_void_p()
+        rc = lib().sub_batch_create(arr, len(self.subs), ctypes.byref(b))
+        if rc != OK:
+            raise SubError(rc, lib().sub_last_error(None).decode())
+        self.b = b
+
+    def run(self):
+        """Run every catalog; returns the list of sub_stats."""
+        st = (sub_stats * len(self.subs))()
+        rc = lib().sub_batch_run(self.b, st)
+        if rc < 0 and rc != ENOTCONVERGED:
+            raise SubError(rc, lib().sub_batch_last_error(self.b).decode())
+        return list(st)
+
+    @property
+    def last_ms(self):
+        return float(lib().sub_batch_last_ms(self.b))
+
+    def close(self):
+        if self.b:
+            lib().sub_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+
+def sub_server_params_default(**overrides) -> sub_server_params:
+    p = sub_server_params()
+    _check(None, lib().sub_server_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Server:
+    """A request loop (``sub_server_*``): ``submit`` queues a job whose host buffers must stay
+    alive until ``poll`` returns its result."""
+
+    def __init__(self, params: sub_server_params | None = None, **kw):
+        self.params = params if params is not None else sub_server_params_default(**kw)
+        s = ctypes.c_void_p()
+        rc = lib().sub_server_create(ctypes.byref(self.params), ctypes.byref(s))
+        if rc != OK:
+            raise SubError(rc, lib().sub_last_error(None).decode())
+        self.s = s
+        self._keep = {}
+
+    def submit(self, job_id, T_obs, A, f, fdot, S_gal_out=None, mask_out=None):
+        """Queue a job; A, f, fdot, S_gal_out, mask_out are host arrays (numpy, or pinned
+        torch CPU tensors) kept referenced until the job comes back."""
+        (pa, wa, na), (pf, _, nf), (pd, _, nd) = (_ptr(A, np.float64), _ptr(f, np.float64),
+                                                  _ptr(fdot, np.float64))
+        if not (na == nf == nd) or wa != HOST:
+            raise ValueError("A, f, fdot must be host arrays of one length")
+        ps, ws_, ncap = _ptr(S_gal_out, np.float64)
+        pm, wm, nm = _ptr(mask_out, np.uint8)
+        if (S_gal_out is not None and ws_ != HOST) or (mask_out is not None and wm != HOST):
+            raise ValueError("result buffers must be host memory")
+        if mask_out is not None and nm < na:
+            raise ValueError("mask buffer smaller than the catalog")
+        rc = lib().sub_server_submit(self.s, int(job_id), float(T_obs), pa, pf, pd, na, ps,
+                                     ncap, pm)
+        if rc != OK:
+            raise SubError(rc, lib().sub_server_last_error(self.s).decode())
+        self._keep[int(job_id)] = (A, f, fdot, S_gal_out, mask_out)
+
+    def poll(self, timeout_ms=0, cap=256):
+        """Finished jobs: a list of dicts (job_id, status, stats, latency_ms, queue_ms,
+        gpu_ms)."""
+        buf = (sub_job_result * cap)()
+        k = lib().sub_server_poll(self.s, buf, cap, int(timeout_ms))
+        out = []
+        for i in range(k):
+            r = buf[i]
+            self._keep.pop(int(r.job_id), None)
+            out.append({"job_id": int(r.job_id), "status": int(r.status),
+                        "stats": r.stats.as_dict(), "latency_ms": r.latency_ms,
+                        "queue_ms": r.queue_ms, "gpu_ms": r.gpu_ms})
+        return out
+
+    def info(self):
+        st = sub_server_stats()
+        lib().sub_server_info(self.s, ctypes.byref(st))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if self.s:
+            lib().sub_server_destroy(self.s)
+            self.s = None
+            self._keep.clear()
 
     def __enter__(self):
         return self

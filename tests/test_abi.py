@@ -50,3 +50,37 @@ def test_invalid_parameters_rejected_before_any_device_call():
         with pytest.raises(gbsub.SubError) as ei:
             gbsub.sub_create(gbsub.sub_params_default(**bad))
         assert ei.value.code == gbsub.EINVAL
+
+
+def test_struct_layouts_match_the_c_header(tmp_path):
+    # sizes and field offsets of every public struct as the C compiler lays them out
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stddef.h>
+#include <stdio.h>
+#include "gbsub.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(sub_params), sizeof(sub_stats),
+         sizeof(sub_server_params), sizeof(sub_job_result), sizeof(sub_server_stats));
+  printf("%zu %zu %zu %zu\n", offsetof(sub_server_params, f_min),
+         offsetof(sub_job_result, stats), offsetof(sub_job_result, latency_ms),
+         offsetof(sub_server_stats, inflight));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split()
+    sizes = [int(x) for x in out[:5]]
+    offs = [int(x) for x in out[5:]]
+    assert sizes == [ctypes.sizeof(t) for t in (gbsub.sub_params, gbsub.sub_stats,
+                                                gbsub.sub_server_params, gbsub.sub_job_result,
+                                                gbsub.sub_server_stats)]
+    assert offs == [gbsub.sub_server_params.f_min.offset, gbsub.sub_job_result.stats.offset,
+                    gbsub.sub_job_result.latency_ms.offset,
+                    gbsub.sub_server_stats.inflight.offset]

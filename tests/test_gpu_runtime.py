@@ -1,0 +1,147 @@
+"""Batches and the serving loop (through the C ABI): every catalog's result is the same,
+bit for bit, as the same catalog run alone on a plain context (whose parity with the
+oracle the other GPU tests establish), whatever else shares the GPU with it; the server
+keeps to its memory budget."""
+import numpy as np
+import pytest
+
+from paper_2602_18560_gb300 import gbsub, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    gbsub.lib()
+
+
+def jobs(count, seed=11, n_lo=2e4, n_hi=4e5):
+    """Catalogs of uneven sizes, populations and observation times."""
+    out = []
+    for i in range(count):
+        n, T, _ = synth.job_draw(seed, i)
+        pop = synth.population_draw(seed, i)
+        n = int(np.exp(np.log(n_lo) + (np.log(n_hi) - np.log(n_lo)) * ((n % 997) / 996.0)))
+        A, f, fdot = synth.catalog(n, seed * 1000 + i, pop)
+        out.append((T, A * 3.0, f, fdot))  # brighter: several iterations each
+    return out
+
+
+def solo(T, A, f, fdot, **kw):
+    with gbsub.Subtraction(T_obs=T, **kw) as s:
+        s.load(A, f, fdot)
+        st = s.run()
+        return st, s.spectrum(), s.resolved()
+
+
+def same(a, b):
+    st_a, sg_a, m_a = a
+    st_b, sg_b, m_b = b
+    assert np.array_equal(sg_a.view(np.uint64), sg_b.view(np.uint64))
+    assert np.array_equal(m_a, m_b)
+    assert st_a.iterations == st_b.iterations and st_a.n_resolved == st_b.n_resolved
+
+
+def test_batch_equals_each_catalog_alone():
+    js = jobs(6)
+    kws = [dict(window=1000, estimator=gbsub.MEDIAN_MEAN),
+           dict(window=500, estimator=gbsub.MEAN),
+           dict(window=1000, estimator=gbsub.MEDIAN_MEAN, precision=gbsub.MIXED),
+           dict(window=257, estimator=gbsub.MEDIAN),
+           dict(window=1000, estimator=gbsub.MEDIAN_MEAN),
+           dict(window=2000, estimator=gbsub.MEAN, precision=gbsub.MIXED)]
+    subs = []
+    for (T, A, f, fdot), kw in zip(js, kws):
+        s = gbsub.Subtraction(T_obs=T, **kw)
+        s.load(A, f, fdot)
+        subs.append(s)
+    try:
+        with gbsub.Batch(subs) as b:
+            for rep in range(2):   # the second run reuses the graph
+                sts = b.run()
+                assert b.last_ms > 0
+                for (T, A, f, fdot), kw, s, st in zip(js, kws, subs, sts):
+                    same((st, s.spectrum(), s.resolved()), solo(T, A, f, fdot, **kw))
+            # a new catalog of another size in one context rebuilds the graph
+            T, A, f, fdot = js[0]
+            subs[1].load(A[:5000], f[:5000], fdot[:5000])
+            sts = b.run()
+            same((sts[1], subs[1].spectrum(), subs[1].resolved()),
+                 solo(js[1][0], A[:5000], f[:5000], fdot[:5000], **kws[1]))
+    finally:
+        for s in subs:
+            s.close()
+
+
+def test_grid_divisor_does_not_change_results():
+    T, A, f, fdot = jobs(1, seed=5, n_lo=3e5, n_hi=3e5)[0]
+    ref = solo(T, A, f, fdot, window=1000, estimator=gbsub.MEDIAN_MEAN)
+    for div in (2, 7, 64):
+        with gbsub.Subtraction(T_obs=T, window=1000, estimator=gbsub.MEDIAN_MEAN) as s:
+            gbsub.sub_set_grid_div(s.ctx, div)
+            s.load(A, f, fdot)
+            st = s.run()
+            same((st, s.spectrum(), s.resolved()), ref)
+    with gbsub.Subtraction(T_obs=T) as s:
+        with pytest.raises(gbsub.SubError):
+            gbsub.sub_set_grid_div(s.ctx, 0)
+
+
+def serve(js, budget, max_inflight, precision=gbsub.FP64):
+    results = {}
+    outs = {}
+    with gbsub.Server(hbm_budget=budget, max_inflight=max_inflight, window=1000,
+                      estimator=gbsub.MEDIAN_MEAN, precision=precision) as srv:
+        for i, (T, A, f, fdot) in enumerate(js):
+            nb = int(np.floor(1e-2 * T)) - int(np.ceil(1e-4 * T)) + 1
+            sg = np.zeros(nb)
+            m = np.zeros(len(A), dtype=np.uint8)
+            outs[i] = (sg, m)
+            srv.submit(i, T, A, f, fdot, sg, m)
+        while len(results) < len(js):
+            for r in srv.poll(timeout_ms=2000):
+                results[r["job_id"]] = r
+        info = srv.info()
+    return results, outs, info
+
+
+def test_server_results_equal_each_job_alone_and_respect_the_budget():
+    js = jobs(12, seed=21)
+    budget = 900 << 20  # a few contexts at a time: jobs queue and contexts are recycled
+    results, outs, info = serve(js, budget, 4)
+    assert info["peak_device_bytes"] <= budget
+    assert info["contexts_created"] >= 2
+    for i, (T, A, f, fdot) in enumerate(js):
+        r = results[i]
+        assert r["status"] in (gbsub.OK, gbsub.ENOTCONVERGED), r
+        assert r["latency_ms"] >= r["queue_ms"] >= 0 and r["gpu_ms"] > 0
+        st_s, sg_s, m_s = solo(T, A, f, fdot, window=1000, estimator=gbsub.MEDIAN_MEAN)
+        sg, m = outs[i]
+        assert np.array_equal(sg.view(np.uint64), sg_s.view(np.uint64))
+        assert np.array_equal(m, m_s)
+        assert r["stats"]["iterations"] == st_s.iterations
+        assert r["stats"]["n_resolved"] == st_s.n_resolved
+
+
+def test_server_same_result_alone_and_in_a_mix():
+    js = jobs(8, seed=33)
+    alone = {}
+    for i, job in enumerate(js):
+        res, outs, _ = serve([job], 0, 1, precision=gbsub.MIXED)
+        alone[i] = outs[0]
+    _, mixed_outs, _ = serve(js, 0, 8, precision=gbsub.MIXED)
+    for i in range(len(js)):
+        assert np.array_equal(alone[i][0].view(np.uint64), mixed_outs[i][0].view(np.uint64))
+        assert np.array_equal(alone[i][1], mixed_outs[i][1])
+
+
+def test_server_rejects_a_job_larger_than_the_budget():
+    T, A, f, fdot = jobs(1, seed=3)[0]
+    with gbsub.Server(hbm_budget=64 << 20, max_inflight=2) as srv:
+        srv.submit(7, T, A, f, fdot)
+        got = srv.poll(timeout_ms=5000)
+        assert len(got) == 1 and got[0]["status"] == gbsub.EBUDGET
+        with pytest.raises(gbsub.SubError):
+            srv.submit(8, -1.0, A, f, fdot)
