@@ -263,6 +263,14 @@ void sub_batch_destroy(sub_batch* b);
  * Errors: SUB_EINVAL. */
 int sub_set_grid_div(sub_ctx* ctx, int32_t div);
 
+/* Test hooks: failures made on purpose, for tests of the error paths.  The catalog pass
+ * waits on its staged copies with a bound of about a second; with
+ * SUB_TEST_SKIP_CATALOG_COPIES it starts none, every wait runs out, the loop stops and
+ * sub_run returns SUB_ETIMEOUT.  The context stays usable: clear the flag (0) and run
+ * again.  Errors: SUB_EINVAL for unknown flags. */
+#define SUB_TEST_SKIP_CATALOG_COPIES 1
+int sub_test_hooks(sub_ctx* ctx, int32_t flags);
+
 /* ------------------------------------------------------------------ serving
  * A request loop for subtraction jobs as a sampler emits them.  Jobs are queued in
  * arrival order and admitted while fewer than max_inflight run and a device-memory budget
@@ -280,7 +288,9 @@ typedef struct {
   int32_t max_iter;
   int32_t tdi2;
   int32_t grid_div;      /* persistent-grid divisor of every context (sub_set_grid_div) */
-  int32_t reserved;
+  int32_t max_contexts;  /* pooled contexts at most (0 = as many as the budget allows); at
+                          * the limit a job waits for an idle context that fits it rather
+                          * than allocating (allocation and freeing synchronise the GPU) */
   double f_min, f_max;
   double rho_th, kappa;
 } sub_server_params;
@@ -322,6 +332,12 @@ int sub_server_submit(sub_server* s, int64_t job_id, double T_obs, const double*
 /* Move up to cap finished jobs into out, waiting up to timeout_ms for the first one
  * (0: no wait).  Returns how many were written. */
 int32_t sub_server_poll(sub_server* s, sub_job_result* out, int32_t cap, int32_t timeout_ms);
+
+/* Create `count` idle contexts for T_obs with room for catalogs of up to n_sources and their
+ * graphs built, before traffic arrives (context creation allocates device memory and
+ * builds tables and graphs: milliseconds that would otherwise land on the first jobs).
+ * Only while no job is queued or running.  Errors: SUB_EINVAL, SUB_ESTATE, SUB_EBUDGET. */
+int sub_server_prewarm(sub_server* s, double T_obs, int64_t n_sources, int32_t count);
 
 /* Queue, in-flight and memory counters. */
 int sub_server_info(sub_server* s, sub_server_stats* st);

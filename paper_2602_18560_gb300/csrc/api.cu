@@ -88,7 +88,8 @@ static void drop_graph(sub_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   c->exec = nullptr;
   c->graph = nullptr;
-  c->graph_N = -1;
+  c->graph_cap = -1;
+  c->graph_gen += 1;
 }
 
 extern "C" int sub_params_default(sub_params* p) {
@@ -216,6 +217,7 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
       {(void**)&c->pre_lo, (size_t)ncell * 8}, {(void**)&c->pre_hi, (size_t)ncell * 8},
       {(void**)&c->uflow, (size_t)pl.nch * 4},
       {(void**)&c->rs, sizeof(RunState)}, {(void**)&c->new_hist, (size_t)p->max_iter * 4},
+      {(void**)&c->dN, 8},
   };
   for (auto& w : want) {
     rc = dalloc(c, w.p, w.b);
@@ -255,14 +257,8 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   return SUB_OK;
 }
 
-extern "C" int sub_load_catalog(sub_ctx* c, const double* A, const double* f, const double* fdot,
-                                int64_t n, int where) {
-  if (!c) return SUB_EINVAL;
-  if (n < 0 || (n > 0 && (!A || !f || !fdot)) || (where != SUB_HOST && where != SUB_DEVICE)) {
-    set_err(c, "invalid catalog arguments");
-    return SUB_EINVAL;
-  }
-  if (n > ((int64_t)1 << 40)) { set_err(c, "catalog too large"); return SUB_EINVAL; }
+// Per-source buffers for catalogs of up to n sources (kept when they already fit).
+static int reserve_sources(sub_ctx* c, int64_t n) {
   if (n > c->cap_N || c->A == nullptr) {
     drop_graph(c);
     dfree(c, c->A); dfree(c, c->f); dfree(c, c->fdot); dfree(c, c->resolved);
@@ -286,13 +282,29 @@ extern "C" int sub_load_catalog(sub_ctx* c, const double* A, const double* f, co
     }
     c->cap_N = (int64_t)m;
   }
+  return SUB_OK;
+}
+
+extern "C" int sub_load_catalog(sub_ctx* c, const double* A, const double* f, const double* fdot,
+                                int64_t n, int where) {
+  if (!c) return SUB_EINVAL;
+  if (n < 0 || (n > 0 && (!A || !f || !fdot)) || (where != SUB_HOST && where != SUB_DEVICE)) {
+    set_err(c, "invalid catalog arguments");
+    return SUB_EINVAL;
+  }
+  if (n > ((int64_t)1 << 40)) { set_err(c, "catalog too large"); return SUB_EINVAL; }
+  {
+    int rc = reserve_sources(c, n);
+    if (rc) return rc;
+  }
   if (n > 0) {
     cudaMemcpyKind k = where == SUB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     CU(cudaMemcpyAsync(c->A, A, (size_t)n * 8, k, c->stream), c);
     CU(cudaMemcpyAsync(c->f, f, (size_t)n * 8, k, c->stream), c);
     CU(cudaMemcpyAsync(c->fdot, fdot, (size_t)n * 8, k, c->stream), c);
   }
-  if (c->N != n) drop_graph(c);
+  launch_set_i64(c->dN, (long long)n, c->stream);
+  CU(cudaGetLastError(), c);
   c->N = n;
   c->ran = false;
   return SUB_OK;
@@ -367,13 +379,13 @@ static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
   if ((e = cudaMemsetAsync(c->dirty + c->plan.nch, 0, (size_t)c->plan.nch, st))) return e;
   launch_build_lists(dirty_of(c, true), c->lists, c->list_counts, st);
   if ((e = cudaMemsetAsync(c->new_hist, 0, (size_t)c->p.max_iter * 4, st))) return e;
-  if (c->N > 0) {
-    if ((e = cudaMemsetAsync(c->resolved, 0, (size_t)c->N, st))) return e;
-  }
+  // sized by the capacity, not the catalog: the captured graph serves every catalog that fits
+  if ((e = cudaMemsetAsync(c->resolved, 0, (size_t)c->cap_N, st))) return e;
   {
     KTimer t(c, st, SUB_K_PREPASS);
-    launch_prepass(c->A, c->f, c->fdot, c->N, c->grid, tables_of(c), thr_kappa_of(c),
-                   thr_live_of(c), c->acc, c->rep, c->cd, c->rs, c->nsm_run, st);
+    launch_prepass(c->A, c->f, c->fdot, c->dN, c->cap_N, c->grid, tables_of(c),
+                   thr_kappa_of(c), thr_live_of(c), c->acc, c->rep, c->cd, c->rs, c->nsm_run,
+                   c->test_flags, st);
   }
   return cudaGetLastError();
 }
@@ -436,7 +448,7 @@ static cudaError_t enqueue_body(sub_ctx* c, cudaStream_t st, unsigned long long 
   double th2 = c->p.rho_th * c->p.rho_th;
   {
     KTimer t(c, st, SUB_K_SNR);
-    launch_snr_resolve(c->cd, c->N > 0 ? c->N : 1, c->grid, tables_of(c), c->Sg, c->inv_f, th2,
+    launch_snr_resolve(c->cd, c->cap_N > 0 ? c->cap_N : 1, c->grid, tables_of(c), c->Sg, c->inv_f, th2,
                        c->p.conv_rtol, snr_mode(c), c->resolved, c->acc, rs, dirty_of(c, true),
                        c->plan.Kc, sg_radius_of(c), c->nsm_run, st);
   }
@@ -499,7 +511,7 @@ static int build_graph(sub_ctx* c) {
     return SUB_ECUDA;
   }
   c->graph = g;
-  c->graph_N = c->N;
+  c->graph_cap = c->cap_N;
   return SUB_OK;
 }
 
@@ -560,6 +572,21 @@ void gbsub::ctx_set_err(sub_ctx* c, const char* fmt, ...) {
 
 int gbsub::ctx_fill_stats(sub_ctx* c, sub_stats* st) { return fill_stats(c, st); }
 
+int gbsub::ctx_prepare(sub_ctx* c, int64_t cap) {
+  int rc = reserve_sources(c, cap);
+  if (rc) return rc;
+  if (c->use_graph && c->graph_cap != c->cap_N) {
+    if (build_graph(c) != SUB_OK) c->use_graph = false;
+  }
+  return SUB_OK;
+}
+
+void gbsub::ctx_set_test_flags(sub_ctx* c, int flags) {
+  if (flags == c->test_flags) return;
+  drop_graph(c);
+  c->test_flags = flags;
+}
+
 void gbsub::ctx_set_grid_div(sub_ctx* c, int div) {
   if (div < 1) div = 1;
   if (div == c->grid_div) return;
@@ -574,7 +601,7 @@ void gbsub::ctx_set_grid_div(sub_ctx* c, int div) {
 extern "C" int sub_run(sub_ctx* c, sub_stats* st) {
   if (!c) return SUB_EINVAL;
   if (c->N < 0) { set_err(c, "no catalog loaded"); return SUB_ESTATE; }
-  if (c->use_graph && c->graph_N != c->N) {
+  if (c->use_graph && c->graph_cap != c->cap_N) {
     if (build_graph(c) != SUB_OK) c->use_graph = false;  // conditional nodes unavailable
   }
   if (c->use_graph) {

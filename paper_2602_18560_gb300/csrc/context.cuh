@@ -54,6 +54,8 @@ struct sub_ctx {
   int64_t N = -1;        // sources loaded (-1: none)
   int64_t cap_N = 0;     // capacity of the per-source buffers
   double *A = nullptr, *f = nullptr, *fdot = nullptr;
+  long long* dN = nullptr;  // the catalog size on the device (read by the catalog pass)
+  int test_flags = 0;       // sub_test_hooks
   Cands cd = {};
   unsigned char* resolved = nullptr;
   // run state
@@ -64,7 +66,8 @@ struct sub_ctx {
   // graph
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
-  int64_t graph_N = -1;
+  int64_t graph_cap = -1;  // catalog capacity the graph was built for
+  int64_t graph_gen = 0;   // bumped whenever launch settings change (batches rebuild)
   bool use_graph = true;
   // timing
   cudaEvent_t ev_start = nullptr, ev_pre = nullptr, ev_end = nullptr;
@@ -88,4 +91,8 @@ int ctx_fill_stats(sub_ctx* c, sub_stats* st);
 cudaError_t ctx_add_run_nodes(sub_ctx* c, cudaGraph_t g, cudaGraphNode_t* last);
 // Grid divisor of the persistent kernels (1 = the whole GPU).
 void ctx_set_grid_div(sub_ctx* c, int div);
+// Buffers for catalogs of up to cap sources and the run's graph, ahead of the first catalog.
+int ctx_prepare(sub_ctx* c, int64_t cap);
+// Test hooks (SUB_TEST_*) baked into the next graph.
+void ctx_set_test_flags(sub_ctx* c, int flags);
 }  // namespace gbsub

@@ -319,11 +319,14 @@ __device__ __forceinline__ void prepass_drain(const double* __restrict__ A,
 
 __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
     const double* __restrict__ A, const double* __restrict__ f, const double* __restrict__ fdot,
-    long long N, Grid g, Tables tb, double thr_kappa, double thr_live,
-    unsigned long long* __restrict__ acc, AccReplicas rep, Cands cd, RunState* rs) {
+    const long long* __restrict__ pN, Grid g, Tables tb, double thr_kappa, double thr_live,
+    unsigned long long* __restrict__ acc, AccReplicas rep, Cands cd, RunState* rs,
+    int test_flags) {
   extern __shared__ __align__(128) double pre_tiles[];  // [stage][A | f | fdot][kPreTile]
   __shared__ __align__(8) uint64_t bar[kPreStages];
   __shared__ long long stage_tile[kPreStages];  // tile held by each stage
+  __shared__ int stage_copying[kPreStages];     // its copies were started
+  const long long N = *pN;
   __shared__ long long slow_q[kSlowCap];
   __shared__ int slow_n;
   const int tid = threadIdx.x;
@@ -339,7 +342,9 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
   auto fetch = [&](int stage) {
     const long long t = (long long)atomicAdd(&rs->next_tile, 1ull);
     stage_tile[stage] = t;
-    if (t < nfull) {
+    stage_copying[stage] = 0;
+    if (t < nfull && !(test_flags & 1)) {
+      stage_copying[stage] = 1;
       double* d = pre_tiles + (size_t)stage * 3 * kPreTile;
       const size_t off = (size_t)t * kPreTile;
       mbar_expect_tx(&bar[stage], 3u * kPreTile * (unsigned)sizeof(double));
@@ -434,10 +439,9 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
     // before its shared memory goes away
     if (tid == 0) {
       atomicOr(&rs->err, ERR_TIMEOUT);
-      for (long long k = i; k < i + kPreStages; ++k) {
-        const long long tk = stage_tile[k % kPreStages];
-        if (tk < nfull) mbar_wait(&bar[k % kPreStages], (unsigned)((k / kPreStages) & 1));
-      }
+      for (long long k = i; k < i + kPreStages; ++k)
+        if (stage_copying[k % kPreStages])
+          mbar_wait(&bar[k % kPreStages], (unsigned)((k / kPreStages) & 1));
     }
     __syncthreads();
     return;
@@ -447,18 +451,23 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
   if (lane == 0 && nkappa) atomicAdd(&rs->ncand, nkappa);
 }
 
-void launch_prepass(const double* A, const double* f, const double* fdot, long long N,
-                    const Grid& g, const Tables& tb, double thr_kappa, double thr_live,
-                    unsigned long long* acc, AccReplicas rep, Cands cd, RunState* rs, int nsm,
-                    cudaStream_t st) {
-  if (N <= 0) return;
-  long long tiles = (N + kPreTile - 1) / kPreTile;
-  long long cap = (long long)nsm * 4;  // resident CTAs (launch bounds, shared memory)
-  int bl = (int)(tiles < cap ? tiles : cap);
-  k_prepass<<<bl, kPrepassThreads, kPrepassSmem, st>>>(A, f, fdot, N, g, tb, thr_kappa, thr_live,
-                                                       acc, rep, cd, rs);
+void launch_prepass(const double* A, const double* f, const double* fdot, const long long* pN,
+                    long long cap, const Grid& g, const Tables& tb, double thr_kappa,
+                    double thr_live, unsigned long long* acc, AccReplicas rep, Cands cd,
+                    RunState* rs, int nsm, int test_flags, cudaStream_t st) {
+  long long tiles = (cap + kPreTile - 1) / kPreTile;
+  long long lim = (long long)nsm * 4;  // resident CTAs (launch bounds, shared memory)
+  int bl = (int)(tiles < lim ? (tiles < 1 ? 1 : tiles) : lim);
+  k_prepass<<<bl, kPrepassThreads, kPrepassSmem, st>>>(A, f, fdot, pN, g, tb, thr_kappa,
+                                                       thr_live, acc, rep, cd, rs, test_flags);
   if (rep.nbins > 0)
     k_fold_replicas<<<(unsigned)((rep.nbins + 255) / 256), 256, 0, st>>>(acc, rep);
+}
+
+__global__ void k_set_i64(long long* p, long long v) { *p = v; }
+
+void launch_set_i64(long long* p, long long v, cudaStream_t st) {
+  k_set_i64<<<1, 1, 0, st>>>(p, v);
 }
 
 // ============================================================================ reductions
@@ -1411,8 +1420,8 @@ __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist
   __syncthreads();
   if (threadIdx.x != 0) return;
   unsigned go = 1u;
-  if (rs->final_pass) {
-    go = 0u;
+  if (rs->final_pass || (rs->err & ERR_TIMEOUT)) {
+    go = 0u;  // the last pass is done, or the catalog pass gave up
   } else {
     bool rstop = rtol_stop(rs, rtol);
     int it = it0 + 1;

@@ -36,7 +36,8 @@ using Clock = std::chrono::steady_clock;
 
 struct sub_batch {
   std::vector<sub_ctx*> ctxs;
-  std::vector<int64_t> sizes;  // catalog sizes the graph was built for
+  std::vector<int64_t> sizes;  // catalog capacities the graph was built for
+  std::vector<int64_t> gens;   // and the contexts' launch-setting generations
   cudaStream_t stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -60,6 +61,7 @@ static void batch_drop_graph(sub_batch* b) {
   b->exec = nullptr;
   b->graph = nullptr;
   b->sizes.clear();
+  b->gens.clear();
 }
 
 static int batch_build(sub_batch* b) {
@@ -79,7 +81,10 @@ static int batch_build(sub_batch* b) {
     return SUB_ECUDA;
   }
   b->graph = g;
-  for (sub_ctx* c : b->ctxs) b->sizes.push_back(c->N);
+  for (sub_ctx* c : b->ctxs) {
+    b->sizes.push_back(c->cap_N);
+    b->gens.push_back(c->graph_gen);
+  }
   return SUB_OK;
 }
 
@@ -128,7 +133,8 @@ extern "C" int sub_batch_run(sub_batch* b, sub_stats* stats) {
       return SUB_ESTATE;
     }
   bool stale = b->exec == nullptr || b->sizes.size() != b->ctxs.size();
-  for (size_t i = 0; !stale && i < b->ctxs.size(); ++i) stale = b->sizes[i] != b->ctxs[i]->N;
+  for (size_t i = 0; !stale && i < b->ctxs.size(); ++i)
+    stale = b->sizes[i] != b->ctxs[i]->cap_N || b->gens[i] != b->ctxs[i]->graph_gen;
   if (stale) {
     int rc = batch_build(b);
     if (rc) return rc;
@@ -173,6 +179,16 @@ extern "C" void sub_batch_destroy(sub_batch* b) {
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
+}
+
+extern "C" int sub_test_hooks(sub_ctx* c, int32_t flags) {
+  if (!c) return SUB_EINVAL;
+  if (flags & ~SUB_TEST_SKIP_CATALOG_COPIES) {
+    ctx_set_err(c, "unknown test hook flags 0x%x", (unsigned)flags);
+    return SUB_EINVAL;
+  }
+  ctx_set_test_flags(c, flags);
+  return SUB_OK;
 }
 
 extern "C" int sub_set_grid_div(sub_ctx* c, int32_t div) {
@@ -270,6 +286,8 @@ static void push_result(sub_server* s, const Job& j, int status, const sub_stats
   s->cv_done.notify_all();
 }
 
+static Slot* make_slot(sub_server* s, double T_obs, int64_t cap, int* status);
+
 // A context for job j: an idle one with the same T_obs and room for the catalog, else a new
 // one if the budget allows (idle contexts are destroyed, least recently used first, to make
 // room).  Returns null when the job must wait for running jobs to finish.
@@ -281,6 +299,18 @@ static Slot* acquire_slot(sub_server* s, const Job& j, int* fail_status) {
     if (!best || sl->ctx->cap_N < best->ctx->cap_N) best = sl;
   }
   if (best) return best;
+  if (s->p.max_contexts > 0 && (int)s->slots.size() >= s->p.max_contexts) {
+    // at the pool limit: an idle context that cannot take this job is replaced; with none
+    // idle the job waits
+    Slot* victim = nullptr;
+    for (Slot* sl : s->slots)
+      if (!sl->busy && (!victim || sl->last_use < victim->last_use)) victim = sl;
+    if (!victim) return nullptr;
+    s->pool_bytes -= sub_device_bytes(victim->ctx);
+    sub_destroy(victim->ctx);
+    s->slots.erase(std::find(s->slots.begin(), s->slots.end(), victim));
+    delete victim;
+  }
   const int64_t need = predicted_bytes(s, j.T_obs, j.n);
   const uint64_t budget = s->p.hbm_budget;
   if (budget && (uint64_t)need > budget) {
@@ -297,31 +327,9 @@ static Slot* acquire_slot(sub_server* s, const Job& j, int* fail_status) {
     s->slots.erase(std::find(s->slots.begin(), s->slots.end(), victim));
     delete victim;
   }
-  sub_params prm;
-  sub_params_default(&prm);
-  prm.T_obs = j.T_obs;
-  prm.f_min = s->p.f_min;
-  prm.f_max = s->p.f_max;
-  prm.window = s->p.window;
-  prm.estimator = s->p.estimator;
-  prm.rho_th = s->p.rho_th;
-  prm.kappa = s->p.kappa;
-  prm.max_iter = s->p.max_iter;
-  prm.tdi2 = s->p.tdi2;
-  prm.precision = s->p.precision;
-  sub_ctx* c = nullptr;
-  int rc = sub_create(&prm, nullptr, &c);
-  if (rc) {
-    *fail_status = rc;
-    return nullptr;
-  }
-  if (s->p.grid_div > 1) sub_set_grid_div(c, s->p.grid_div);
-  Slot* sl = new Slot;
-  sl->srv = s;
-  sl->ctx = c;
-  s->slots.push_back(sl);
-  s->pool_bytes += sub_device_bytes(c);
-  s->contexts_created += 1;
+  int st = SUB_OK;
+  Slot* sl = make_slot(s, j.T_obs, j.n, &st);
+  if (!sl) *fail_status = st;
   return sl;
 }
 
@@ -440,8 +448,10 @@ extern "C" int sub_server_params_default(sub_server_params* p) {
 extern "C" int sub_server_create(const sub_server_params* p, sub_server** out) {
   if (!out || !p) return SUB_EINVAL;
   *out = nullptr;
-  if (p->max_inflight < 1 || p->max_inflight > 256 || p->grid_div < 1 || p->grid_div > 64) {
-    set_global_error("sub_server_create: max_inflight must be 1 .. 256, grid_div 1 .. 64");
+  if (p->max_inflight < 1 || p->max_inflight > 256 || p->grid_div < 1 || p->grid_div > 64 ||
+      p->max_contexts < 0) {
+    set_global_error("sub_server_create: max_inflight must be 1 .. 256, grid_div 1 .. 64, "
+                     "max_contexts >= 0");
     return SUB_EINVAL;
   }
   sub_server* s = new (std::nothrow) sub_server;
@@ -515,6 +525,62 @@ extern "C" int sub_server_info(sub_server* s, sub_server_stats* st) {
   st->device_bytes = s->pool_bytes;
   st->peak_device_bytes = s->peak_bytes;
   st->contexts_created = s->contexts_created;
+  return SUB_OK;
+}
+
+// A context for T_obs with room for `cap` sources and its graph built, ready for jobs.
+static Slot* make_slot(sub_server* s, double T_obs, int64_t cap, int* status) {
+  sub_params prm;
+  sub_params_default(&prm);
+  prm.T_obs = T_obs;
+  prm.f_min = s->p.f_min;
+  prm.f_max = s->p.f_max;
+  prm.window = s->p.window;
+  prm.estimator = s->p.estimator;
+  prm.rho_th = s->p.rho_th;
+  prm.kappa = s->p.kappa;
+  prm.max_iter = s->p.max_iter;
+  prm.tdi2 = s->p.tdi2;
+  prm.precision = s->p.precision;
+  sub_ctx* c = nullptr;
+  *status = sub_create(&prm, nullptr, &c);
+  if (*status) return nullptr;
+  if (s->p.grid_div > 1) sub_set_grid_div(c, s->p.grid_div);
+  if (cap > 0) *status = ctx_prepare(c, cap);
+  if (*status) {
+    sub_destroy(c);
+    return nullptr;
+  }
+  Slot* sl = new Slot;
+  sl->srv = s;
+  sl->ctx = c;
+  s->slots.push_back(sl);
+  s->pool_bytes += sub_device_bytes(c);
+  if (s->pool_bytes > s->peak_bytes) s->peak_bytes = s->pool_bytes;
+  s->contexts_created += 1;
+  return sl;
+}
+
+extern "C" int sub_server_prewarm(sub_server* s, double T_obs, int64_t n_sources,
+                                  int32_t count) {
+  if (!s || !(T_obs > 0.0) || n_sources < 0 || count < 0) return SUB_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);  // the worker touches the pool only for jobs
+  if (!s->queue.empty() || s->inflight > 0) {
+    s->err = "sub_server_prewarm: jobs are queued or running";
+    return SUB_ESTATE;
+  }
+  for (int32_t i = 0; i < count; ++i) {
+    const int64_t need = predicted_bytes(s, T_obs, n_sources);
+    if (s->p.hbm_budget && (uint64_t)(s->pool_bytes + need) > s->p.hbm_budget) {
+      s->err = "sub_server_prewarm: the budget is full";
+      return SUB_EBUDGET;
+    }
+    int st = SUB_OK;
+    if (!make_slot(s, T_obs, n_sources, &st)) {
+      s->err = "sub_server_prewarm: context creation failed";
+      return st;
+    }
+  }
   return SUB_OK;
 }
 

@@ -64,7 +64,7 @@ class sub_server_params(ctypes.Structure):
         ("hbm_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
         ("window", ctypes.c_int32), ("estimator", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tdi2", ctypes.c_int32),
-        ("grid_div", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("grid_div", ctypes.c_int32), ("max_contexts", ctypes.c_int32),
         ("f_min", ctypes.c_double), ("f_max", ctypes.c_double),
         ("rho_th", ctypes.c_double), ("kappa", ctypes.c_double),
     ]
@@ -93,8 +93,9 @@ EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_run", "s
            "sub_get_tables", "sub_get_timing", "sub_profile", "sub_device_bytes", "sub_destroy",
            "sub_last_error", "sub_running_mean_noalloc", "sub_get_power", "sub_batch_create",
            "sub_batch_run", "sub_batch_last_ms", "sub_batch_last_error", "sub_batch_destroy",
-           "sub_set_grid_div", "sub_server_params_default", "sub_server_create",
+           "sub_set_grid_div", "sub_test_hooks", "sub_server_params_default", "sub_server_create",
            "sub_server_submit", "sub_server_poll", "sub_server_info", "sub_server_last_error",
+           "sub_server_prewarm",
            "sub_server_destroy")
 KERNELS = ("prepass", "sort", "median", "prefix", "mean", "snr", "control")
 
@@ -140,11 +141,13 @@ def lib(build_if_missing: bool = True):
             "sub_batch_last_error": (ctypes.c_char_p, [P]),
             "sub_batch_destroy": (None, [P]),
             "sub_set_grid_div": (i32, [P, i32]),
+            "sub_test_hooks": (i32, [P, i32]),
             "sub_server_params_default": (i32, [ctypes.POINTER(sub_server_params)]),
             "sub_server_create": (i32, [ctypes.POINTER(sub_server_params), ctypes.POINTER(P)]),
             "sub_server_submit": (i32, [P, i64, ctypes.c_double, P, P, P, i64, P, i64, P]),
             "sub_server_poll": (i32, [P, ctypes.POINTER(sub_job_result), i32, i32]),
             "sub_server_info": (i32, [P, ctypes.POINTER(sub_server_stats)]),
+            "sub_server_prewarm": (i32, [P, ctypes.c_double, i64, i32]),
             "sub_server_last_error": (ctypes.c_char_p, [P]),
             "sub_server_destroy": (None, [P]),
         }
@@ -382,6 +385,13 @@ def sub_set_grid_div(ctx, div: int):
     return _check(ctx, lib().sub_set_grid_div(ctx, int(div)))
 
 
+TEST_SKIP_CATALOG_COPIES = 1
+
+
+def sub_test_hooks(ctx, flags: int):
+    return _check(ctx, lib().sub_test_hooks(ctx, int(flags)))
+
+
 class Batch:
     """Several ``Subtraction`` contexts run together in one graph launch
     (``sub_batch_*``).  The contexts must outlive the batch."""
@@ -483,6 +493,12 @@ class Server:
                         "stats": r.stats.as_dict(), "latency_ms": r.latency_ms,
                         "queue_ms": r.queue_ms, "gpu_ms": r.gpu_ms})
         return out
+
+    def prewarm(self, T_obs, n_sources, count):
+        """Idle contexts for T_obs with room for n_sources, created before traffic arrives."""
+        rc = lib().sub_server_prewarm(self.s, float(T_obs), int(n_sources), int(count))
+        if rc != OK:
+            raise SubError(rc, lib().sub_server_last_error(self.s).decode())
 
     def info(self):
         st = sub_server_stats()

@@ -224,3 +224,35 @@ def workload(name: str) -> Workload:
     if name == "nb3e7_4yr":
         return Workload(name, 30_000_000, 4 * YEAR, 2, population_draw(2, 0))
     raise KeyError(name)
+
+
+def _catalog_task(args):
+    n, seed, pop, start = args
+    return catalog(n, seed, pop, start=start)
+
+
+def catalogs_parallel(specs, procs=None, slice_size=1 << 21):
+    """catalog(n, seed, pop) for every (n, seed, pop) of specs, computed by spawned worker
+    processes over slices of each index range.  Every source is a pure function of its
+    seed and index, so the result is identical to calling catalog() in this process."""
+    import multiprocessing as mp
+    import os
+    procs = procs or min(16, os.cpu_count() or 1)
+    tasks, owners = [], []
+    for i, (n, seed, pop) in enumerate(specs):
+        for s in range(0, n, slice_size):
+            tasks.append((min(slice_size, n - s), seed, pop, s))
+            owners.append(i)
+    if procs <= 1 or len(tasks) <= 1:
+        parts = [_catalog_task(t) for t in tasks]
+    else:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            parts = pool.map(_catalog_task, tasks, chunksize=1)
+    out = []
+    for i, (n, _, _) in enumerate(specs):
+        mine = [p for p, o in zip(parts, owners) if o == i]
+        if not mine:
+            out.append((np.empty(0), np.empty(0), np.empty(0)))
+        else:
+            out.append(tuple(np.concatenate([p[k] for p in mine]) for k in range(3)))
+    return out

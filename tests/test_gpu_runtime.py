@@ -145,3 +145,80 @@ def test_server_rejects_a_job_larger_than_the_budget():
         assert len(got) == 1 and got[0]["status"] == gbsub.EBUDGET
         with pytest.raises(gbsub.SubError):
             srv.submit(8, -1.0, A, f, fdot)
+
+
+def test_timeout_path_reports_and_leaves_the_context_usable():
+    # the catalog pass starts no copies on purpose: its bounded waits (about a second) run
+    # out, the loop stops, the run reports SUB_ETIMEOUT; the next run without the hook is
+    # normal and equals a fresh context's
+    T, A, f, fdot = jobs(1, seed=9, n_lo=5e4, n_hi=5e4)[0]
+    ref = solo(T, A, f, fdot, window=1000, estimator=gbsub.MEDIAN_MEAN)
+    with gbsub.Subtraction(T_obs=T, window=1000, estimator=gbsub.MEDIAN_MEAN) as s:
+        s.load(A, f, fdot)
+        gbsub.sub_test_hooks(s.ctx, gbsub.TEST_SKIP_CATALOG_COPIES)
+        with pytest.raises(gbsub.SubError) as ei:
+            s.run()
+        assert ei.value.code == gbsub.ETIMEOUT
+        gbsub.sub_test_hooks(s.ctx, 0)
+        st = s.run()
+        same((st, s.spectrum(), s.resolved()), ref)
+
+
+def test_graph_is_reused_across_catalog_sizes():
+    # one context, catalogs of different sizes within its capacity: same results as fresh
+    # contexts (the captured graph reads the catalog size on the device)
+    js = jobs(3, seed=17, n_lo=5e4, n_hi=3e5)
+    big = max(js, key=lambda j: len(j[1]))
+    with gbsub.Subtraction(T_obs=big[0], window=1000, estimator=gbsub.MEDIAN_MEAN) as s:
+        s.load(*big[1:])
+        s.run()
+        for T, A, f, fdot in js:
+            if T != big[0]:
+                continue
+            for n in (len(A), len(A) // 3, 1, 0):
+                s.load(A[:n], f[:n], fdot[:n])
+                st = s.run()
+                same((st, s.spectrum(), s.resolved()),
+                     solo(T, A[:n], f[:n], fdot[:n], window=1000,
+                          estimator=gbsub.MEDIAN_MEAN))
+
+
+def test_server_prewarm_serves_without_creating_contexts():
+    js = [j for j in jobs(6, seed=41) if j[0] == jobs(6, seed=41)[0][0]]
+    T = js[0][0]
+    with gbsub.Server(max_inflight=4, window=1000, estimator=gbsub.MEDIAN_MEAN) as srv:
+        srv.prewarm(T, max(len(j[1]) for j in js), 2)
+        assert srv.info()["contexts_created"] == 2
+        outs = []
+        for i, (T_, A, f, fdot) in enumerate(js):
+            nb = int(np.floor(1e-2 * T_)) - int(np.ceil(1e-4 * T_)) + 1
+            outs.append((np.zeros(nb), np.zeros(len(A), dtype=np.uint8)))
+            srv.submit(i, T_, A, f, fdot, *outs[-1])
+        got = []
+        while len(got) < len(js):
+            got += srv.poll(timeout_ms=2000)
+        assert srv.info()["contexts_created"] == 2
+    for (T_, A, f, fdot), (sg, m) in zip(js, outs):
+        st, sg_s, m_s = solo(T_, A, f, fdot, window=1000, estimator=gbsub.MEDIAN_MEAN)
+        assert np.array_equal(sg.view(np.uint64), sg_s.view(np.uint64))
+        assert np.array_equal(m, m_s)
+
+
+def test_server_pool_stays_within_max_contexts():
+    js = jobs(8, seed=51)
+    outs = []
+    with gbsub.Server(max_inflight=3, max_contexts=2, window=1000,
+                      estimator=gbsub.MEDIAN_MEAN) as srv:
+        for i, (T, A, f, fdot) in enumerate(js):
+            nb = int(np.floor(1e-2 * T)) - int(np.ceil(1e-4 * T)) + 1
+            outs.append((np.zeros(nb), np.zeros(len(A), dtype=np.uint8)))
+            srv.submit(i, T, A, f, fdot, *outs[-1])
+        got = []
+        while len(got) < len(js):
+            got += srv.poll(timeout_ms=2000)
+            assert srv.info()["contexts"] <= 2
+    assert all(r["status"] in (gbsub.OK, gbsub.ENOTCONVERGED) for r in got)
+    for (T, A, f, fdot), (sg, m) in zip(js, outs):
+        st, sg_s, m_s = solo(T, A, f, fdot, window=1000, estimator=gbsub.MEDIAN_MEAN)
+        assert np.array_equal(sg.view(np.uint64), sg_s.view(np.uint64))
+        assert np.array_equal(m, m_s)

@@ -71,3 +71,13 @@ def test_portable_elementary_functions():
     z = rng.uniform(1e-5, 10, 20000)
     for p in (5 / 3, 11 / 3, 2 / 3, -0.4367):
         assert np.max(np.abs(synth.ppow(z, p) - z**p) / z**p) < 1e-14
+
+
+def test_parallel_generation_is_identical():
+    pop = synth.Population(3.5, 2.5)
+    specs = [(5000, 3, pop), (0, 4, pop), (1234, 9, synth.Population(3.1, 1.7))]
+    got = synth.catalogs_parallel(specs, procs=2, slice_size=1000)
+    for (n, seed, p), g in zip(specs, got):
+        ref = synth.catalog(n, seed, p)
+        for a, b in zip(g, ref):
+            np.testing.assert_array_equal(a, b)
