@@ -58,6 +58,31 @@ def parse():
     return ap.parse_args()
 
 
+
+# ---------------------------------------------------------------- multi-process helpers
+# One process per GPU, each on its own replica catalog (the catalogs are independent: no
+# data-path collective); the timed region's length is the slowest rank's, and the value is
+# the units every rank processed over that time.
+
+def replica_seed(seed, rank):
+    """Catalog seed of a rank's replica (rank 0 runs the workload's own catalog)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x, pg, device):
+    """The largest x over all ranks (x itself without a process group)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, units_per_rank, seconds):
+    """Units per second of the whole job: every rank's units over the slowest rank's time."""
+    return ws * units_per_rank / seconds
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rk = int(os.environ.get("RANK", "0"))
@@ -233,7 +258,7 @@ def main():
     from paper_2602_18560_gb300 import gbsub
 
     w = synth.workload(args.workload)
-    seed = w.seed + 1000 * rank
+    seed = replica_seed(w.seed, rank)
     A, f, fdot = synth.catalog(w.n_sources, seed, w.pop)
     N = w.n_sources
     est = EST[args.estimator]
@@ -264,13 +289,8 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     st = gbsub.sub_get_stats(sub.ctx)
     pre_ms, loop_ms, tot_ms = sub.timing()
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_max = float(t.item())
-    else:
-        ms_max = ms
-    value = ws * N / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, pg, "cuda")
+    value = whole_job_rate(ws, N, ms_max * 1e-3)
 
     # ---------------------------------------------------------------- parity vs stored oracle values
     parity = None
@@ -365,11 +385,8 @@ def main():
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
         te = sum(times[1:]) / reps
-        if pg:
-            t = torch.tensor([te], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": ws * N / te, "unit": "sources/s", "h2d_bytes_per_step": 24 * N,
+        te = max_over_ranks(te, pg, "cuda")
+        e2e = {"value": whole_job_rate(ws, N, te), "unit": "sources/s", "h2d_bytes_per_step": 24 * N,
                "d2h_bytes_per_step": 8 * nb + N, "ms_per_step": te * 1e3,
                "api": "sub_load_catalog(SUB_HOST pinned) + sub_run + sub_get_spectrum + "
                       "sub_get_resolved_mask"}
@@ -483,11 +500,8 @@ def run_batch(args, ws, rank, local_rank):
             sts = batch.run()
             times.append(batch.last_ms)
     ms = sum(times) / len(times)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * 64 / (ms * 1e-3)
+    ms = max_over_ranks(ms, pg, "cuda")
+    value = whole_job_rate(ws, 64, ms * 1e-3)
 
     # accuracy of the batch against the sequential FP64 runs (whose oracle parity the
     # tests establish)
