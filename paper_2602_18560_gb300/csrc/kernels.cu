@@ -172,31 +172,74 @@ __global__ void k_fold_replicas(unsigned long long* __restrict__ acc, AccReplica
 // FP64 path of the catalog pass: the sweep of one source, its pieces deposited; returns
 // the sum of its contributions.  Kept out of line so that none of it is speculated into
 // the common path.
+// Bins of a source's sweep that the FP64 path walks: [k0, k1] (absolute bin numbers),
+// empty when the sweep leaves the band.
+__device__ __forceinline__ void sweep_bins(const Sweep& sw, const Grid& g, long long* k0,
+                                           long long* k1) {
+  *k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
+  *k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
+}
+
+// Deposit bins k0 + off, k0 + off + step, ... <= k1 of a multi-bin sweep; returns the sum
+// of their contributions in that order.
+__device__ __forceinline__ double sweep_deposit(const Sweep& sw, const Grid& g, const Tables& tb,
+                                                double a2, long long k0, long long k1, int off,
+                                                int step, unsigned long long* acc,
+                                                unsigned* err) {
+  double r = 0.0;
+  for (long long k = k0 + off; k <= k1; k += step) {
+    double w = sweep_weight(sw, k);
+    if (w > 0.0) {
+      long long j = k - g.k_lo;
+      double q = __dmul_rn(__dmul_rn(a2, w), tb.gq[j]);
+      deposit_q(acc, j, q, err);
+      r = __dadd_rn(r, q);
+    }
+  }
+  return r;
+}
+
+// FP64 path of the catalog pass for one source: the sweep, its pieces deposited; returns
+// the sum of its contributions.  Kept out of line so that none of it is speculated into the
+// common path.
 __device__ __noinline__ double prepass_slow(double a2, double fs, double fds, const Grid g,
                                             const Tables tb, unsigned long long* acc,
                                             unsigned* err) {
   Sweep sw = make_sweep(fs, fds, g.T, g.T2);
-  double r = 0.0;
   if (sw.ka == sw.kb) {
     long long j = sw.ka - g.k_lo;
     if (j >= 0 && j < g.nb) {
       double q = __dmul_rn(a2, tb.gq[j]);
       deposit_q(acc, j, q, err);
-      r = q;
+      return q;
     }
-  } else {
-    long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
-    long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
-    for (long long k = k0; k <= k1; ++k) {
-      double w = sweep_weight(sw, k);
-      if (w > 0.0) {
-        long long j = k - g.k_lo;
-        double q = __dmul_rn(__dmul_rn(a2, w), tb.gq[j]);
-        deposit_q(acc, j, q, err);
-        r = __dadd_rn(r, q);
-      }
-    }
+    return 0.0;
   }
+  long long k0, k1;
+  sweep_bins(sw, g, &k0, &k1);
+  return sweep_deposit(sw, g, tb, a2, k0, k1, 0, 1, acc, err);
+}
+
+// Bins the FP64 path of a source would walk (0 for a single-bin sweep).
+__device__ __noinline__ long long slow_span(double fs, double fds, const Grid g) {
+  Sweep sw = make_sweep(fs, fds, g.T, g.T2);
+  if (sw.ka == sw.kb) return 0;
+  long long k0, k1;
+  sweep_bins(sw, g, &k0, &k1);
+  return k1 >= k0 ? k1 - k0 + 1 : 0;
+}
+
+// The FP64 path of one long sweep, by a whole warp: the lanes share its bins; the sum of the
+// contributions comes back in every lane.
+__device__ __noinline__ double prepass_slow_warp(double a2, double fs, double fds, const Grid g,
+                                                 const Tables tb, unsigned long long* acc,
+                                                 unsigned* err) {
+  const int lane = threadIdx.x & 31;
+  Sweep sw = make_sweep(fs, fds, g.T, g.T2);
+  long long k0, k1;
+  sweep_bins(sw, g, &k0, &k1);
+  double r = sweep_deposit(sw, g, tb, a2, k0, k1, lane, 32, acc, err);
+  for (int o = 16; o > 0; o >>= 1) r = __dadd_rn(r, __shfl_xor_sync(0xFFFFFFFFu, r, o));
   return r;
 }
 
@@ -293,6 +336,11 @@ constexpr int kPrePer = kPreTile / kPrepassThreads;    // sources per thread per
 constexpr int kSlowCap = kPrepassThreads + kPreTile;   // queue entries (drained at >= 256)
 constexpr size_t kPrepassSmem = (size_t)kPreStages * kPreTile * 3 * sizeof(double);
 
+// Sweeps longer than this many bins are walked by a whole warp (loud high-frequency sources
+// sweep up to hundreds of bins; one lane walking them in FP64 would hold its warp, and the
+// launch, long after every other warp is done).
+constexpr long long kSlowLaneBins = 4;
+
 __device__ __forceinline__ void prepass_drain(const double* __restrict__ A,
                                               const double* __restrict__ f,
                                               const double* __restrict__ fdot, const Grid& g,
@@ -300,20 +348,35 @@ __device__ __forceinline__ void prepass_drain(const double* __restrict__ A,
                                               unsigned long long* __restrict__ acc, Cands& cd,
                                               RunState* rs, const long long* q, int cnt,
                                               unsigned long long& nkappa) {
+  const int lane = threadIdx.x & 31;
   // every thread takes entries tid, tid + blockDim.x, ...
   for (int base = 0; base < cnt; base += blockDim.x) {
     const int i = base + threadIdx.x;
     const bool valid = i < cnt;
     long long s = valid ? q[i] : 0;
     double a2 = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
+    bool wide = false;
     if (valid) {
       double a = A[s];
       fs = f[s];
       fds = fdot[s];
       a2 = __dmul_rn(a, a);
-      r = prepass_slow(a2, fs, fds, g, tb, acc, &rs->err);
+      wide = slow_span(fs, fds, g) > kSlowLaneBins;
+      if (!wide) r = prepass_slow(a2, fs, fds, g, tb, acc, &rs->err);
     }
-    prepass_decide(r, tk_bits, tl_bits, valid, s, a2, fs, fds, g, cd, rs, nkappa);
+    prepass_decide(r, tk_bits, tl_bits, valid && !wide, s, a2, fs, fds, g, cd, rs, nkappa);
+    unsigned pending = __ballot_sync(0xFFFFFFFFu, wide);
+    while (pending) {
+      const int src = __ffs(pending) - 1;
+      pending &= pending - 1;
+      const long long sw_s = __shfl_sync(0xFFFFFFFFu, s, src);
+      const double sw_a2 = __shfl_sync(0xFFFFFFFFu, a2, src);
+      const double sw_f = __shfl_sync(0xFFFFFFFFu, fs, src);
+      const double sw_fd = __shfl_sync(0xFFFFFFFFu, fds, src);
+      const double rw = prepass_slow_warp(sw_a2, sw_f, sw_fd, g, tb, acc, &rs->err);
+      prepass_decide(rw, tk_bits, tl_bits, lane == 0, sw_s, sw_a2, sw_f, sw_fd, g, cd, rs,
+                     nkappa);
+    }
   }
 }
 
