@@ -160,6 +160,8 @@ class ClockSampler:
 
 
 def kernels_per_iteration(est):
+    # mean: prefix, mean, SNR, control; median: sort, median, SNR, control;
+    # median-then-mean: sort, median, prefix, mean, SNR, control
     return {0: 4, 1: 4, 2: 6}[est]
 
 
@@ -400,8 +402,10 @@ def main():
                          "iteration and the final re-estimate took %.1f s; scaled to the run's %d "
                          "iterations as t*%d/2" % (dt, st.iterations, st.iterations)}
 
-    launches = args.steps * (1 + st.iterations * kernels_per_iteration(est)
-                             + (0 if st.converged else kernels_per_iteration(est) - 1))
+    # per run: work lists, catalog pass, replica fold; then the iterations (and a final
+    # estimate when max_iter stops the loop)
+    launches = args.steps * (3 + st.iterations * kernels_per_iteration(est)
+                             + (0 if st.converged else kernels_per_iteration(est)))
     line = {
         "metric": "sources subtracted/sec to convergence", "value": value, "unit": "sources/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
