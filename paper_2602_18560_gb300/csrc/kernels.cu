@@ -1349,10 +1349,14 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const float th2f = (float)th2;
   unsigned local_new = 0, local_exact = 0;
-  for (long long cbase = ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5) * 32;
-       cbase < nlive; cbase += nwarps * 32) {
+  // group grp holds candidates grp, grp + ngroups, grp + 2 ngroups, ...: candidates that
+  // sit together in the list (the catalog pass emits the long sweeps of its FP64 path in
+  // runs) are spread over many warps
+  const long long ngroups = (nlive + 31) / 32;
+  for (long long grp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; grp < ngroups;
+       grp += nwarps) {
     bool todo = false, wide = false;
-    const long long c = cbase + lane;
+    const long long c = grp + (long long)lane * ngroups;
     int4 pk = make_int4(0, 0, 0, 0);
     if (c < nlive && !cd.res[c]) {
       pk = cd.pk[c];
@@ -1384,7 +1388,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
     }
     unsigned pending = __ballot_sync(0xFFFFFFFFu, wide);
     while (pending) {
-      const long long cw = cbase + (__ffs(pending) - 1);
+      const long long cw = grp + (long long)(__ffs(pending) - 1) * ngroups;
       pending &= pending - 1;
       int kcount;
       float r2 = screen_part(cd, cw, cd.pk[cw], g, tb, inv_f, lane, 32, kcount);
