@@ -193,12 +193,27 @@ __device__ __forceinline__ Sweep make_sweep(double f, double fdot, double T, dou
   return s;
 }
 
-// Weight of cell k for a sweep that touches more than one cell.
+// Weight of cell k for a sweep that touches more than one cell (the FP64 decision of the
+// SNR uses this, the oracle's own division).
 __device__ __forceinline__ double sweep_weight(const Sweep& s, i64 k) {
   double a = fmax(s.lo, __dsub_rn((double)k, 0.5));
   double b = fmin(s.hi, __dadd_rn((double)k, 0.5));
   if (!(b > a)) return 0.0;
   return __ddiv_rn(__dsub_rn(b, a), __dsub_rn(s.hi, s.lo));
+}
+
+// The same weight as (b - a) times inv = RN(1 / (hi - lo)), one division per sweep instead of
+// one per cell (an FP64 division is a dozen FP64-pipe operations on this GPU).  Within one
+// rounding of sweep_weight; the deposits and the removals both use it, so a removal still
+// cancels its deposit exactly.
+__device__ __forceinline__ double sweep_inv_len(const Sweep& s) {
+  return __drcp_rn(__dsub_rn(s.hi, s.lo));
+}
+__device__ __forceinline__ double sweep_weight_inv(const Sweep& s, i64 k, double inv) {
+  double a = fmax(s.lo, __dsub_rn((double)k, 0.5));
+  double b = fmin(s.hi, __dadd_rn((double)k, 0.5));
+  if (!(b > a)) return 0.0;
+  return __dmul_rn(__dsub_rn(b, a), inv);
 }
 
 }  // namespace gbsub

@@ -187,8 +187,9 @@ __device__ __forceinline__ double sweep_deposit(const Sweep& sw, const Grid& g, 
                                                 int step, unsigned long long* acc,
                                                 unsigned* err) {
   double r = 0.0;
+  const double inv = sweep_inv_len(sw);
   for (long long k = k0 + off; k <= k1; k += step) {
-    double w = sweep_weight(sw, k);
+    double w = sweep_weight_inv(sw, k, inv);
     if (w > 0.0) {
       long long j = k - g.k_lo;
       double q = __dmul_rn(__dmul_rn(a2, w), tb.gq[j]);
@@ -930,8 +931,13 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
       const int Z = zeros[l];
       const int oal = pf[la >> 5] + __popc(bl[la >> 5] & ((1u << (la & 31)) - 1u));
       const int oar = pf[ra >> 5] + __popc(bl[ra >> 5] & ((1u << (ra & 31)) - 1u));
-      const int obl = pf[lb >> 5] + __popc(bl[lb >> 5] & ((1u << (lb & 31)) - 1u));
-      const int obr = pf[rb >> 5] + __popc(bl[rb >> 5] & ((1u << (rb & 31)) - 1u));
+      // the two order statistics are neighbours: their descents share a node at most
+      // levels, and then share its ranks
+      int obl = oal, obr = oar;
+      if (__any_sync(__activemask(), la != lb || ra != rb)) {  // lanes still in the loop
+        obl = pf[lb >> 5] + __popc(bl[lb >> 5] & ((1u << (lb & 31)) - 1u));
+        obr = pf[rb >> 5] + __popc(bl[rb >> 5] & ((1u << (rb & 31)) - 1u));
+      }
       const int za = (ra - oar) - (la - oal), zb = (rb - obr) - (lb - obl);
       const int bit = 1 << (LV - 1 - l);
       if (ka < za) {
@@ -1322,8 +1328,9 @@ __device__ __forceinline__ void remove_part(const Cands& cd, long long c, const 
   }
   long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
   long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
+  const double inv = sweep_inv_len(sw);
   for (long long k = k0 + off; k <= k1; k += step) {
-    double w = sweep_weight(sw, k);
+    double w = sweep_weight_inv(sw, k, inv);
     if (w > 0.0) {
       long long j = k - g.k_lo;
       remove_q(acc, j, __dmul_rn(__dmul_rn(a2, w), tb.gq[j]));
