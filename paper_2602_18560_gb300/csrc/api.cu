@@ -537,6 +537,9 @@ static int fill_stats(sub_ctx* c, sub_stats* st) {
   if (r.err & ERR_TIMEOUT) {
     status = SUB_ETIMEOUT;
     set_err(c, "a staged copy of the catalog did not arrive in time; the run was abandoned");
+  } else if (r.err & ERR_INPUT) {
+    status = SUB_EINVAL;
+    set_err(c, "the catalog holds non-finite values of A, f or fdot; those sources were skipped");
   } else if (r.err & ERR_RANGE) {
     status = SUB_ERANGE;
     set_err(c, "a deposited power exceeded the fixed-point range (P/S_instr >= 2^31 in one bin)");

@@ -23,7 +23,14 @@ constexpr double kQLimit = 170141183460469231731687303715884105728.0;          /
 constexpr int kMaxWindow = 8192;
 
 // Error bits raised on the device.
-enum : unsigned { ERR_RANGE = 1u, ERR_WINDOW = 2u, ERR_CAND = 4u, ERR_TIMEOUT = 8u };
+enum : unsigned { ERR_RANGE = 1u, ERR_INPUT = 2u, ERR_TIMEOUT = 8u };
+
+// All three finite (exponent field not all ones), from the bits: no FP64 instruction.
+__device__ __forceinline__ bool finite3(double a, double b, double c) {
+  const unsigned long long m = 0x7FF0000000000000ull;
+  return ((__double_as_longlong(a) & m) != m) && ((__double_as_longlong(b) & m) != m) &&
+         ((__double_as_longlong(c) & m) != m);
+}
 
 // ---------------------------------------------------------------- 128-bit unsigned
 struct U128 {

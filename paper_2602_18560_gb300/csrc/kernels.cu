@@ -467,6 +467,9 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
           float x = __fadd_rn(phi, du);
           single = (x >= m) && (x < __fsub_rn(1.0f, m));
         }
+        if (single && !finite3(a2, fs, fds)) {
+          single = false;  // a non-finite amplitude or frequency derivative: refused below
+        }
         if (single) {
           valid = true;
           long long j = k0 - g.k_lo;
@@ -478,8 +481,10 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
               deposit_q(acc, j, q, &rs->err);
             r = q;
           }
-        } else {
+        } else if (finite3(a2, fs, fds)) {
           slow = true;
+        } else {
+          atomicOr(&rs->err, ERR_INPUT);  // the source is skipped; the run reports it
         }
       }
       if (slow) slow_q[atomicAdd(&slow_n, 1)] = s;
@@ -805,6 +810,13 @@ void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned lo
 
 __device__ __forceinline__ int wm_levels(int M) { return 32 - __clz(M - 1); }
 
+// Ones of a level's bitset before position i (the word holds its bits in the low half and
+// the ones of all earlier words in the high half).
+__device__ __forceinline__ int wm_rank1(const u64* rkl, int i) {
+  const u64 e = rkl[i >> 5];
+  return (int)(e >> 32) + __popc((uint32_t)e & ((1u << (i & 31)) - 1u));
+}
+
 // One tile; returns the largest relative change of S_n among its outputs (conv_rtol).
 template <typename K>
 __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
@@ -829,8 +841,9 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   uint16_t* seq1 = (uint16_t*)sm_raw;                        // [M] (steps 2-3, over sk)
   uint16_t* src = seq1 + M;                                  // [M] rank -> element
   uint16_t* seq0 = (uint16_t*)(sm_raw + sizeof(K) * (size_t)M);  // [M]
-  uint32_t* bits = (uint32_t*)(seq0 + M);                    // [LV][ws]
-  uint16_t* pre = (uint16_t*)(bits + (size_t)LV * ws);       // [LV][ws]
+  // [LV][ws]: per bitset word, its 32 bits (low half) and the ones before it (high half),
+  // so that a rank is one 64-bit load
+  u64* rk = (u64*)(seq0 + M);
 
   // 1. merged ranks.  Chunk u-1 precedes chunk u on equal keys (its positions are lower).
   for (int i = tid; i < len0; i += T) sk[i] = skey[span + i];
@@ -869,31 +882,30 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   uint16_t* nxt = seq1;
   for (int l = 0; l < LV; ++l) {
     const int sh = LV - 1 - l;
-    uint32_t* bl = bits + (size_t)l * ws;
-    uint16_t* pf = pre + (size_t)l * ws;
+    u64* rkl = rk + (size_t)l * ws;
+    uint32_t* half = (uint32_t*)rkl;  // word w: bits at half[2 w], prefix at half[2 w + 1]
     for (int it = 0; it < nit; ++it) {
       const int i = it * T + tid;
       const int b = (i < M) ? ((cur[i] >> sh) & 1) : 0;
       const unsigned w = __ballot_sync(0xFFFFFFFFu, b);
-      if (lane == 0 && i < M) bl[i >> 5] = w;
+      if (lane == 0 && i < M) half[2 * (i >> 5)] = w;
     }
     __syncthreads();
     if (warp == 0) {
       int run = 0;
       for (int w0 = 0; w0 < nwm; w0 += 32) {
         const int w = w0 + lane;
-        const int c = (w < nwm) ? __popc(bl[w]) : 0;
+        const int c = (w < nwm) ? __popc(half[2 * w]) : 0;
         int incl = c;
         for (int s = 1; s < 32; s <<= 1) {
           int t = __shfl_up_sync(0xFFFFFFFFu, incl, s);
           if (lane >= s) incl += t;
         }
-        if (w < nwm) pf[w] = (uint16_t)(run + incl - c);
+        if (w < nwm) half[2 * w + 1] = (uint32_t)(run + incl - c);
         run += __shfl_sync(0xFFFFFFFFu, incl, 31);
       }
       if (lane == 0) {
-        pf[nwm] = (uint16_t)run;
-        bl[nwm] = 0u;
+        rkl[nwm] = (u64)run << 32;
         zeros[l] = M - run;
       }
     }
@@ -904,7 +916,8 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
         const int i = it * T + tid;
         if (i < M) {
           const int x = cur[i];
-          const int ob = pf[i >> 5] + __popc(bl[i >> 5] & ((1u << lane) - 1u));
+          const u64 e = rkl[i >> 5];
+          const int ob = (int)(e >> 32) + __popc((uint32_t)e & ((1u << lane) - 1u));
           nxt[((x >> sh) & 1) ? Z + ob : i - ob] = (uint16_t)x;
         }
       }
@@ -926,17 +939,16 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
     int la = (int)(s - span), ra = (int)(e + 1 - span), ka = cnt >> 1, va = 0;
     int lb = la, rb = ra, kb = ka > 0 ? ka - 1 : 0, vb = 0;
     for (int l = 0; l < LV; ++l) {
-      const uint32_t* bl = bits + (size_t)l * ws;
-      const uint16_t* pf = pre + (size_t)l * ws;
+      const u64* rkl = rk + (size_t)l * ws;
       const int Z = zeros[l];
-      const int oal = pf[la >> 5] + __popc(bl[la >> 5] & ((1u << (la & 31)) - 1u));
-      const int oar = pf[ra >> 5] + __popc(bl[ra >> 5] & ((1u << (ra & 31)) - 1u));
+      const int oal = wm_rank1(rkl, la);
+      const int oar = wm_rank1(rkl, ra);
       // the two order statistics are neighbours: their descents share a node at most
       // levels, and then share its ranks
       int obl = oal, obr = oar;
       if (__any_sync(__activemask(), la != lb || ra != rb)) {  // lanes still in the loop
-        obl = pf[lb >> 5] + __popc(bl[lb >> 5] & ((1u << (lb & 31)) - 1u));
-        obr = pf[rb >> 5] + __popc(bl[rb >> 5] & ((1u << (rb & 31)) - 1u));
+        obl = wm_rank1(rkl, lb);
+        obr = wm_rank1(rkl, rb);
       }
       const int za = (ra - oar) - (la - oal), zb = (rb - obr) - (lb - obl);
       const int bit = 1 << (LV - 1 - l);
@@ -1005,7 +1017,7 @@ size_t median_smem_bytes(int Kc, int key_bytes) {
   int M = 2 * Kc, LV = 0;
   while ((1 << LV) < M) ++LV;
   size_t ws = (size_t)M / 32 + 1;
-  return (size_t)key_bytes * M + (size_t)2 * M + (size_t)LV * ws * (4 + 2);
+  return (size_t)key_bytes * M + (size_t)2 * M + (size_t)LV * ws * 8;
 }
 
 void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,

@@ -341,3 +341,17 @@ def test_mixed_precision_1e6_workload():
     st, ref, ndiff, err = mixed_vs_oracle(A, f, fdot, w.T_obs, gbsub.MEDIAN_MEAN, 1000)
     assert ndiff == 0
     assert st.iterations == ref["iterations"]
+
+
+def test_non_finite_catalog_values_are_reported():
+    A, f, fdot = synth.catalog(5000, 61, synth.Population(3.5, 2.0))
+    for field, bad in ((0, np.inf), (1, np.nan), (2, -np.inf), (1, np.inf)):
+        cat = [A.copy(), f.copy(), fdot.copy()]
+        cat[field][1234] = bad
+        with gbsub.Subtraction(T_obs=synth.YEAR, window=100) as s:
+            s.load(*cat)
+            with pytest.raises(gbsub.SubError) as ei:
+                s.run()
+            assert ei.value.code == gbsub.EINVAL
+            s.load(A, f, fdot)   # a clean catalog runs normally afterwards
+            assert s.run().n_sources == len(A)
