@@ -64,9 +64,12 @@ extern "C" {
 #define SUB_MIXED 1
 #define SUB_FP64_STRICT 2
 
-/* Location of a caller buffer. */
+/* Location of a caller buffer.  SUB_HOST_MAPPED (catalog only): page-locked host memory
+ * that the catalog pass reads in place over the host link, with no copy (see
+ * sub_load_catalog). */
 #define SUB_HOST 0
 #define SUB_DEVICE 1
+#define SUB_HOST_MAPPED 2
 
 /* Problem statement (Sec. III.A: T_obs, band, grid 1/T_obs; App. C S_instr;
  * App. D window N, rho_th, kappa). */
@@ -119,11 +122,18 @@ int sub_params_default(sub_params* p);
  * Errors: SUB_EINVAL (bad parameters), SUB_ENOMEM, SUB_ECUDA, SUB_EBUDGET. */
 int sub_create(const sub_params* p, void* stream, sub_ctx** out);
 
-/* Copy a catalog of n sources into the context (SoA, FP64, n >= 0).
+/* Load a catalog of n sources into the context (SoA, FP64, n >= 0).
  *   A    : strain amplitudes (>= 0), Eq. (GB waveform).
  *   f    : frequencies in Hz at t = 0, Eq. (phase Taylor expansion).
  *   fdot : frequency derivatives in Hz/s (either sign).
- *   where: SUB_HOST or SUB_DEVICE for all three arrays.
+ *   where: for all three arrays:
+ *          SUB_HOST, SUB_DEVICE: the arrays are copied on the context's stream; page-locked
+ *            or device arrays stay unchanged until the stream has passed the copies (a
+ *            sub_run that waits, or a stream synchronisation);
+ *          SUB_HOST_MAPPED: page-locked host memory (cudaHostAlloc, cudaHostRegister or a
+ *            pinned tensor) that every later sub_run reads in place; nothing is copied, and
+ *            the caller keeps the arrays alive and unchanged until the next load or
+ *            sub_destroy.  Memory that is not page-locked: SUB_EINVAL.
  * Replaces any previous catalog.  Errors: SUB_EINVAL, SUB_ENOMEM, SUB_EBUDGET,
  * SUB_ECUDA. */
 int sub_load_catalog(sub_ctx* ctx, const double* A, const double* f, const double* fdot,

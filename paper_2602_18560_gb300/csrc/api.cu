@@ -217,7 +217,7 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
       {(void**)&c->pre_lo, (size_t)ncell * 8}, {(void**)&c->pre_hi, (size_t)ncell * 8},
       {(void**)&c->uflow, (size_t)pl.nch * 4},
       {(void**)&c->rs, sizeof(RunState)}, {(void**)&c->new_hist, (size_t)p->max_iter * 4},
-      {(void**)&c->dN, 8},
+      {(void**)&c->dcat, sizeof(CatalogRef)},
   };
   for (auto& w : want) {
     rc = dalloc(c, w.p, w.b);
@@ -285,25 +285,53 @@ static int reserve_sources(sub_ctx* c, int64_t n) {
   return SUB_OK;
 }
 
+// Device address of page-locked host memory, or nullptr when p is not such memory.
+static const double* mapped_address(const double* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // an unknown pointer leaves a (non-sticky) error behind
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
+  return static_cast<const double*>(at.devicePointer);
+}
+
 extern "C" int sub_load_catalog(sub_ctx* c, const double* A, const double* f, const double* fdot,
                                 int64_t n, int where) {
   if (!c) return SUB_EINVAL;
-  if (n < 0 || (n > 0 && (!A || !f || !fdot)) || (where != SUB_HOST && where != SUB_DEVICE)) {
+  if (n < 0 || (n > 0 && (!A || !f || !fdot)) ||
+      (where != SUB_HOST && where != SUB_DEVICE && where != SUB_HOST_MAPPED)) {
     set_err(c, "invalid catalog arguments");
     return SUB_EINVAL;
   }
   if (n > ((int64_t)1 << 40)) { set_err(c, "catalog too large"); return SUB_EINVAL; }
+  CatalogRef ref = {nullptr, nullptr, nullptr, (long long)n, 1, 0};
+  if (where == SUB_HOST_MAPPED && n > 0) {
+    ref.A = mapped_address(A);
+    ref.f = mapped_address(f);
+    ref.fdot = mapped_address(fdot);
+    if (!ref.A || !ref.f || !ref.fdot) {
+      set_err(c, "SUB_HOST_MAPPED needs page-locked (pinned) host memory");
+      return SUB_EINVAL;
+    }
+    ref.staged = 0;
+  }
   {
     int rc = reserve_sources(c, n);
     if (rc) return rc;
   }
-  if (n > 0) {
-    cudaMemcpyKind k = where == SUB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    CU(cudaMemcpyAsync(c->A, A, (size_t)n * 8, k, c->stream), c);
-    CU(cudaMemcpyAsync(c->f, f, (size_t)n * 8, k, c->stream), c);
-    CU(cudaMemcpyAsync(c->fdot, fdot, (size_t)n * 8, k, c->stream), c);
+  if (where != SUB_HOST_MAPPED) {
+    ref.A = c->A;
+    ref.f = c->f;
+    ref.fdot = c->fdot;
+    if (n > 0) {
+      cudaMemcpyKind k = where == SUB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+      CU(cudaMemcpyAsync(c->A, A, (size_t)n * 8, k, c->stream), c);
+      CU(cudaMemcpyAsync(c->f, f, (size_t)n * 8, k, c->stream), c);
+      CU(cudaMemcpyAsync(c->fdot, fdot, (size_t)n * 8, k, c->stream), c);
+    }
   }
-  launch_set_i64(c->dN, (long long)n, c->stream);
+  launch_set_catalog(c->dcat, ref, c->stream);
   CU(cudaGetLastError(), c);
   c->N = n;
   c->ran = false;
@@ -383,9 +411,8 @@ static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
   if ((e = cudaMemsetAsync(c->resolved, 0, (size_t)c->cap_N, st))) return e;
   {
     KTimer t(c, st, SUB_K_PREPASS);
-    launch_prepass(c->A, c->f, c->fdot, c->dN, c->cap_N, c->grid, tables_of(c),
-                   thr_kappa_of(c), thr_live_of(c), c->acc, c->rep, c->cd, c->rs, c->nsm_run,
-                   c->test_flags, st);
+    launch_prepass(c->dcat, c->cap_N, c->grid, tables_of(c), thr_kappa_of(c), thr_live_of(c),
+                   c->acc, c->rep, c->cd, c->rs, c->nsm_run, c->test_flags, st);
   }
   return cudaGetLastError();
 }

@@ -13,6 +13,7 @@
 #include "kernels.cuh"
 
 using gbsub::AccReplicas;
+using gbsub::CatalogRef;
 using gbsub::Cands;
 using gbsub::Grid;
 using gbsub::RunState;
@@ -54,7 +55,7 @@ struct sub_ctx {
   int64_t N = -1;        // sources loaded (-1: none)
   int64_t cap_N = 0;     // capacity of the per-source buffers
   double *A = nullptr, *f = nullptr, *fdot = nullptr;
-  long long* dN = nullptr;  // the catalog size on the device (read by the catalog pass)
+  CatalogRef* dcat = nullptr;  // where the catalog pass reads the catalog (on the device)
   int test_flags = 0;       // sub_test_hooks
   Cands cd = {};
   unsigned char* resolved = nullptr;

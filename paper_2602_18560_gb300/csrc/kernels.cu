@@ -382,15 +382,18 @@ __device__ __forceinline__ void prepass_drain(const double* __restrict__ A,
 }
 
 __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
-    const double* __restrict__ A, const double* __restrict__ f, const double* __restrict__ fdot,
-    const long long* __restrict__ pN, Grid g, Tables tb, double thr_kappa, double thr_live,
+    const CatalogRef* __restrict__ cat, Grid g, Tables tb, double thr_kappa, double thr_live,
     unsigned long long* __restrict__ acc, AccReplicas rep, Cands cd, RunState* rs,
     int test_flags) {
   extern __shared__ __align__(128) double pre_tiles[];  // [stage][A | f | fdot][kPreTile]
   __shared__ __align__(8) uint64_t bar[kPreStages];
   __shared__ long long stage_tile[kPreStages];  // tile held by each stage
   __shared__ int stage_copying[kPreStages];     // its copies were started
-  const long long N = *pN;
+  const double* __restrict__ A = cat->A;
+  const double* __restrict__ f = cat->f;
+  const double* __restrict__ fdot = cat->fdot;
+  const long long N = cat->n;
+  const bool use_tma = cat->staged != 0;
   __shared__ long long slow_q[kSlowCap];
   __shared__ int slow_n;
   const int tid = threadIdx.x;
@@ -400,7 +403,9 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
   const u64 tl_bits = (u64)__double_as_longlong(thr_live);
   unsigned long long nkappa = 0;
   const long long ntiles = (N + kPreTile - 1) / kPreTile;
-  const long long nfull = N / kPreTile;  // full tiles come through TMA, the ragged one directly
+  // full tiles of device memory come through TMA; the ragged one, and every tile of a catalog
+  // in host memory, through plain loads
+  const long long nfull = use_tma ? N / kPreTile : 0;
   // Thread 0 takes the next tile from the global counter (CTAs that run faster take more
   // tiles) and, when it is full, starts its copy into `stage`.
   auto fetch = [&](int stage) {
@@ -442,6 +447,23 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
     const double* sA = pre_tiles + (size_t)stage * 3 * kPreTile;
     const double* sF = sA + kPreTile;
     const double* sD = sF + kPreTile;
+    // every load of the tile first: from host memory each one takes a microsecond or more
+    double av[kPrePer], fv[kPrePer], dv[kPrePer];
+#pragma unroll
+    for (int k = 0; k < kPrePer; ++k) {
+      const int idx = tid + k * kPrepassThreads;
+      const long long s = t * kPreTile + idx;
+      av[k] = fv[k] = dv[k] = 0.0;
+      if (staged) {
+        av[k] = sA[idx];
+        fv[k] = sF[idx];
+        dv[k] = sD[idx];
+      } else if (s < N) {
+        av[k] = A[s];
+        fv[k] = f[s];
+        dv[k] = fdot[s];
+      }
+    }
 #pragma unroll
     for (int k = 0; k < kPrePer; ++k) {
       const int idx = tid + k * kPrepassThreads;
@@ -449,9 +471,9 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
       bool valid = false, slow = false;
       double a2 = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
       if (s < N) {
-        double a = staged ? sA[idx] : A[s];
-        fs = staged ? sF[idx] : f[s];
-        fds = staged ? sD[idx] : fdot[s];
+        const double a = av[k];
+        fs = fv[k];
+        fds = dv[k];
         a2 = __dmul_rn(a, a);
         // Common case without FP64: bin of f T + 1/2 exactly, and an FP32 bound on the
         // sweep fdot T^2 proving that f T + fdot T^2 + 1/2 stays in the same bin (the FP64
@@ -520,23 +542,22 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
   if (lane == 0 && nkappa) atomicAdd(&rs->ncand, nkappa);
 }
 
-void launch_prepass(const double* A, const double* f, const double* fdot, const long long* pN,
-                    long long cap, const Grid& g, const Tables& tb, double thr_kappa,
-                    double thr_live, unsigned long long* acc, AccReplicas rep, Cands cd,
-                    RunState* rs, int nsm, int test_flags, cudaStream_t st) {
+void launch_prepass(const CatalogRef* cat, long long cap, const Grid& g, const Tables& tb,
+                    double thr_kappa, double thr_live, unsigned long long* acc, AccReplicas rep,
+                    Cands cd, RunState* rs, int nsm, int test_flags, cudaStream_t st) {
   long long tiles = (cap + kPreTile - 1) / kPreTile;
   long long lim = (long long)nsm * 4;  // resident CTAs (launch bounds, shared memory)
   int bl = (int)(tiles < lim ? (tiles < 1 ? 1 : tiles) : lim);
-  k_prepass<<<bl, kPrepassThreads, kPrepassSmem, st>>>(A, f, fdot, pN, g, tb, thr_kappa,
-                                                       thr_live, acc, rep, cd, rs, test_flags);
+  k_prepass<<<bl, kPrepassThreads, kPrepassSmem, st>>>(cat, g, tb, thr_kappa, thr_live, acc,
+                                                       rep, cd, rs, test_flags);
   if (rep.nbins > 0)
     k_fold_replicas<<<(unsigned)((rep.nbins + 255) / 256), 256, 0, st>>>(acc, rep);
 }
 
-__global__ void k_set_i64(long long* p, long long v) { *p = v; }
+__global__ void k_set_catalog(CatalogRef* p, CatalogRef v) { *p = v; }
 
-void launch_set_i64(long long* p, long long v, cudaStream_t st) {
-  k_set_i64<<<1, 1, 0, st>>>(p, v);
+void launch_set_catalog(CatalogRef* p, const CatalogRef& v, cudaStream_t st) {
+  k_set_catalog<<<1, 1, 0, st>>>(p, v);
 }
 
 // ============================================================================ reductions

@@ -147,16 +147,26 @@ struct AccReplicas {
   long long nbins;
 };
 
-// The catalog pass over the *pN sources (read on the device, so that one captured launch
-// serves every catalog of up to cap sources).  test_flags & 1: issue no catalog copies, so
+// Where the catalog pass finds the catalog.  Each load writes it on the stream, so that one
+// captured launch serves every catalog of up to the capacity it was built for.
+struct CatalogRef {
+  const double* A;
+  const double* f;
+  const double* fdot;
+  long long n;
+  int staged;  // 1: device memory, staged in tiles by bulk copies
+               // 0: page-locked host memory, read in place with plain loads
+  int pad;
+};
+
+// The catalog pass over the cat->n sources.  test_flags & 1: issue no catalog copies, so
 // that the bounded waits run out (tests of the timeout path).
-void launch_prepass(const double* A, const double* f, const double* fdot, const long long* pN,
-                    long long cap, const Grid& g, const Tables& tb, double thr_kappa,
-                    double thr_live, unsigned long long* acc, AccReplicas rep, Cands cd,
-                    RunState* rs, int nsm, int test_flags, cudaStream_t st);
+void launch_prepass(const CatalogRef* cat, long long cap, const Grid& g, const Tables& tb,
+                    double thr_kappa, double thr_live, unsigned long long* acc, AccReplicas rep,
+                    Cands cd, RunState* rs, int nsm, int test_flags, cudaStream_t st);
 
 // *p = v on the stream.
-void launch_set_i64(long long* p, long long v, cudaStream_t st);
+void launch_set_catalog(CatalogRef* p, const CatalogRef& v, cudaStream_t st);
 
 // P[j] = S_j Q_j 2^-96 for every bin.
 void launch_power_out(const unsigned long long* acc, const double* S, long long n, double* P,

@@ -21,7 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ETIMEOUT, EBUDGET, ERANGE, ESTATE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
 MEAN, MEDIAN, MEDIAN_MEAN = 0, 1, 2
 FP64, MIXED, FP64_STRICT = 0, 1, 2
-HOST, DEVICE = 0, 1
+HOST, DEVICE, HOST_MAPPED = 0, 1, 2
 YEAR = 365.25 * 86400.0
 
 _ERRNAMES = {OK: "SUB_OK", EINVAL: "SUB_EINVAL", ENOMEM: "SUB_ENOMEM", ECUDA: "SUB_ECUDA",
@@ -210,11 +210,17 @@ def sub_create(params: sub_params, stream=None):
     return ctx
 
 
-def sub_load_catalog(ctx, A, f, fdot):
+def sub_load_catalog(ctx, A, f, fdot, mapped=False):
+    """mapped: the arrays are page-locked host memory that every run reads in place
+    (SUB_HOST_MAPPED); the caller keeps them alive and unchanged until the next load."""
     (pa, wa, na), (pf, wf, nf), (pd, wd, nd) = (_ptr(A, np.float64), _ptr(f, np.float64),
                                                 _ptr(fdot, np.float64))
     if not (na == nf == nd) or not (wa == wf == wd):
         raise ValueError("A, f, fdot must have the same length and location")
+    if mapped:
+        if wa != HOST:
+            raise ValueError("a mapped catalog lives in host memory")
+        wa = HOST_MAPPED
     return _check(ctx, lib().sub_load_catalog(ctx, pa, pf, pd, na, wa))
 
 
@@ -325,9 +331,10 @@ class Subtraction:
         self.ctx = sub_create(self.params, stream)
         self.n_sources = None
 
-    def load(self, A, f, fdot):
-        sub_load_catalog(self.ctx, A, f, fdot)
+    def load(self, A, f, fdot, mapped=False):
+        sub_load_catalog(self.ctx, A, f, fdot, mapped)
         self.n_sources = int(len(A))
+        self._mapped = (A, f, fdot) if mapped else None  # kept alive while runs read them
         return self
 
     def run(self, wait=True):

@@ -70,6 +70,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(sub_server_params, f_min),
          offsetof(sub_job_result, stats), offsetof(sub_job_result, latency_ms),
          offsetof(sub_server_stats, inflight));
+  printf("%d %d %d\n", SUB_HOST, SUB_DEVICE, SUB_HOST_MAPPED);
   return 0;
 }
 ''')
@@ -77,7 +78,8 @@ int main(void) {
     subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     out = subprocess.check_output([str(exe)]).decode().split()
     sizes = [int(x) for x in out[:5]]
-    offs = [int(x) for x in out[5:]]
+    offs = [int(x) for x in out[5:9]]
+    assert [int(x) for x in out[9:]] == [gbsub.HOST, gbsub.DEVICE, gbsub.HOST_MAPPED]
     assert sizes == [ctypes.sizeof(t) for t in (gbsub.sub_params, gbsub.sub_stats,
                                                 gbsub.sub_server_params, gbsub.sub_job_result,
                                                 gbsub.sub_server_stats)]

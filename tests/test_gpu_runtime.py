@@ -222,3 +222,27 @@ def test_server_pool_stays_within_max_contexts():
         st, sg_s, m_s = solo(T, A, f, fdot, window=1000, estimator=gbsub.MEDIAN_MEAN)
         assert np.array_equal(sg.view(np.uint64), sg_s.view(np.uint64))
         assert np.array_equal(m, m_s)
+
+
+def test_mapped_catalog_equals_a_copied_one():
+    # the catalog pass reads page-locked host memory in place: same bits as a copied catalog,
+    # through one captured graph whatever the last load was (mapped, copied, ragged size)
+    import torch
+    T, A, f, fdot = jobs(1, seed=13, n_lo=3e5, n_hi=3e5)[0]
+    kw = dict(window=1000, estimator=gbsub.MEDIAN_MEAN)
+    pins = [torch.from_numpy(x.copy()).pin_memory() for x in (A, f, fdot)]
+    n = len(A) // 3 + 7
+    with gbsub.Subtraction(T_obs=T, **kw) as s:
+        s.load(*pins, mapped=True)
+        same((s.run(), s.spectrum(), s.resolved()), solo(T, A, f, fdot, **kw))
+        s.load(A, f, fdot)
+        same((s.run(), s.spectrum(), s.resolved()), solo(T, A, f, fdot, **kw))
+        s.load(*(p[:n] for p in pins), mapped=True)
+        same((s.run(), s.spectrum(), s.resolved()), solo(T, A[:n], f[:n], fdot[:n], **kw))
+        with pytest.raises(gbsub.SubError) as ei:
+            s.load(A.copy(), f, fdot, mapped=True)  # pageable memory
+        assert ei.value.code == gbsub.EINVAL
+    with gbsub.Subtraction(T_obs=T, precision=gbsub.MIXED, **kw) as s:
+        s.load(*pins, mapped=True)
+        same((s.run(), s.spectrum(), s.resolved()),
+             solo(T, A, f, fdot, precision=gbsub.MIXED, **kw))
