@@ -648,6 +648,167 @@ __device__ __forceinline__ void cmp_keep(K& k, int& x, K ko, int xo, bool keep_m
   }
 }
 
+// Re-sort of a chunk whose values changed at few positions since it was last sorted (the
+// iterations after the first remove a few sources each).  The unchanged elements keep their
+// relative order.  An unchanged element's new index is its old index, less the changed
+// elements before it in the old order, plus the changed elements whose new (key, position)
+// precede it; a changed element's new index is its rank among the changed elements plus the
+// unchanged elements that precede it, found by a binary search of the old order.  This is
+// the (key, position) order the full sort produces, so the two paths write the same arrays.
+// Returns false, having written nothing, when more than kResortMax positions changed.
+constexpr int kResortMax = 128;
+
+template <typename K>
+__device__ __forceinline__ bool key_pos_less(K ka, int pa, K kb, int pb) {
+  return ka < kb || (ka == kb && pa < pb);
+}
+
+template <int E, typename K>
+__device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __restrict__ skey_c,
+                                   uint16_t* __restrict__ srank_c, unsigned char* raw) {
+  K* old_k = (K*)raw;                                // [kpad] old keys, in old sorted order
+  K* ch_k = old_k + kpad;                            // [kResortMax] changed: new keys
+  K* cs_k = ch_k + kResortMax;                       // [kResortMax] the same, sorted
+  uint16_t* old_p = (uint16_t*)(cs_k + kResortMax);  // [kpad] position of each old index
+  uint16_t* csum = old_p + kpad;                     // [kpad + 2] changed before an old index
+  uint16_t* ch_p = csum + kpad + 2;                  // [kResortMax] changed: positions
+  uint16_t* cs_p = ch_p + kResortMax;                // [kResortMax] the same, sorted
+  unsigned char* chg = (unsigned char*)(cs_p + kResortMax);  // [kpad] changed, by position
+  __shared__ int n_changed;
+  __shared__ int bad_state;
+  __shared__ int warp_sum[32];
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  // 1. the old sorted state of the chunk (an index out of range, which a consistent state
+  // never holds, sends the chunk to the full sort)
+  if (tid == 0) {
+    n_changed = 0;
+    bad_state = 0;
+  }
+  for (int i = tid; i < len; i += T) old_k[i] = skey_c[i];
+  int r[E];
+#pragma unroll
+  for (int a = 0; a < E; ++a) {
+    const int p = tid * E + a;
+    r[a] = p < len ? (int)srank_c[p] : 0;
+    if (r[a] >= len) {
+      bad_state = 1;
+      r[a] = 0;
+    }
+  }
+  __syncthreads();
+  if (bad_state) {
+    __syncthreads();  // every thread has read the flag
+    return false;
+  }
+#pragma unroll
+  for (int a = 0; a < E; ++a) {
+    const int p = tid * E + a;
+    if (p < len) old_p[r[a]] = (uint16_t)p;
+  }
+  __syncthreads();
+  // 2. positions whose key changed, gathered in any order
+#pragma unroll
+  for (int a = 0; a < E; ++a) {
+    const int p = tid * E + a;
+    const bool c = p < len && knew[a] != old_k[r[a]];
+    chg[p] = c ? 1 : 0;
+    if (c) {
+      const int slot = atomicAdd(&n_changed, 1);
+      if (slot < kResortMax) {
+        ch_k[slot] = knew[a];
+        ch_p[slot] = (uint16_t)p;
+      }
+    }
+  }
+  __syncthreads();
+  const int C = n_changed;
+  __syncthreads();  // every thread has read the count before the caller reuses shared memory
+  if (C > kResortMax) return false;
+  if (C == 0) return true;
+  // 3. csum[i] = changed elements among old indices < i (exclusive scan in old order)
+  int f[E], run = 0;
+#pragma unroll
+  for (int a = 0; a < E; ++a) {
+    const int i = tid * E + a;
+    f[a] = i < len ? chg[old_p[i] & (kpad - 1)] : 0;
+    run += f[a];
+  }
+  int incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_sum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = T >> 5;
+    int v = lane < nw ? warp_sum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane < nw) warp_sum[lane] = v;  // inclusive over warps
+  }
+  __syncthreads();
+  int ex = incl - run + (wid > 0 ? warp_sum[wid - 1] : 0);
+#pragma unroll
+  for (int a = 0; a < E; ++a) {
+    const int i = tid * E + a;
+    if (i < len) csum[i] = (uint16_t)ex;
+    ex += f[a];
+  }
+  if (tid == 0) csum[len] = (uint16_t)C;
+  __syncthreads();
+  // 4. changed elements: rank among themselves, plus the unchanged ones before them
+  for (int t = tid; t < C; t += T) {
+    const K ke = ch_k[t];
+    const int pe = ch_p[t];
+    int crank = 0;
+    for (int u = 0; u < C; ++u) crank += key_pos_less<K>(ch_k[u], ch_p[u], ke, pe) ? 1 : 0;
+    int lo = 0, hi = len;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (key_pos_less<K>(old_k[mid], old_p[mid], ke, pe))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int ni = crank + lo - (int)csum[lo];
+    cs_k[crank] = ke;
+    cs_p[crank] = (uint16_t)pe;
+    if (ni < len) {  // always, for a consistent old state
+      skey_c[ni] = ke;
+      srank_c[pe] = (uint16_t)ni;
+    }
+  }
+  __syncthreads();
+  // 5. unchanged elements: old index, less the changed before, plus the changed below them
+#pragma unroll
+  for (int a = 0; a < E; ++a) {
+    const int i = tid * E + a;
+    if (i < len && !f[a]) {
+      const K ki = old_k[i];
+      const int pi = old_p[i];
+      int lo = 0, hi = C;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key_pos_less<K>(cs_k[mid], cs_p[mid], ki, pi))
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      const int ni = i - (int)csum[i] + lo;
+      if (ni < len && pi < len) {  // always, for a consistent old state
+        skey_c[ni] = ki;
+        srank_c[pi] = (uint16_t)ni;
+      }
+    }
+  }
+  return true;
+}
+
 template <int E, typename K>
 __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
                                                      K* __restrict__ skey,
@@ -658,6 +819,9 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
   const int T = blockDim.x, tid = threadIdx.x;
   const int kpad = pl.kpad;  // = T * E
   const int nitem = d.count(kListR0, pl.nch);
+  // after the first iteration of a tracked run every chunk holds the sorted state of its
+  // previous values
+  const bool resort = d.base != nullptr && d.rs->iter > 0;
   for (int item = blockIdx.x; item < nitem; item += gridDim.x) {
     const int b = d.item(kListR0, item);  // a chunk whose input changed
     const long long base = (long long)b * pl.Kc;
@@ -671,6 +835,10 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
       if (i < len) kv = sort_key<K>(spec_value(in, base + i), pl.key_scale);
       k[a] = kv;
       x[a] = i;
+    }
+    if (resort && resort_few_changes<E, K>(k, len, kpad, skey + base, srank + base, sort_raw)) {
+      __syncthreads();  // before the next chunk overwrites shared memory
+      continue;
     }
     bool first_smem = true;
     for (int kk = 2; kk <= kpad; kk <<= 1) {
@@ -783,7 +951,11 @@ static void launch_sort_as(void (*kern)(SpecIn, long long, SmoothPlan, K*, uint1
 static int sort_per_thread(const SmoothPlan& pl) { return pl.kpad <= 2048 ? 2 : pl.kpad / 1024; }
 static int sort_threads(const SmoothPlan& pl) { return pl.kpad / sort_per_thread(pl); }
 static size_t sort_smem(const SmoothPlan& pl) {
-  return (size_t)pl.kpad * ((pl.fp32_keys ? 4 : 8) + sizeof(uint16_t));
+  const size_t kb = pl.fp32_keys ? 4 : 8;
+  const size_t full = (size_t)pl.kpad * (kb + sizeof(uint16_t));
+  const size_t few = (size_t)pl.kpad * (kb + 2 + 1) + (size_t)(pl.kpad + 2) * 2 +
+                     (size_t)kResortMax * 2 * (kb + 2);
+  return full > few ? full : few;
 }
 template <typename K, typename F>
 static void with_sort_kernel_k(const SmoothPlan& pl, F fn) {
@@ -1577,10 +1749,13 @@ void configure_kernels() {
   cudaFuncSetAttribute(k_prepass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepassSmem);
   SmoothPlan p64 = {}, p32 = {};
   p32.fp32_keys = 1;
-  for (int kp : {64, 4096, 8192}) {
+  for (int kp : {64, 4096, 8192}) {  // one of each instantiation; 8192: the widest sort
     p64.kpad = p32.kpad = kp;
     auto set = [](auto kern) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      SmoothPlan widest = {};
+      widest.kpad = 8192;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sort_smem(widest));
     };
     with_sort_kernel(p64, set);
     with_sort_kernel(p32, set);

@@ -158,6 +158,14 @@ def test_dense_catalog_many_iterations(dense, est, W):
         assert st.iterations >= 3
 
 
+def test_widest_window_run(dense):
+    # W = 8192: the widest chunks (eight elements per sorting thread) through a whole run,
+    # the re-sorts of chunks with few changed bins included
+    A, f, fdot = dense
+    keep = f < 1e-3
+    compare_run(A[keep], f[keep], fdot[keep], synth.YEAR, gbsub.MEDIAN_MEAN, 8192, f_max=1e-3)
+
+
 def test_chirping_sources_span_many_bins():
     A, f, fdot = synth.catalog(20000, 5, synth.Population(2.0, 2.0))
     fdot = fdot * 3e3   # sweeps of up to hundreds of bins, some leaving the band
