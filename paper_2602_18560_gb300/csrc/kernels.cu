@@ -1037,88 +1037,100 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   // [LV][ws]: per bitset word, its 32 bits (low half) and the ones before it (high half),
   // so that a rank is one 64-bit load
   u64* rk = (u64*)(seq0 + M);
+  uint16_t* mr = (uint16_t*)rk;  // [M] merged index of (chunk, sorted index) (step 1, over rk)
+  __shared__ int warp_ones[32];
 
   // 1. merged ranks.  Chunk u-1 precedes chunk u on equal keys (its positions are lower).
   for (int i = tid; i < len0; i += T) sk[i] = skey[span + i];
   for (int i = tid; i < len1; i += T) sk[Kc + i] = skey[span + Kc + i];
   __syncthreads();
+  {
+    // merge path: thread t emits the merged indices [d0, d1) of the two sorted chunks,
+    // starting where a binary search on the diagonal d0 puts it
+    const int L = len0 + len1, per = (L + T - 1) / T;
+    const int d0 = min(tid * per, L), d1 = min(d0 + per, L);
+    if (d0 < d1) {
+      const K* A = sk;
+      const K* B = sk + Kc;
+      int lo = max(0, d0 - len1), hi = min(d0, len0);
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] <= B[d0 - 1 - mid])
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      int i = lo, j = d0 - lo;
+      for (int m = d0; m < d1; ++m) {
+        if (i < len0 && (j >= len1 || A[i] <= B[j]))
+          mr[i++] = (uint16_t)m;
+        else
+          mr[Kc + j++] = (uint16_t)m;
+      }
+    }
+  }
+  __syncthreads();
   for (int p = tid; p < M; p += T) {
     const int X = p >= Kc, q = p - X * Kc;
-    const int lenX = X ? len1 : len0;
     int v;
-    if (q < lenX) {
+    if (q < (X ? len1 : len0)) {
       const int si = srank[span + p];
-      const K key = sk[p - q + si];
-      const K* oth = X ? sk : sk + Kc;
-      int lo = 0, hi = X ? len0 : len1;
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        K km = oth[mid];
-        bool before = X ? (km <= key) : (km < key);
-        if (before) lo = mid + 1; else hi = mid;
-      }
-      v = si + lo;
+      v = mr[X * Kc + si];
+      src[v] = (uint16_t)((X << 15) | si);
     } else {
       v = len0 + len1 + (X ? (Kc - len0) + (q - len1) : (q - len0));
     }
     seq0[p] = (uint16_t)v;
   }
   __syncthreads();
-  for (int p = tid; p < M; p += T) {
-    const int X = p >= Kc, q = p - X * Kc;
-    if (q < (X ? len1 : len0)) src[seq0[p]] = (uint16_t)((X << 15) | srank[span + p]);
-  }
 
-  // 2. wavelet matrix (T is a multiple of 32 and M of 64: every warp covers whole words)
-  const int nit = (M + T - 1) / T;
+  // 2. wavelet matrix.  Warp w owns the words [w wpw, (w + 1) wpw) of every level (M is a
+  // multiple of 64: whole words).  A level takes two barriers: one after the warps have
+  // counted their ones, one after the stable partition.
+  const int nwarp = T >> 5;
+  const int wpw = (nwm + nwarp - 1) / nwarp;
+  const int w0 = warp * wpw, w1 = min(w0 + wpw, nwm);
   uint16_t* cur = seq0;
   uint16_t* nxt = seq1;
   for (int l = 0; l < LV; ++l) {
     const int sh = LV - 1 - l;
     u64* rkl = rk + (size_t)l * ws;
-    uint32_t* half = (uint32_t*)rkl;  // word w: bits at half[2 w], prefix at half[2 w + 1]
-    for (int it = 0; it < nit; ++it) {
-      const int i = it * T + tid;
-      const int b = (i < M) ? ((cur[i] >> sh) & 1) : 0;
-      const unsigned w = __ballot_sync(0xFFFFFFFFu, b);
-      if (lane == 0 && i < M) half[2 * (i >> 5)] = w;
+    int mine = 0;
+    for (int k = w0; k < w1; ++k)
+      mine += __popc(__ballot_sync(0xFFFFFFFFu, (cur[k * 32 + lane] >> sh) & 1));
+    if (lane == 0) warp_ones[warp] = mine;
+    __syncthreads();
+    // ones of the warps before this one, and of all
+    const int c = lane < nwarp ? warp_ones[lane] : 0;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    int run = __shfl_sync(0xFFFFFFFFu, incl - c, warp);
+    const int Z = M - total;
+    for (int k = w0; k < w1; ++k) {
+      const int i = k * 32 + lane;
+      const int x = cur[i];
+      const int b = (x >> sh) & 1;
+      const unsigned bits = __ballot_sync(0xFFFFFFFFu, b);
+      if (lane == 0) rkl[k] = ((u64)run << 32) | bits;
+      if (l + 1 < LV) {
+        const int ob = run + __popc(bits & ((1u << lane) - 1u));
+        nxt[b ? Z + ob : i - ob] = (uint16_t)x;
+      }
+      run += __popc(bits);
+    }
+    if (tid == 0) {
+      rkl[nwm] = (u64)total << 32;
+      zeros[l] = Z;
     }
     __syncthreads();
-    if (warp == 0) {
-      int run = 0;
-      for (int w0 = 0; w0 < nwm; w0 += 32) {
-        const int w = w0 + lane;
-        const int c = (w < nwm) ? __popc(half[2 * w]) : 0;
-        int incl = c;
-        for (int s = 1; s < 32; s <<= 1) {
-          int t = __shfl_up_sync(0xFFFFFFFFu, incl, s);
-          if (lane >= s) incl += t;
-        }
-        if (w < nwm) half[2 * w + 1] = (uint32_t)(run + incl - c);
-        run += __shfl_sync(0xFFFFFFFFu, incl, 31);
-      }
-      if (lane == 0) {
-        rkl[nwm] = (u64)run << 32;
-        zeros[l] = M - run;
-      }
-    }
-    __syncthreads();
-    if (l + 1 < LV) {
-      const int Z = zeros[l];
-      for (int it = 0; it < nit; ++it) {
-        const int i = it * T + tid;
-        if (i < M) {
-          const int x = cur[i];
-          const u64 e = rkl[i >> 5];
-          const int ob = (int)(e >> 32) + __popc((uint32_t)e & ((1u << lane) - 1u));
-          nxt[((x >> sh) & 1) ? Z + ob : i - ob] = (uint16_t)x;
-        }
-      }
-      __syncthreads();
-      uint16_t* t = cur;
-      cur = nxt;
-      nxt = t;
-    }
+    uint16_t* t = cur;
+    cur = nxt;
+    nxt = t;
   }
 
   // 3. selections
@@ -1210,7 +1222,8 @@ size_t median_smem_bytes(int Kc, int key_bytes) {
   int M = 2 * Kc, LV = 0;
   while ((1 << LV) < M) ++LV;
   size_t ws = (size_t)M / 32 + 1;
-  return (size_t)key_bytes * M + (size_t)2 * M + (size_t)LV * ws * 8;
+  size_t rk = (size_t)LV * ws * 8, mr = (size_t)2 * M;  // the merged indices sit over rk
+  return (size_t)key_bytes * M + (size_t)2 * M + (rk > mr ? rk : mr);
 }
 
 void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
