@@ -822,8 +822,10 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
   // after the first iteration of a tracked run every chunk holds the sorted state of its
   // previous values
   const bool resort = d.base != nullptr && d.rs->iter > 0;
+  int b_next = d.item(kListR0, blockIdx.x);  // loaded beside the count (grid <= list length)
   for (int item = blockIdx.x; item < nitem; item += gridDim.x) {
-    const int b = d.item(kListR0, item);  // a chunk whose input changed
+    const int b = b_next;  // a chunk whose input changed
+    if (item + (int)gridDim.x < nitem) b_next = d.item(kListR0, item + gridDim.x);
     const long long base = (long long)b * pl.Kc;
     const int len = (int)((n - base) < pl.Kc ? (n - base) : pl.Kc);
     K k[E];
@@ -1202,9 +1204,12 @@ __global__ void __launch_bounds__(512, 2) k_median_wm(
   __shared__ int zeros[16];
   double relmax = 0.0;
   const int nitem = d.count(kListTile, pl.nch + 1);
+  int u_next = d.item(kListTile, blockIdx.x);  // loaded beside the count (grid <= list length)
   for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
     // a tile whose windows changed
-    double r = median_tile<K>(skey, srank, n, pl, o, d.item(kListTile, it), sm_raw, zeros);
+    const int u = u_next;
+    if (it + (int)gridDim.x < nitem) u_next = d.item(kListTile, it + gridDim.x);
+    double r = median_tile<K>(skey, srank, n, pl, o, u, sm_raw, zeros);
     relmax = r > relmax ? r : relmax;
     __syncthreads();  // before the next tile overwrites shared memory
   }
@@ -1358,8 +1363,11 @@ __global__ void k_chunk_prefix(SpecIn in, long long n, SmoothPlan pl,
   // chunks whose input changed (a chunk within in_radius of them is dirty)
   const int list = kListR0 + in_radius;
   const int nitem = d.count(list, pl.nch);
+  int b_next = d.item(list, blockIdx.x);  // loaded beside the count (grid <= list length)
   for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
-    chunk_prefix(in, n, pl, pre_lo, pre_hi, sig, uflow, x_out, d.item(list, it), warp_tot,
+    const int b = b_next;
+    if (it + (int)gridDim.x < nitem) b_next = d.item(list, it + gridDim.x);
+    chunk_prefix(in, n, pl, pre_lo, pre_hi, sig, uflow, x_out, b, warp_tot,
                  warp_max, any_uf);
     __syncthreads();
   }
@@ -1405,8 +1413,10 @@ __global__ void k_window_mean(const double* __restrict__ x, long long n, SmoothP
   // output chunks with a dirty chunk within out_radius
   const int list = kListR0 + out_radius;
   const int nitem = d.count(list, pl.nch);
+  int b_next = d.item(list, blockIdx.x);  // loaded beside the count (grid <= list length)
   for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
-    const long long b = d.item(list, it);
+    const long long b = b_next;
+    if (it + (int)gridDim.x < nitem) b_next = d.item(list, it + gridDim.x);
     const long long jend = (b + 1) * pl.Kc < n ? (b + 1) * pl.Kc : n;
     for (long long j = b * pl.Kc + threadIdx.x; j < jend; j += blockDim.x) {
       long long s = j - h > 0 ? j - h : 0;
