@@ -299,8 +299,9 @@ typedef struct {
   int32_t tdi2;
   int32_t grid_div;      /* persistent-grid divisor of every context (sub_set_grid_div) */
   int32_t max_contexts;  /* pooled contexts at most (0 = as many as the budget allows); at
-                          * the limit a job waits for an idle context that fits it rather
-                          * than allocating (allocation and freeing synchronise the GPU) */
+                          * the limit a job that a busy context could take waits for it,
+                          * and only a job that none could take replaces an idle context
+                          * (allocation and freeing synchronise the GPU) */
   double f_min, f_max;
   double rho_th, kappa;
 } sub_server_params;

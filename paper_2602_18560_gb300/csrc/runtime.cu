@@ -300,8 +300,13 @@ static Slot* acquire_slot(sub_server* s, const Job& j, int* fail_status) {
   }
   if (best) return best;
   if (s->p.max_contexts > 0 && (int)s->slots.size() >= s->p.max_contexts) {
-    // at the pool limit: an idle context that cannot take this job is replaced; with none
-    // idle the job waits
+    // At the pool limit a job that a busy context could take waits for it: replacing an
+    // idle context of another observation time would only move the shortage there, and
+    // building a context costs far more than one job.
+    for (Slot* sl : s->slots)
+      if (sl->busy && sl->ctx->p.T_obs == j.T_obs && sl->ctx->cap_N >= j.n) return nullptr;
+    // Otherwise an idle context that cannot take this job is replaced; with none idle the
+    // job waits.
     Slot* victim = nullptr;
     for (Slot* sl : s->slots)
       if (!sl->busy && (!victim || sl->last_use < victim->last_use)) victim = sl;

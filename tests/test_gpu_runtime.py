@@ -204,6 +204,31 @@ def test_server_prewarm_serves_without_creating_contexts():
         assert np.array_equal(m, m_s)
 
 
+def test_full_pool_waits_instead_of_rebuilding():
+    # a pool prewarmed to its limit for two observation times: bursts of one of them wait
+    # for its busy contexts instead of replacing the other's, so no context is ever built
+    js = jobs(16, seed=61)
+    Ts = sorted({j[0] for j in js})[:2]
+    js = [j for j in js if j[0] in Ts]
+    outs = []
+    with gbsub.Server(max_inflight=8, max_contexts=4, window=1000,
+                      estimator=gbsub.MEDIAN_MEAN) as srv:
+        for T in Ts:
+            srv.prewarm(T, max(len(j[1]) for j in js if j[0] == T), 2)
+        for i, (T, A, f, fdot) in enumerate(js):
+            nb = int(np.floor(1e-2 * T)) - int(np.ceil(1e-4 * T)) + 1
+            outs.append((np.zeros(nb), np.zeros(len(A), dtype=np.uint8)))
+            srv.submit(i, T, A, f, fdot, *outs[-1])
+        got = []
+        while len(got) < len(js):
+            got += srv.poll(timeout_ms=2000)
+        assert srv.info()["contexts_created"] == 2 * len(Ts)
+    for (T, A, f, fdot), (sg, m) in zip(js, outs):
+        st, sg_s, m_s = solo(T, A, f, fdot, window=1000, estimator=gbsub.MEDIAN_MEAN)
+        assert np.array_equal(sg.view(np.uint64), sg_s.view(np.uint64))
+        assert np.array_equal(m, m_s)
+
+
 def test_server_pool_stays_within_max_contexts():
     js = jobs(8, seed=51)
     outs = []
