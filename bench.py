@@ -139,6 +139,11 @@ class ClockSampler:
             self.fh.close()
 
     def summary(self):
+        if getattr(self, "_summary", None) is None:
+            self._summary = self._read()
+        return self._summary
+
+    def _read(self):
         if self.proc is None or not self.path:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
@@ -180,6 +185,28 @@ def algorithmic_bytes(kernel, N, nb, nlive, est):
     if kernel == "snr":       # kept candidates + two FP32 table reads per bin
         return 40 * nlive
     return 0
+
+
+def unit_bytes(kernel, Kc, est):
+    """Bytes one work item of a loop kernel must move: a chunk of Kc bins, or a median tile
+    (Kc outputs from the keys and ranks of two chunks)."""
+    if kernel == "sort":      # spectrum words + S_instr -> sorted keys, ranks
+        return (32 + 8 + 8 + 2) * Kc
+    if kernel == "median":    # keys and ranks of two chunks -> Kc medians (+ inv_f as S_gal)
+        return 2 * 10 * Kc + 8 * Kc + (4 * Kc if est == 1 else 0)
+    if kernel == "prefix":    # input (spectrum words + S, or the median) -> prefix sums
+        return ((40 + 8) * Kc if est == 0 else 8 * Kc) + 16 * Kc
+    if kernel == "mean":      # two prefix sums per output -> S_gal + inv_f
+        return (16 + 12) * Kc
+    return 0
+
+
+def loop_units(kernel, work, est):
+    """Work items a loop kernel was handed over a run (sub_get_work), None for the others."""
+    lists = {2: {"sort": "changed", "median": "tiles", "prefix": "within1", "mean": "within2"},
+             1: {"sort": "changed", "median": "tiles"},
+             0: {"prefix": "changed", "mean": "within1"}}[est]
+    return work[lists[kernel]] if kernel in lists else None
 
 
 def cpu_oracle_sample(A, f, fdot, T, est, W, iters_hint):
@@ -334,40 +361,74 @@ def main():
             a = acc.setdefault(k, [0.0, 0])
             a[0] += t
             a[1] += n
-    kernels = {k: {"ms_per_run": v[0] / prof_runs, "launches_per_run": v[1] / prof_runs}
-               for k, v in acc.items() if v[1] > 0}
-    dom = max(kernels, key=lambda k: kernels[k]["ms_per_run"])
+    work = sub.work()  # work items of the (deterministic) profiling runs
     nb = st.n_bins
-    per_launch_ms = kernels[dom]["ms_per_run"] / kernels[dom]["launches_per_run"]
     nlive = st.n_live
-    algo = algorithmic_bytes(dom, N, nb, nlive, est)
+    Kc = 32 * ((args.window + 31) // 32)
+    kernels = {}
+    for k, (t, n) in acc.items():
+        if n == 0:
+            continue
+        ms_run, launches = t / prof_runs, n / prof_runs
+        units = loop_units(k, work, est)
+        if units is not None:
+            bytes_run = units * unit_bytes(k, Kc, est)
+        elif k == "snr":
+            bytes_run = algorithmic_bytes(k, N, nb, nlive, est) * launches
+        else:
+            bytes_run = algorithmic_bytes(k, N, nb, nlive, est)
+        kernels[k] = {"ms_per_run": ms_run, "launches_per_run": launches,
+                      "units_per_run": units, "algorithmic_bytes_per_run": bytes_run,
+                      "GB/s": bytes_run / (ms_run * 1e-3) / 1e9}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_run"])
     hbm, hbm_kind = peaks()
-    achieved = algo / (per_launch_ms * 1e-3) / 1e9
-    # the catalog pass separately (timed inside the graph of the last timed step)
-    pre_algo = algorithmic_bytes("prepass", N, nb, nlive, est)
-    per_iter = sum(algorithmic_bytes(k, N, nb, nlive, est)
-                   for k in kernels if k not in ("prepass", "control"))
-    whole_bytes = pre_algo + st.iterations * per_iter + N
-    traffic = None
+    tr = {}
     prof_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof_path):
         try:
             with open(prof_path) as fh:
-                tr = json.load(fh)
-            ent = tr.get(w.name, {}).get(dom)
-            if ent and ent.get("kernel_source_sha256") == source_digest():
-                traffic = ent["dram_bytes_per_launch"]
+                tr_all = json.load(fh).get(w.name, {})
+            tr = {k: v for k, v in tr_all.items() if v.get("kernel_source_sha256") == source_digest()}
         except Exception:
-            traffic = None
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "peak_kind": hbm_kind,
-                "traffic": traffic, "algorithmic_bytes_per_launch": algo,
-                "ms_per_launch": per_launch_ms,
-                "catalog_pass": {"ms": pre_ms, "GB/s": pre_algo / (pre_ms * 1e-3) / 1e9,
-                                 "frac": pre_algo / (pre_ms * 1e-3) / 1e9 / hbm},
-                "whole_run": {"algorithmic_bytes": whole_bytes,
-                              "GB/s": whole_bytes / (ms * 1e-3) / 1e9,
-                              "frac": whole_bytes / (ms * 1e-3) / 1e9 / hbm}}
+            tr = {}
+    kd = kernels[dom]
+    per_launch_ms = kd["ms_per_run"] / kd["launches_per_run"]
+    bytes_launch = kd["algorithmic_bytes_per_run"] / kd["launches_per_run"]
+    # DRAM traffic of the first (full) launch from ncu, scaled by the units of an average launch
+    traffic = None
+    if dom in tr:
+        t0 = tr[dom]["dram_bytes_per_launch"]
+        u0 = tr[dom].get("units_first_launch")
+        traffic = (t0 * (kd["units_per_run"] / kd["launches_per_run"]) / u0
+                   if (u0 and kd["units_per_run"] is not None) else t0)
+    if dom in ("prepass", "snr", "prefix", "mean") or dom not in tr:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": bytes_launch / (per_launch_ms * 1e-3) / 1e9,
+                    "peak": hbm, "unit": "GB/s", "peak_kind": hbm_kind}
+        roofline["frac"] = roofline["achieved"] / hbm
+    else:
+        # sort and median: shared-memory and integer work on an L2-resident spectrum, bound by
+        # instruction issue (one warp instruction per scheduler per clock)
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        fmax = clk.summary().get("sm_max_mhz") or 2070.0
+        peak_issue = nsm * 4 * fmax * 1e6 / 1e9
+        inst_launch = tr[dom]["warp_inst_per_unit"] * kd["units_per_run"] / kd["launches_per_run"]
+        roofline = {"bound": "alu", "kernel": dom,
+                    "achieved": inst_launch / (per_launch_ms * 1e-3) / 1e9,
+                    "peak": peak_issue, "unit": "G warp-instructions/s",
+                    "peak_kind": "derived: %d SMs x 4 schedulers x %.0f MHz" % (nsm, fmax),
+                    "hbm_view": {"GB/s": bytes_launch / (per_launch_ms * 1e-3) / 1e9,
+                                 "frac": bytes_launch / (per_launch_ms * 1e-3) / 1e9 / hbm}}
+        roofline["frac"] = roofline["achieved"] / peak_issue
+    pre_algo = algorithmic_bytes("prepass", N, nb, nlive, est)
+    whole_bytes = sum(v["algorithmic_bytes_per_run"] for v in kernels.values()) + N
+    roofline.update({"traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
+                     "ms_per_launch": per_launch_ms,
+                     "catalog_pass": {"ms": pre_ms, "GB/s": pre_algo / (pre_ms * 1e-3) / 1e9,
+                                      "frac": pre_algo / (pre_ms * 1e-3) / 1e9 / hbm,
+                                      "traffic": tr.get("prepass", {}).get("dram_bytes_per_launch")},
+                     "whole_run": {"algorithmic_bytes": whole_bytes,
+                                   "GB/s": whole_bytes / (ms * 1e-3) / 1e9,
+                                   "frac": whole_bytes / (ms * 1e-3) / 1e9 / hbm}})
 
     # ---------------------------------------------------------------- end to end (host buffers)
     e2e = None

@@ -193,6 +193,15 @@ int sub_get_tables(sub_ctx* ctx, double* S, double* R, int64_t n, int where);
  * Any pointer may be null. */
 int sub_get_timing(sub_ctx* ctx, float* prepass_ms, float* loop_ms, float* total_ms);
 
+/* Work items the loop kernels of the last sub_run were handed, summed over its
+ * iterations: work[0] chunks (Kc bins each) whose values changed, work[1] chunks within
+ * one chunk of such a chunk, work[2] within two, work[3] median tiles (Kc outputs each).
+ * Which kernel takes which list depends on the estimator: median-then-mean sorts 0,
+ * selects medians on 3, sums prefixes on 1 and window means on 2; median sorts 0 and
+ * selects on 3; mean sums prefixes on 0 and window means on 1.  Writes min(n, 4) entries.
+ * Synchronises. */
+int sub_get_work(sub_ctx* ctx, int64_t* work, int32_t n);
+
 /* Kernels of the path, in the order of SUB_K_* below. */
 #define SUB_K_PREPASS 0   /* catalog pass: sweep, deposit, rho_0, candidates  */
 #define SUB_K_SORT 1      /* per-chunk sort (median)                           */

@@ -405,7 +405,7 @@ static cudaError_t enqueue_pre(sub_ctx* c, cudaStream_t st) {
   // the first iteration reads set 0: every chunk is new
   if ((e = cudaMemsetAsync(c->dirty, 1, (size_t)c->plan.nch, st))) return e;
   if ((e = cudaMemsetAsync(c->dirty + c->plan.nch, 0, (size_t)c->plan.nch, st))) return e;
-  launch_build_lists(dirty_of(c, true), c->lists, c->list_counts, st);
+  launch_build_lists(dirty_of(c, true), c->lists, c->list_counts, c->rs, st);
   if ((e = cudaMemsetAsync(c->new_hist, 0, (size_t)c->p.max_iter * 4, st))) return e;
   // sized by the capacity, not the catalog: the captured graph serves every catalog that fits
   if ((e = cudaMemsetAsync(c->resolved, 0, (size_t)c->cap_N, st))) return e;
@@ -747,6 +747,15 @@ extern "C" int sub_get_timing(sub_ctx* c, float* prepass_ms, float* loop_ms, flo
   if (prepass_ms) *prepass_ms = a;
   if (loop_ms) *loop_ms = b;
   if (total_ms) *total_ms = a + b;
+  return SUB_OK;
+}
+
+extern "C" int sub_get_work(sub_ctx* c, int64_t* work, int32_t n) {
+  if (!c || (n > 0 && !work)) return SUB_EINVAL;
+  if (!c->ran) { set_err(c, "no run yet"); return SUB_ESTATE; }
+  CU(cudaMemcpyAsync(c->h_rs, c->rs, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream), c);
+  CU(cudaStreamSynchronize(c->stream), c);
+  for (int i = 0; i < n && i < 4; ++i) work[i] = (int64_t)c->h_rs->work[i];
   return SUB_OK;
 }
 

@@ -1699,12 +1699,14 @@ __device__ void build_lists_cta(const unsigned char* __restrict__ cur, int nch,
   if (threadIdx.x < kNumLists) counts[threadIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void k_build_lists(Dirty d, int* lists, int* counts) {
+__global__ void k_build_lists(Dirty d, int* lists, int* counts, RunState* rs) {
   build_lists_cta(d.base + (size_t)(d.rs->iter & 1) * d.nch, d.nch, lists, counts);
+  __syncthreads();
+  if (threadIdx.x < kNumLists) rs->work[threadIdx.x] += (unsigned long long)counts[threadIdx.x];
 }
 
-void launch_build_lists(Dirty d, int* lists, int* counts, cudaStream_t st) {
-  k_build_lists<<<1, 1024, 0, st>>>(d, lists, counts);
+void launch_build_lists(Dirty d, int* lists, int* counts, RunState* rs, cudaStream_t st) {
+  k_build_lists<<<1, 1024, 0, st>>>(d, lists, counts, rs);
 }
 
 __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist,
@@ -1742,6 +1744,8 @@ __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist
   rs->count_new = 0ull;
   rs->relchg_bits = 0ull;
   if (!go) rs->stopped = 1;
+  if (go && dirty)  // the lists just built go to the next iteration's kernels
+    for (int i = 0; i < kNumLists; ++i) rs->work[i] += (unsigned long long)counts[i];
   if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, go);
 }
 

@@ -34,6 +34,7 @@ struct RunState {
   unsigned long long max_p_bits;    // scratch maximum (estimate on a given spectrum)
   unsigned long long relchg_bits;   // max relative change of S_n (conv_rtol)
   unsigned long long next_tile;  // catalog tiles handed out so far (catalog pass)
+  unsigned long long work[4];    // work-list items the loop kernels were handed (by list)
   unsigned err;
   unsigned pad;
 };
@@ -206,7 +207,7 @@ void launch_snr_resolve(Cands cd, long long ncap, const Grid& g, const Tables& t
                         Dirty d, int Kc, int sg_radius, int nsm, cudaStream_t st);
 
 // Work lists of the set the next iteration reads (set rs->iter & 1).
-void launch_build_lists(Dirty d, int* lists, int* counts, cudaStream_t st);
+void launch_build_lists(Dirty d, int* lists, int* counts, RunState* rs, cudaStream_t st);
 
 // Loop control; it also clears the dirty set the finished iteration read and builds the
 // work lists of the next one.

@@ -90,7 +90,8 @@ _lib = None
 _lock = threading.Lock()
 EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_run", "sub_get_stats",
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
-           "sub_get_tables", "sub_get_timing", "sub_profile", "sub_device_bytes", "sub_destroy",
+           "sub_get_tables", "sub_get_timing", "sub_get_work", "sub_profile", "sub_device_bytes",
+           "sub_destroy",
            "sub_last_error", "sub_running_mean_noalloc", "sub_get_power", "sub_batch_create",
            "sub_batch_run", "sub_batch_last_ms", "sub_batch_last_error", "sub_batch_destroy",
            "sub_set_grid_div", "sub_test_hooks", "sub_server_params_default", "sub_server_create",
@@ -130,6 +131,7 @@ def lib(build_if_missing: bool = True):
             "sub_get_tables": (i32, [P, P, P, i64, i32]),
             "sub_get_power": (i32, [P, P, i64, i32]),
             "sub_get_timing": (i32, [P, P, P, P]),
+            "sub_get_work": (i32, [P, P, i32]),
             "sub_profile": (i32, [P, P, P, ctypes.POINTER(sub_stats)]),
             "sub_device_bytes": (i64, [P]),
             "sub_destroy": (None, [P]),
@@ -298,6 +300,14 @@ def sub_get_tables(ctx):
     return S, R
 
 
+def sub_get_work(ctx):
+    """Work-list items the loop kernels of the last run were handed, by list: chunks whose
+    values changed, chunks within one and within two of them, median tiles."""
+    w = (ctypes.c_int64 * 4)()
+    _check(ctx, lib().sub_get_work(ctx, w, 4))
+    return {"changed": w[0], "within1": w[1], "within2": w[2], "tiles": w[3]}
+
+
 def sub_get_timing(ctx):
     """(prepass_ms, loop_ms, total_ms) of the last run, from events inside its graph."""
     a, b, t = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
@@ -360,6 +370,9 @@ class Subtraction:
 
     def timing(self):
         return sub_get_timing(self.ctx)
+
+    def work(self):
+        return sub_get_work(self.ctx)
 
     def profile(self):
         return sub_profile(self.ctx)

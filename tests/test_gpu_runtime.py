@@ -271,3 +271,21 @@ def test_mapped_catalog_equals_a_copied_one():
         s.load(*pins, mapped=True)
         same((s.run(), s.spectrum(), s.resolved()),
              solo(T, A, f, fdot, precision=gbsub.MIXED, **kw))
+
+
+def test_work_counts_follow_the_dirty_chunks():
+    # the loop kernels' work items per run: every chunk in the first iteration, then the
+    # lists nest (changed chunks within their one- and two-chunk neighbourhoods), each changed
+    # chunk gives at most two median tiles, and a repeated run repeats them exactly
+    T, A, f, fdot = jobs(1, seed=71, n_lo=2e5, n_hi=2e5)[0]
+    with gbsub.Subtraction(T_obs=T, window=1000, estimator=gbsub.MEDIAN_MEAN) as s:
+        s.load(A, f, fdot)
+        st = s.run()
+        w = s.work()
+        nch = -(-st.n_bins // 1024)
+        assert st.iterations >= 2
+        assert w["changed"] >= nch and w["tiles"] >= nch + 1
+        assert w["changed"] <= w["within1"] <= w["within2"] <= nch * (st.iterations + 1)
+        assert w["changed"] <= w["tiles"] <= 2 * w["changed"]
+        s.run()
+        assert s.work() == w
