@@ -7,9 +7,9 @@ It shares no code with the CUDA path.  The arithmetic lives in ``oracle.cpp``
 module compiles it with g++ and exposes it through ctypes with numpy arrays.
 
 Parity status per function (what pins it is in the test suite):
-  tables, pieces, SNR, deposition, estimators, loop: pinned (closed forms,
-  quadrature of the waveform average, brute force, library special cases,
-  invariants).  The paper's Table III counts are not reproducible here
+  tables, pieces, SNR, deposition, estimators, loop, coarse-graining: pinned
+  (closed forms, quadrature of the waveform average, brute force, library special
+  cases, invariants).  The paper's Table III counts are not reproducible here
   (parity unpinned for them: different catalog and waveform model).
 """
 from __future__ import annotations
@@ -102,6 +102,8 @@ def lib():
             L.orc_power.argtypes = [d, P, P, i64, P]
             L.orc_snr2.restype = None
             L.orc_snr2.argtypes = [d, i64, i64, P, P, P, P, P, P, i64, P]
+            L.orc_coarse_grain.restype = None
+            L.orc_coarse_grain.argtypes = [d, d, d, i64, i64, P, i32, P, P, P]
             L.orc_run.restype = i32
             L.orc_run.argtypes = [ctypes.POINTER(Params), P, P, P, i64, P, P,
                                   ctypes.POINTER(Stats), P, i64]
@@ -193,6 +195,16 @@ def power(T, R, D):
     P = np.empty_like(D)
     lib().orc_power(T, _p(R), _p(D), D.size, _p(P))
     return P
+
+
+def coarse_grain(T, f_min, f_max, k_lo, x, nbins=100):
+    """(S_k, f_k, N_k): bin averages of the per-bin series x over nbins log-spaced bins."""
+    x = _f64(x)
+    S = np.empty(nbins)
+    fk = np.empty(nbins)
+    c = np.empty(nbins, dtype=np.int64)
+    lib().orc_coarse_grain(T, f_min, f_max, k_lo, x.size, _p(x), nbins, _p(S), _p(fk), _p(c))
+    return S, fk, c
 
 
 def snr2(T, k_lo, n, S_instr, R, S_gal, A, f, fdot):

@@ -403,4 +403,32 @@ int orc_run(const orc_params* prm, const double* A, const double* f, const doubl
   return converged ? 0 : 1;
 }
 
+// Coarse-graining (Sec. "Coarse-graining of the data": the bin averages of the spectrum
+// and of the frequencies).  The band [f_min, f_max] is split into nb logarithmically spaced
+// bins with edges e_k = 10^(log10 f_min + k (log10 f_max - log10 f_min) / nb).  Reading:
+// bin k holds the grid frequencies f_i = (k_lo + i) / T with e_k <= f_i < e_{k+1}; the
+// first bin also takes the grid frequencies below e_1, the last those from e_{nb-1} on.
+// Each bin averages x and f over its frequencies; an empty bin gets NaN and a zero count.
+void orc_coarse_grain(double T, double f_min, double f_max, int64_t k_lo, int64_t n,
+                      const double* x, int32_t nb, double* S_out, double* f_out, int64_t* cnt) {
+  const double l0 = std::log10(f_min), l1 = std::log10(f_max);
+  std::vector<double> edge(nb + 1);
+  for (int32_t k = 0; k <= nb; ++k) edge[k] = std::pow(10.0, l0 + (double)k * (l1 - l0) / (double)nb);
+  std::vector<double> sx(nb, 0.0), sf(nb, 0.0);
+  std::vector<int64_t> c(nb, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    const double f = (double)(k_lo + i) / T;
+    int32_t k = 0;
+    while (k + 1 < nb && f >= edge[k + 1]) ++k;  // the highest bin whose lower edge is <= f
+    sx[k] += x[i];
+    sf[k] += f;
+    c[k] += 1;
+  }
+  for (int32_t k = 0; k < nb; ++k) {
+    cnt[k] = c[k];
+    S_out[k] = c[k] ? sx[k] / (double)c[k] : std::nan("");
+    f_out[k] = c[k] ? sf[k] / (double)c[k] : std::nan("");
+  }
+}
+
 }  // extern "C"
