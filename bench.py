@@ -430,6 +430,19 @@ def main():
                                    "GB/s": whole_bytes / (ms * 1e-3) / 1e9,
                                    "frac": whole_bytes / (ms * 1e-3) / 1e9 / hbm}})
 
+    # ---------------------------------------------------------------- coarse graining of S_gal
+    cg = None
+    try:
+        sub.coarse_grain()
+        t0 = time.perf_counter()
+        for _ in range(20):
+            Sk, fk, ck = sub.coarse_grain()
+        cg = {"nbins": 100, "ms_per_call": (time.perf_counter() - t0) / 20 * 1e3,
+              "api": "sub_coarse_grain(S_gal of the run, 100 log bins) -> host",
+              "empty_bins": int(np.sum(ck == 0))}
+    except Exception as exc:  # reported, not fatal: the subtraction line stands on its own
+        cg = {"error": str(exc)}
+
     # ---------------------------------------------------------------- end to end (host buffers)
     e2e = None
     if not args.no_e2e:
@@ -497,6 +510,7 @@ def main():
                   "resolved_per_iteration": [int(x) for x in sub.history()],
                   "prepass_ms": pre_ms, "loop_ms": loop_ms},
         "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "coarse_grain": cg,
         "gpu_launches": launches, "parity": parity,
     }
     line["clocks"] = clk.summary()

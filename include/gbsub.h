@@ -193,6 +193,22 @@ int sub_get_tables(sub_ctx* ctx, double* S, double* R, int64_t n, int where);
  * Any pointer may be null. */
 int sub_get_timing(sub_ctx* ctx, float* prepass_ms, float* loop_ms, float* total_ms);
 
+/* Coarse graining (Sec. "Coarse-graining of the data", the bin-averaged spectrum and the
+ * bin-averaged frequencies): the band [f_min, f_max] is split into nbins logarithmically
+ * spaced bins with edges e_k = 10^(log10 f_min + k (log10 f_max - log10 f_min) / nbins); a
+ * grid frequency f_i = (k_lo + i) / T_obs belongs to the highest bin whose lower edge is
+ * at most f_i (bin 0 also takes the grid frequencies below e_1).
+ *   x         : n_bins values on the grid (host or device per `where`), or null for the
+ *               S_gal of the last sub_run (SUB_ESTATE before any run)
+ *   add_instr : nonzero to average S_instr + x (the noise PSD S_n) instead of x
+ *   nbins     : 1 .. 2^20 (the paper: 100)
+ *   S_out[k]  : mean of the series over bin k;  f_out[k]: mean frequency of bin k;
+ *   count_out[k]: N_k, the grid frequencies in bin k.  An empty bin gives NaN means.
+ *               Any output may be null; all are nbins long, at `where`.
+ * Synchronises.  Errors: SUB_EINVAL, SUB_ESTATE, SUB_ENOMEM, SUB_EBUDGET, SUB_ECUDA. */
+int sub_coarse_grain(sub_ctx* ctx, const double* x, int32_t add_instr, int32_t nbins,
+                     double* S_out, double* f_out, int64_t* count_out, int where);
+
 /* Work items the loop kernels of the last sub_run were handed, summed over its
  * iterations: work[0] chunks (Kc bins each) whose values changed, work[1] chunks within
  * one chunk of such a chunk, work[2] within two, work[3] median tiles (Kc outputs each).

@@ -713,6 +713,67 @@ extern "C" int sub_estimate(sub_ctx* c, const double* P, double* out, int64_t n,
   return SUB_OK;
 }
 
+// First grid index of every coarse bin (Sec. "Coarse-graining of the data"): edges
+// e_k = 10^(log10 f_min + k (log10 f_max - log10 f_min) / nb); a grid frequency
+// f_i = (k_lo + i) / T belongs to the highest bin whose lower edge is <= f_i (bin 0 takes
+// everything below e_1).  Each boundary is settled by the same FP64 comparison f_i >= e_k.
+static void coarse_bounds(double T, double f_min, double f_max, int64_t k_lo, int64_t n, int nb,
+                          std::vector<long long>& idx) {
+  const double l0 = std::log10(f_min), l1 = std::log10(f_max);
+  idx.assign((size_t)nb + 1, 0);
+  idx[nb] = n;
+  for (int k = 1; k < nb; ++k) {
+    const double e = std::pow(10.0, l0 + (double)k * (l1 - l0) / (double)nb);
+    long long i = (long long)std::ceil(e * T) - k_lo;
+    if (i < 0) i = 0;
+    if (i > n) i = n;
+    while (i > 0 && (double)(k_lo + i - 1) / T >= e) --i;
+    while (i < n && (double)(k_lo + i) / T < e) ++i;
+    idx[k] = i < idx[k - 1] ? idx[k - 1] : i;
+  }
+}
+
+extern "C" int sub_coarse_grain(sub_ctx* c, const double* x, int32_t add_instr, int32_t nbins,
+                                double* S_out, double* f_out, int64_t* count_out, int where) {
+  if (!c) return SUB_EINVAL;
+  if (nbins < 1 || nbins > (1 << 20)) { set_err(c, "nbins must be in 1 .. 2^20"); return SUB_EINVAL; }
+  if (where != SUB_HOST && where != SUB_DEVICE) { set_err(c, "bad where"); return SUB_EINVAL; }
+  if (!x && !c->ran) { set_err(c, "no run yet (and no series given)"); return SUB_ESTATE; }
+  const int64_t n = c->grid.nb;
+  cudaStream_t st = c->stream;
+  if (nbins > c->cg_cap) {
+    dfree(c, c->cg);
+    c->cg = nullptr;
+    c->cg_cap = 0;
+    int rc = dalloc(c, (void**)&c->cg, (size_t)nbins * 32 + 8);
+    if (rc) return rc;
+    c->cg_cap = nbins;
+  }
+  double* dS = c->cg;
+  double* df = dS + c->cg_cap;
+  long long* dc = (long long*)(df + c->cg_cap);
+  long long* de = dc + c->cg_cap;
+  std::vector<long long> idx;
+  coarse_bounds(c->p.T_obs, c->p.f_min, c->p.f_max, c->grid.k_lo, n, nbins, idx);
+  CU(cudaMemcpyAsync(de, idx.data(), idx.size() * 8, cudaMemcpyHostToDevice, st), c);
+  const double* in = c->Sg;
+  if (x && where == SUB_DEVICE) {
+    in = x;
+  } else if (x) {
+    CU(cudaMemcpyAsync(c->estimate_in, x, (size_t)n * 8, cudaMemcpyHostToDevice, st), c);
+    in = c->estimate_in;
+  }
+  launch_coarse_grain(in, add_instr ? c->S : nullptr, de, nbins, c->grid.k_lo, c->p.T_obs, dS, df,
+                      dc, st);
+  CU(cudaGetLastError(), c);
+  const cudaMemcpyKind k = where == SUB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (S_out) CU(cudaMemcpyAsync(S_out, dS, (size_t)nbins * 8, k, st), c);
+  if (f_out) CU(cudaMemcpyAsync(f_out, df, (size_t)nbins * 8, k, st), c);
+  if (count_out) CU(cudaMemcpyAsync(count_out, dc, (size_t)nbins * 8, k, st), c);
+  CU(cudaStreamSynchronize(st), c);
+  return SUB_OK;
+}
+
 extern "C" int sub_get_power(sub_ctx* c, double* P, int64_t n, int where) {
   if (!c) return SUB_EINVAL;
   if (n != c->grid.nb || !P) { set_err(c, "n must equal n_bins"); return SUB_EINVAL; }

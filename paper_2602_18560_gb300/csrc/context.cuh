@@ -42,6 +42,8 @@ struct sub_ctx {
   AccReplicas rep = {nullptr, 0};     // private copies of the first bins (catalog pass)
   double *P = nullptr, *M = nullptr, *Sg = nullptr;
   double* estimate_in = nullptr;  // input copy of sub_estimate
+  double* cg = nullptr;           // coarse graining: [S | f | counts | edges] of cg_cap bins
+  int cg_cap = 0;
   float* inv_f = nullptr;
   int* sig = nullptr;
   unsigned char* dirty = nullptr;  // two sets of one byte per chunk

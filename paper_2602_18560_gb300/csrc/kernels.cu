@@ -1674,6 +1674,44 @@ void launch_snr_resolve(Cands cd, long long ncap, const Grid& g, const Tables& t
                                    sg_radius);
 }
 
+// ============================================================================ coarse graining
+// Bin averages of a per-bin series over log-spaced frequency bins (the coarse-grained
+// spectrum and frequencies).  Bin k covers the grid indices [edge[k], edge[k+1]); one CTA
+// per bin sums its values in a fixed order (no atomics), so the result is reproducible.
+// The mean frequency of indices a .. b-1 is (2 k_lo + a + b - 1) / (2 T) exactly.
+__global__ void __launch_bounds__(256) k_coarse_grain(const double* __restrict__ x,
+                                                      const double* __restrict__ S,
+                                                      const long long* __restrict__ edge,
+                                                      long long k_lo, double T,
+                                                      double* __restrict__ S_out,
+                                                      double* __restrict__ f_out,
+                                                      long long* __restrict__ cnt_out) {
+  __shared__ double part[8];
+  const int k = blockIdx.x;
+  const long long a = edge[k], b = edge[k + 1];
+  double s = 0.0;
+  for (long long i = a + threadIdx.x; i < b; i += blockDim.x)
+    s = __dadd_rn(s, S ? __dadd_rn(S[i], x[i]) : x[i]);
+  for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xFFFFFFFFu, s, o));
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = __dadd_rn(t, part[w]);
+    const long long c = b - a;
+    cnt_out[k] = c;
+    S_out[k] = c > 0 ? __ddiv_rn(t, (double)c) : __longlong_as_double(0x7FF8000000000000ll);
+    f_out[k] = c > 0 ? __ddiv_rn((double)(2 * k_lo + a + b - 1), __dmul_rn(2.0, T))
+                     : __longlong_as_double(0x7FF8000000000000ll);
+  }
+}
+
+void launch_coarse_grain(const double* x, const double* S, const long long* edge, int nbins,
+                         long long k_lo, double T, double* S_out, double* f_out,
+                         long long* cnt_out, cudaStream_t st) {
+  k_coarse_grain<<<nbins, 256, 0, st>>>(x, S, edge, k_lo, T, S_out, f_out, cnt_out);
+}
+
 // ============================================================================ loop control
 
 // Work lists from the dirty set `cur` (one CTA).  Their order depends on the atomics,

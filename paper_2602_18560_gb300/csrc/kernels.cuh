@@ -169,6 +169,12 @@ void launch_prepass(const CatalogRef* cat, long long cap, const Grid& g, const T
 // *p = v on the stream.
 void launch_set_catalog(CatalogRef* p, const CatalogRef& v, cudaStream_t st);
 
+// Coarse graining: for every bin k of [edge[k], edge[k+1]) (nbins + 1 edges on the device),
+// the mean of x (of S + x when S is given), the mean frequency (k_lo + i) / T and the count.
+void launch_coarse_grain(const double* x, const double* S, const long long* edge, int nbins,
+                         long long k_lo, double T, double* S_out, double* f_out,
+                         long long* cnt_out, cudaStream_t st);
+
 // P[j] = S_j Q_j 2^-96 for every bin.
 void launch_power_out(const unsigned long long* acc, const double* S, long long n, double* P,
                       cudaStream_t st);

@@ -90,7 +90,8 @@ _lib = None
 _lock = threading.Lock()
 EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_run", "sub_get_stats",
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
-           "sub_get_tables", "sub_get_timing", "sub_get_work", "sub_profile", "sub_device_bytes",
+           "sub_get_tables", "sub_get_timing", "sub_get_work", "sub_coarse_grain", "sub_profile",
+           "sub_device_bytes",
            "sub_destroy",
            "sub_last_error", "sub_running_mean_noalloc", "sub_get_power", "sub_batch_create",
            "sub_batch_run", "sub_batch_last_ms", "sub_batch_last_error", "sub_batch_destroy",
@@ -132,6 +133,7 @@ def lib(build_if_missing: bool = True):
             "sub_get_power": (i32, [P, P, i64, i32]),
             "sub_get_timing": (i32, [P, P, P, P]),
             "sub_get_work": (i32, [P, P, i32]),
+            "sub_coarse_grain": (i32, [P, P, i32, i32, P, P, P, i32]),
             "sub_profile": (i32, [P, P, P, ctypes.POINTER(sub_stats)]),
             "sub_device_bytes": (i64, [P]),
             "sub_destroy": (None, [P]),
@@ -300,6 +302,30 @@ def sub_get_tables(ctx):
     return S, R
 
 
+def sub_coarse_grain(ctx, x=None, nbins=100, add_instr=False):
+    """(S_k, f_k, N_k): bin averages over nbins log-spaced bins of x (n_bins values, host or
+    device), or of the last run's S_gal when x is None; of S_instr + x with add_instr."""
+    where = HOST
+    px = None
+    if x is not None:
+        px, where, n = _ptr(x, np.float64)
+        nb, _ = n_bins_of(ctx)
+        if n != nb:
+            raise ValueError("x must hold n_bins (%d) values" % nb)
+    if where == DEVICE:
+        import torch
+        dev = x.device
+        S = torch.empty(nbins, dtype=torch.float64, device=dev)
+        f = torch.empty(nbins, dtype=torch.float64, device=dev)
+        c = torch.empty(nbins, dtype=torch.int64, device=dev)
+        ptrs = [ctypes.c_void_p(t.data_ptr()) for t in (S, f, c)]
+    else:
+        S, f, c = np.empty(nbins), np.empty(nbins), np.empty(nbins, dtype=np.int64)
+        ptrs = [t.ctypes.data_as(ctypes.c_void_p) for t in (S, f, c)]
+    _check(ctx, lib().sub_coarse_grain(ctx, px, int(bool(add_instr)), nbins, *ptrs, where))
+    return S, f, c
+
+
 def sub_get_work(ctx):
     """Work-list items the loop kernels of the last run were handed, by list: chunks whose
     values changed, chunks within one and within two of them, median tiles."""
@@ -373,6 +399,9 @@ class Subtraction:
 
     def work(self):
         return sub_get_work(self.ctx)
+
+    def coarse_grain(self, x=None, nbins=100, add_instr=False):
+        return sub_coarse_grain(self.ctx, x, nbins, add_instr)
 
     def profile(self):
         return sub_profile(self.ctx)
