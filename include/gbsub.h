@@ -139,6 +139,28 @@ int sub_create(const sub_params* p, void* stream, sub_ctx** out);
 int sub_load_catalog(sub_ctx* ctx, const double* A, const double* f, const double* fdot,
                      int64_t n, int where);
 
+/* Generate a catalog on the device instead of loading one (the synthetic population model:
+ * f from a power law p(f) ~ f^-gamma on [0.1, 10] mHz, A = 1e-23 X (f / 1 mHz)^(2/3) with
+ * X ~ Gamma(shape, 1), fdot the GW-driven chirp of Sec. II.A with Mc ~ U(0.2, 0.8) Msun).
+ * Source s is a pure function of (seed, s): a counter-based Philox4x32-10 stream, and
+ * single-precision arithmetic of basic operations only, so the same catalog comes out on
+ * any machine; it is returned in FP64.
+ *   n     : sources (0 .. 2^40);  seed: any 64-bit value
+ *   gamma : power-law index, -8 .. 10;  shape: Gamma shape of the amplitude factor, 1 .. 1e6
+ *   fused : nonzero: nothing is stored; every sub_run generates each source inside the
+ *           catalog pass, so no catalog crosses the host link or sits in device memory;
+ *           zero: the catalog is generated once into the context's catalog arrays and runs
+ *           read it like a loaded catalog.
+ * Replaces any previous catalog.  Errors: SUB_EINVAL, SUB_ENOMEM, SUB_EBUDGET, SUB_ECUDA. */
+int sub_load_generated(sub_ctx* ctx, int64_t n, uint64_t seed, double gamma, double shape,
+                       int32_t fused);
+
+/* Sources start .. start+n-1 of the current catalog into A, f, fdot (n doubles each, at
+ * `where`): copied from where the catalog lives, or generated again for a fused generated
+ * catalog.  Synchronises.  Errors: SUB_EINVAL, SUB_ESTATE (no catalog), SUB_ECUDA. */
+int sub_get_catalog(sub_ctx* ctx, double* A, double* f, double* fdot, int64_t start, int64_t n,
+                    int where);
+
 /* Run the subtraction of App. D on the loaded catalog:
  *   rho_0 against S_instr; candidates rho_0 >= kappa rho_th; then repeat
  *   { S_gal = estimator of the residual power; rho against S_instr + S_gal;

@@ -335,6 +335,70 @@ extern "C" int sub_load_catalog(sub_ctx* c, const double* A, const double* f, co
   CU(cudaGetLastError(), c);
   c->N = n;
   c->ran = false;
+  c->cat_kind = where == SUB_HOST_MAPPED ? kCatHostMapped : kCatDevice;
+  c->cat_host[0] = A;
+  c->cat_host[1] = f;
+  c->cat_host[2] = fdot;
+  return SUB_OK;
+}
+
+extern "C" int sub_load_generated(sub_ctx* c, int64_t n, uint64_t seed, double gamma,
+                                  double shape, int32_t fused) {
+  if (!c) return SUB_EINVAL;
+  if (n < 0 || n > ((int64_t)1 << 40) || !(gamma >= -8.0 && gamma <= 10.0) ||
+      !(shape >= 1.0 && shape <= 1e6)) {
+    set_err(c, "generated catalog: need 0 <= n <= 2^40, -8 <= gamma <= 10, 1 <= shape <= 1e6");
+    return SUB_EINVAL;
+  }
+  {
+    int rc = reserve_sources(c, n);
+    if (rc) return rc;
+  }
+  if (fused) {
+    launch_gen_setup(c->dcat, n, seed, gamma, shape, nullptr, nullptr, nullptr, c->stream);
+  } else {
+    launch_gen_setup(c->dcat, n, seed, gamma, shape, c->A, c->f, c->fdot, c->stream);
+    launch_generate(c->dcat, 0, n, c->A, c->f, c->fdot, c->stream);
+  }
+  CU(cudaGetLastError(), c);
+  c->N = n;
+  c->ran = false;
+  c->cat_kind = fused ? kCatGenerated : kCatDevice;
+  return SUB_OK;
+}
+
+extern "C" int sub_get_catalog(sub_ctx* c, double* A, double* f, double* fdot, int64_t start,
+                               int64_t n, int where) {
+  if (!c) return SUB_EINVAL;
+  if (where != SUB_HOST && where != SUB_DEVICE) { set_err(c, "bad where"); return SUB_EINVAL; }
+  if (c->N < 0) { set_err(c, "no catalog loaded"); return SUB_ESTATE; }
+  if (start < 0 || n < 0 || start + n > c->N || (n > 0 && (!A || !f || !fdot))) {
+    set_err(c, "sub_get_catalog: need 0 <= start, start + n <= %lld and three buffers",
+            (long long)c->N);
+    return SUB_EINVAL;
+  }
+  if (n == 0) return SUB_OK;
+  cudaStream_t st = c->stream;
+  const size_t b = (size_t)n * 8;
+  double* out[3] = {A, f, fdot};
+  if (c->cat_kind == kCatGenerated) {
+    if (where == SUB_DEVICE) {
+      launch_generate(c->dcat, start, n, A, f, fdot, st);
+    } else {  // through the (otherwise unused) catalog arrays
+      launch_generate(c->dcat, start, n, c->A, c->f, c->fdot, st);
+      const double* src[3] = {c->A, c->f, c->fdot};
+      for (int i = 0; i < 3; ++i)
+        CU(cudaMemcpyAsync(out[i], src[i], b, cudaMemcpyDeviceToHost, st), c);
+    }
+  } else {
+    const double* dev[3] = {c->A, c->f, c->fdot};
+    for (int i = 0; i < 3; ++i) {
+      const double* src = (c->cat_kind == kCatHostMapped ? c->cat_host[i] : dev[i]) + start;
+      CU(cudaMemcpyAsync(out[i], src, b, cudaMemcpyDefault, st), c);
+    }
+  }
+  CU(cudaGetLastError(), c);
+  CU(cudaStreamSynchronize(st), c);
   return SUB_OK;
 }
 

@@ -58,6 +58,8 @@ struct sub_ctx {
   int64_t cap_N = 0;     // capacity of the per-source buffers
   double *A = nullptr, *f = nullptr, *fdot = nullptr;
   CatalogRef* dcat = nullptr;  // where the catalog pass reads the catalog (on the device)
+  int cat_kind = 1;            // kCatDevice (copied or materialised), kCatHostMapped, kCatGenerated
+  const double* cat_host[3] = {nullptr, nullptr, nullptr};  // the mapped arrays (kCatHostMapped)
   int test_flags = 0;       // sub_test_hooks
   Cands cd = {};
   unsigned char* resolved = nullptr;

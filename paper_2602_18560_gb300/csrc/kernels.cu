@@ -342,7 +342,17 @@ constexpr size_t kPrepassSmem = (size_t)kPreStages * kPreTile * 3 * sizeof(doubl
 // launch, long after every other warp is done).
 constexpr long long kSlowLaneBins = 4;
 
-__device__ __forceinline__ void prepass_drain(const double* __restrict__ A,
+// Source s of a generated catalog (kept out of line: the common path of the pass stays
+// small when the catalog is read from memory).
+__device__ __noinline__ double3 gen_source_at(const CatalogRef* __restrict__ cat, long long s) {
+  const GenParams g = cat->gen;
+  double3 r;
+  gen_source(g, s, &r.x, &r.y, &r.z);
+  return r;
+}
+
+__device__ __forceinline__ void prepass_drain(const CatalogRef* __restrict__ cat,
+                                              const double* __restrict__ A,
                                               const double* __restrict__ f,
                                               const double* __restrict__ fdot, const Grid& g,
                                               const Tables& tb, u64 tk_bits, u64 tl_bits,
@@ -358,9 +368,17 @@ __device__ __forceinline__ void prepass_drain(const double* __restrict__ A,
     double a2 = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
     bool wide = false;
     if (valid) {
-      double a = A[s];
-      fs = f[s];
-      fds = fdot[s];
+      double a;
+      if (cat->staged == kCatGenerated) {
+        const double3 gsrc = gen_source_at(cat, s);
+        a = gsrc.x;
+        fs = gsrc.y;
+        fds = gsrc.z;
+      } else {
+        a = A[s];
+        fs = f[s];
+        fds = fdot[s];
+      }
       a2 = __dmul_rn(a, a);
       wide = slow_span(fs, fds, g) > kSlowLaneBins;
       if (!wide) r = prepass_slow(a2, fs, fds, g, tb, acc, &rs->err);
@@ -393,7 +411,8 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
   const double* __restrict__ f = cat->f;
   const double* __restrict__ fdot = cat->fdot;
   const long long N = cat->n;
-  const bool use_tma = cat->staged != 0;
+  const bool use_tma = cat->staged == kCatDevice;
+  const bool generated = cat->staged == kCatGenerated;
   __shared__ long long slow_q[kSlowCap];
   __shared__ int slow_n;
   const int tid = threadIdx.x;
@@ -459,9 +478,16 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
         fv[k] = sF[idx];
         dv[k] = sD[idx];
       } else if (s < N) {
-        av[k] = A[s];
-        fv[k] = f[s];
-        dv[k] = fdot[s];
+        if (generated) {
+          const double3 gsrc = gen_source_at(cat, s);
+          av[k] = gsrc.x;
+          fv[k] = gsrc.y;
+          dv[k] = gsrc.z;
+        } else {
+          av[k] = A[s];
+          fv[k] = f[s];
+          dv[k] = fdot[s];
+        }
       }
     }
 #pragma unroll
@@ -519,7 +545,7 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
     }
     const int cnt = slow_n;
     if (cnt >= kPrepassThreads) {
-      prepass_drain(A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, slow_q, cnt, nkappa);
+      prepass_drain(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, slow_q, cnt, nkappa);
       __syncthreads();
       if (tid == 0) slow_n = 0;
       __syncthreads();
@@ -537,7 +563,7 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
     __syncthreads();
     return;
   }
-  prepass_drain(A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, slow_q, slow_n, nkappa);
+  prepass_drain(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, slow_q, slow_n, nkappa);
   for (int o = 16; o > 0; o >>= 1) nkappa += __shfl_xor_sync(0xFFFFFFFFu, nkappa, o);
   if (lane == 0 && nkappa) atomicAdd(&rs->ncand, nkappa);
 }
@@ -558,6 +584,66 @@ __global__ void k_set_catalog(CatalogRef* p, CatalogRef v) { *p = v; }
 
 void launch_set_catalog(CatalogRef* p, const CatalogRef& v, cudaStream_t st) {
   k_set_catalog<<<1, 1, 0, st>>>(p, v);
+}
+
+// ---------------------------------------------------------------- generated catalogs
+__global__ void k_gen_setup(CatalogRef* ref, long long n, unsigned long long seed, double gamma,
+                            double shape, const double* A, const double* f, const double* fdot) {
+  GenParams g;
+  g.k0 = (unsigned)seed;
+  g.k1 = (unsigned)(seed >> 32);
+  const float e = __double2float_rn(__dsub_rn(1.0, gamma));
+  const float lmin = gen_log(__double2float_rn(1e-4)), lmax = gen_log(__double2float_rn(1e-2));
+  g.power = fabs(__dsub_rn(gamma, 1.0)) >= 1e-6 ? 1 : 0;
+  g.a = g.power ? gen_exp(__fmul_rn(e, lmin)) : 0.0f;
+  g.b = g.power ? gen_exp(__fmul_rn(e, lmax)) : 0.0f;
+  g.inv_e = g.power ? __fdiv_rn(1.0f, e) : 0.0f;
+  g.lmin = lmin;
+  g.span = __fsub_rn(lmax, lmin);
+  g.d = __fsub_rn(__double2float_rn(shape), (float)(1.0 / 3.0));
+  g.c = __fdiv_rn(1.0f, __fsqrt_rn(__fmul_rn(9.0f, g.d)));
+  g.pref = __fmul_rn((float)19.2, gen_exp(__fmul_rn((float)(8.0 / 3.0),
+                                                    gen_log((float)3.141592653589793))));
+  g.log1e3 = gen_log((float)1e-3);
+  CatalogRef r;
+  r.A = A;
+  r.f = f;
+  r.fdot = fdot;
+  r.n = n;
+  r.staged = A ? kCatDevice : kCatGenerated;
+  r.pad = 0;
+  r.gen = g;
+  *ref = r;
+}
+
+void launch_gen_setup(CatalogRef* ref, long long n, unsigned long long seed, double gamma,
+                      double shape, const double* A, const double* f, const double* fdot,
+                      cudaStream_t st) {
+  k_gen_setup<<<1, 1, 0, st>>>(ref, n, seed, gamma, shape, A, f, fdot);
+}
+
+__global__ void __launch_bounds__(256) k_generate(const CatalogRef* __restrict__ ref,
+                                                  long long start, long long n,
+                                                  double* __restrict__ A, double* __restrict__ f,
+                                                  double* __restrict__ fdot) {
+  const GenParams g = ref->gen;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double a, fs, fd;
+    gen_source(g, start + i, &a, &fs, &fd);
+    A[i] = a;
+    f[i] = fs;
+    fdot[i] = fd;
+  }
+}
+
+void launch_generate(const CatalogRef* ref, long long start, long long n, double* A, double* f,
+                     double* fdot, cudaStream_t st) {
+  if (n <= 0) return;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
+  long long want = (n + 255) / 256, cap = (long long)(nsm > 0 ? nsm : 1) * 8;
+  k_generate<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(ref, start, n, A, f, fdot);
 }
 
 // ============================================================================ reductions

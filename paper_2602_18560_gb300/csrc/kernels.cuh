@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "generate.cuh"
+
 namespace gbsub {
 
 // Candidates that can still be resolved (rho_0 > rho_th), structure of arrays.
@@ -157,8 +159,11 @@ struct CatalogRef {
   long long n;
   int staged;  // 1: device memory, staged in tiles by bulk copies
                // 0: page-locked host memory, read in place with plain loads
+               // 2: generated: every source is computed from gen inside the pass
   int pad;
+  GenParams gen;  // the recipe's constants (generated catalogs)
 };
+enum { kCatHostMapped = 0, kCatDevice = 1, kCatGenerated = 2 };
 
 // The catalog pass over the cat->n sources.  test_flags & 1: issue no catalog copies, so
 // that the bounded waits run out (tests of the timeout path).
@@ -168,6 +173,17 @@ void launch_prepass(const CatalogRef* cat, long long cap, const Grid& g, const T
 
 // *p = v on the stream.
 void launch_set_catalog(CatalogRef* p, const CatalogRef& v, cudaStream_t st);
+
+// A generated catalog of n sources (seed, power-law index gamma, Gamma shape >= 1): its
+// constants are computed on the device into ref->gen.  With A null the catalog pass generates
+// every source itself (ref->staged = kCatGenerated); otherwise A, f, fdot receive the
+// catalog (launch_generate) and the pass reads them like a loaded one.
+void launch_gen_setup(CatalogRef* ref, long long n, unsigned long long seed, double gamma,
+                      double shape, const double* A, const double* f, const double* fdot,
+                      cudaStream_t st);
+// Sources start .. start+n-1 of the generated catalog described by ref->gen into A, f, fdot.
+void launch_generate(const CatalogRef* ref, long long start, long long n, double* A, double* f,
+                     double* fdot, cudaStream_t st);
 
 // Coarse graining: for every bin k of [edge[k], edge[k+1]) (nbins + 1 edges on the device),
 // the mean of x (of S + x when S is given), the mean frequency (k_lo + i) / T and the count.

@@ -88,7 +88,8 @@ class sub_server_stats(ctypes.Structure):
 
 _lib = None
 _lock = threading.Lock()
-EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_run", "sub_get_stats",
+EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_load_generated",
+           "sub_get_catalog", "sub_run", "sub_get_stats",
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
            "sub_get_tables", "sub_get_timing", "sub_get_work", "sub_coarse_grain", "sub_profile",
            "sub_device_bytes",
@@ -133,6 +134,9 @@ def lib(build_if_missing: bool = True):
             "sub_get_power": (i32, [P, P, i64, i32]),
             "sub_get_timing": (i32, [P, P, P, P]),
             "sub_get_work": (i32, [P, P, i32]),
+            "sub_load_generated": (i32, [P, i64, ctypes.c_uint64, ctypes.c_double,
+                                         ctypes.c_double, i32]),
+            "sub_get_catalog": (i32, [P, P, P, P, i64, i64, i32]),
             "sub_coarse_grain": (i32, [P, P, i32, i32, P, P, P, i32]),
             "sub_profile": (i32, [P, P, P, ctypes.POINTER(sub_stats)]),
             "sub_device_bytes": (i64, [P]),
@@ -226,6 +230,29 @@ def sub_load_catalog(ctx, A, f, fdot, mapped=False):
             raise ValueError("a mapped catalog lives in host memory")
         wa = HOST_MAPPED
     return _check(ctx, lib().sub_load_catalog(ctx, pa, pf, pd, na, wa))
+
+
+def sub_load_generated(ctx, n, seed, gamma=11.0 / 3.0, shape=2.0, fused=True):
+    """A catalog generated on the device (the single-precision recipe; synth.catalog_single
+    is the same recipe on the host).  fused: every run generates the sources inside its
+    catalog pass; otherwise they are generated once into device memory."""
+    return _check(ctx, lib().sub_load_generated(ctx, int(n), int(seed) & (2**64 - 1),
+                                                float(gamma), float(shape), int(bool(fused))))
+
+
+def sub_get_catalog(ctx, start, n, device=False):
+    """(A, f, fdot) of sources start .. start+n-1 of the current catalog."""
+    if device:
+        import torch
+        outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3)]
+        ptrs = [ctypes.c_void_p(t.data_ptr()) for t in outs]
+        where = DEVICE
+    else:
+        outs = [np.empty(n) for _ in range(3)]
+        ptrs = [t.ctypes.data_as(ctypes.c_void_p) for t in outs]
+        where = HOST
+    _check(ctx, lib().sub_get_catalog(ctx, *ptrs, int(start), int(n), where))
+    return tuple(outs)
 
 
 def sub_run(ctx, wait: bool = True):
@@ -359,6 +386,11 @@ def sub_destroy(ctx):
         lib().sub_destroy(ctx)
 
 
+def _default_population():
+    from . import synth
+    return synth.Population()
+
+
 class Subtraction:
     """One context: ``Subtraction(T_obs=..., window=..., estimator=...)``."""
 
@@ -372,6 +404,17 @@ class Subtraction:
         self.n_sources = int(len(A))
         self._mapped = (A, f, fdot) if mapped else None  # kept alive while runs read them
         return self
+
+    def load_generated(self, n, seed, pop=None, fused=True):
+        pop = pop if pop is not None else _default_population()
+        sub_load_generated(self.ctx, n, seed, pop.gamma, pop.shape, fused)
+        self.n_sources = int(n)
+        self._mapped = None
+        return self
+
+    def catalog(self, start=0, n=None, device=False):
+        n = self.n_sources - start if n is None else n
+        return sub_get_catalog(self.ctx, start, n, device)
 
     def run(self, wait=True):
         return sub_run(self.ctx, wait)

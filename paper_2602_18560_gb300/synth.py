@@ -184,6 +184,118 @@ def catalog(n: int, seed: int, pop: Population | None = None, start: int = 0,
     return A, f, fdot
 
 
+# ------------------------------------------------------------------ single-precision recipe
+# The catalog recipe of the device generator: the same counters and distributions as
+# catalog(), evaluated in IEEE single precision with basic operations only (no fused
+# multiply-add), so that numpy float32 here and the GPU produce the same bits.  Values are
+# returned as FP64 (exact conversions).  log: the atanh series up to t^13; exp: Taylor to r^8.
+_F = np.float32
+_LN2_HI32 = _F(0.693145751953125)        # 16 significant bits: exact products with |k| < 256
+_LN2_LO32 = _F(1.4286067653301870e-06)
+_LN2_32 = _F(0.6931471805599453)
+_SQRT_HALF32 = _F(0.7071067811865476)
+_TINY32 = _F(1.1754943508222875e-38)      # smallest normal float
+_LOG_C32 = [_F(1.0 / k) for k in (13, 11, 9, 7, 5, 3, 1)]
+_EXP_C32 = [_F(1.0 / math.factorial(i)) for i in range(8, -1, -1)]
+
+
+def plog32(x):
+    x = np.maximum(np.asarray(x, dtype=np.float32), _TINY32)
+    m, e = np.frexp(x)
+    small = m < _SQRT_HALF32
+    m = np.where(small, m * _F(2.0), m).astype(np.float32)
+    e = (e - small.astype(e.dtype)).astype(np.float32)
+    t = (m - _F(1.0)) / (m + _F(1.0))
+    t2 = t * t
+    acc = np.full(t.shape, _LOG_C32[0], dtype=np.float32)
+    for c in _LOG_C32[1:]:
+        acc = acc * t2 + c
+    return e * _LN2_HI32 + (e * _LN2_LO32 + _F(2.0) * t * acc)
+
+
+def pexp32(x):
+    x = np.asarray(x, dtype=np.float32)
+    k = np.rint(x / _LN2_32)
+    r = (x - k * _LN2_HI32) - k * _LN2_LO32
+    acc = np.full(r.shape, _EXP_C32[0], dtype=np.float32)
+    for c in _EXP_C32[1:]:
+        acc = acc * r + c
+    return np.ldexp(acc, k.astype(np.int32)).astype(np.float32)
+
+
+def u32f(a):
+    """Uniform float in (0, 1) from one 32-bit word (single precision)."""
+    return (np.asarray(a, dtype=np.uint32).astype(np.float32) + _F(0.5)) / _F(4294967296.0)
+
+
+def single_constants(pop: Population):
+    """Per-population constants of the single-precision recipe (all in float32)."""
+    e = _F(1.0 - pop.gamma)
+    lmin, lmax = plog32(_F(F_MIN)), plog32(_F(F_MAX))
+    power = abs(pop.gamma - 1.0) >= 1e-6
+    a = pexp32(e * lmin) if power else _F(0.0)
+    b = pexp32(e * lmax) if power else _F(0.0)
+    inv_e = _F(1.0) / e if power else _F(0.0)
+    span = lmax - lmin  # log-uniform case
+    d = _F(pop.shape) - _F(1.0 / 3.0)
+    c = _F(1.0) / np.sqrt(_F(9.0) * d)
+    pref = _F(19.2) * pexp32(_F(8.0 / 3.0) * plog32(_F(math.pi)))
+    return dict(power=power, a=_F(a), b=_F(b), inv_e=_F(inv_e), lmin=_F(lmin), span=_F(span),
+                d=_F(d), c=_F(c), pref=_F(pref), log1e3=_F(plog32(_F(1e-3))))
+
+
+def catalog_single(n: int, seed: int, pop: Population | None = None, start: int = 0,
+                   chunk: int = 1 << 22):
+    """Sources start .. start+n-1 of the single-precision recipe with this seed, as FP64
+    (A, f, fdot): the catalog the device generator produces."""
+    pop = pop or Population()
+    if pop.shape < 1.0:
+        raise ValueError("shape must be >= 1")
+    k = single_constants(pop)
+    k0, k1 = seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF
+    A = np.empty(n)
+    f = np.empty(n)
+    fdot = np.empty(n)
+    gm = _F(GMSUN_C3)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        idx = np.arange(start + s, start + e, dtype=np.int64)
+        lo = (idx & 0xFFFFFFFF).astype(np.uint64)
+        hi = (idx >> 32).astype(np.uint64)
+        x0, x1, x2, x3 = philox4x32_10(lo, hi, _STREAM_FM, 0, k0, k1)
+        u = u32f(x0)
+        if k["power"]:
+            fs = pexp32(k["inv_e"] * plog32(k["a"] + u * (k["b"] - k["a"])))
+        else:
+            fs = pexp32(k["lmin"] + u * k["span"])
+        mc = (_F(0.2) + _F(0.6) * u32f(x2)) * gm
+        # Gamma(shape, 1): Marsaglia-Tsang, a polar-method normal per attempt
+        X = np.full(idx.shape, k["d"], dtype=np.float32)
+        todo = np.arange(idx.size)
+        for t in range(_MAX_GAMMA_TRIES):
+            if todo.size == 0:
+                break
+            y0, y1, y2, y3 = philox4x32_10(lo[todo], hi[todo], _STREAM_GAMMA + t, 0, k0, k1)
+            p = _F(2.0) * u32f(y0) - _F(1.0)
+            q = _F(2.0) * u32f(y1) - _F(1.0)
+            s2 = p * p + q * q
+            inside = (s2 < _F(1.0)) & (s2 > _F(0.0))
+            s2 = np.where(inside, s2, _F(0.5)).astype(np.float32)
+            z = p * np.sqrt(_F(-2.0) * plog32(s2) / s2)
+            v = _F(1.0) + k["c"] * z
+            ok = inside & (v > _F(0.0))
+            v = np.where(ok, v * v * v, _F(1.0)).astype(np.float32)
+            ua = u32f(y2)
+            acc = ok & (plog32(ua) < _F(0.5) * z * z + k["d"] - k["d"] * v + k["d"] * plog32(v))
+            X[todo[acc]] = (k["d"] * v)[acc]
+            todo = todo[~acc]
+        lf = plog32(fs)
+        f[s:e] = fs
+        fdot[s:e] = k["pref"] * pexp32(_F(5.0 / 3.0) * plog32(mc) + _F(11.0 / 3.0) * lf)
+        A[s:e] = (_F(1e-23) * X) * pexp32(_F(2.0 / 3.0) * (lf - k["log1e3"]))
+    return A, f, fdot
+
+
 def population_draw(seed: int, index: int, gamma_range=(3.0, 4.5), shape_range=(1.5, 3.0)):
     """Per-catalog population parameters drawn uniformly from the given ranges."""
     x0, x1, x2, x3 = philox4x32_10(index & 0xFFFFFFFF, index >> 32, _STREAM_POP, 0,

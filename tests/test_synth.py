@@ -81,3 +81,47 @@ def test_parallel_generation_is_identical():
         ref = synth.catalog(n, seed, p)
         for a, b in zip(g, ref):
             np.testing.assert_array_equal(a, b)
+
+
+# ---------------------------------------------------------------- single-precision recipe
+def test_single_precision_log_exp_are_accurate():
+    x = np.float32(np.random.default_rng(0).uniform(1e-30, 1e3, 200000))
+    ref = np.log(x.astype(np.float64))
+    err = np.abs(synth.plog32(x).astype(np.float64) - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max() < 3e-7
+    y = np.float32(np.random.default_rng(1).uniform(-80.0, 20.0, 200000))
+    ref = np.exp(y.astype(np.float64))
+    assert np.max(np.abs(synth.pexp32(y).astype(np.float64) - ref) / ref) < 3e-7
+
+
+def test_single_recipe_distributions():
+    pop = synth.Population(gamma=3.5, shape=2.5)
+    n = 200_000
+    A, f, fdot = synth.catalog_single(n, 9, pop)
+    assert np.all(f >= 1e-4 * (1 - 1e-6)) and np.all(f <= 1e-2 * (1 + 1e-6))
+    # f: Kolmogorov-Smirnov distance to the truncated power law
+    e = 1.0 - pop.gamma
+    cdf = (np.sort(f) ** e - 1e-4 ** e) / (1e-2 ** e - 1e-4 ** e)
+    ks = np.max(np.abs(cdf - (np.arange(n) + 0.5) / n))
+    assert ks < 1.63 / np.sqrt(n)  # 1% level
+    # amplitude factor X ~ Gamma(shape, 1): mean and variance both equal the shape
+    X = A / (1e-23 * (f / 1e-3) ** (2.0 / 3.0))
+    assert abs(X.mean() - pop.shape) < 5 * np.sqrt(pop.shape / n)
+    assert abs(X.var() - pop.shape) < 0.05 * pop.shape
+    # chirp mass from fdot = (96/5) pi^(8/3) Mc^(5/3) f^(11/3): uniform on [0.2, 0.8] Msun
+    mc = (fdot / (96.0 / 5.0 * np.pi ** (8.0 / 3.0) * f ** (11.0 / 3.0))) ** 0.6 / synth.GMSUN_C3
+    assert mc.min() > 0.2 - 1e-5 and mc.max() < 0.8 + 1e-5
+    assert abs(mc.mean() - 0.5) < 5 * 0.6 / np.sqrt(12 * n)
+
+
+def test_single_recipe_slices_seeds_and_log_uniform_case():
+    pop = synth.Population(gamma=1.0, shape=1.0)
+    A, f, fdot = synth.catalog_single(50_000, 4, pop)
+    a2, f2, d2 = synth.catalog_single(1000, 4, pop, start=31_000)
+    assert np.array_equal(a2, A[31_000:32_000]) and np.array_equal(f2, f[31_000:32_000])
+    assert np.array_equal(d2, fdot[31_000:32_000])
+    # log-uniform f for gamma = 1
+    u = np.log(np.sort(f) / 1e-4) / np.log(100.0)
+    assert np.max(np.abs(u - (np.arange(f.size) + 0.5) / f.size)) < 1.63 / np.sqrt(f.size)
+    other = synth.catalog_single(1000, 5, pop)[1]
+    assert not np.array_equal(other, f[:1000])
