@@ -443,6 +443,51 @@ def main():
     except Exception as exc:  # reported, not fatal: the subtraction line stands on its own
         cg = {"error": str(exc)}
 
+    # ---------------------------------------------------------------- catalogs generated on the device
+    # the same population and size, drawn by the device generator (the single-precision recipe)
+    gen = None
+    if not args.no_e2e:
+        try:
+            gsub = gbsub.Subtraction(prm, stream=stream.cuda_stream)
+            res_gen = {}
+            for fused in (True, False):
+                gsub.load_generated(N, seed, w.pop, fused=fused)
+                for _ in range(3):
+                    gsub.run(wait=True)
+                torch.cuda.synchronize()
+                g0 = torch.cuda.Event(enable_timing=True)
+                g1 = torch.cuda.Event(enable_timing=True)
+                g0.record(stream)
+                for _ in range(10):
+                    gbsub.sub_run(gsub.ctx, wait=False)
+                g1.record(stream)
+                torch.cuda.synchronize()
+                res_gen["fused" if fused else "materialised"] = {
+                    "ms_per_run": g0.elapsed_time(g1) / 10,
+                    "catalog_pass_ms": gsub.timing()[0]}
+            # parameters in, coarse-grained foreground out: generate inside the pass, run,
+            # 100 bin averages of S_gal to the host
+            times = []
+            for _ in range(4):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                gsub.load_generated(N, seed, w.pop, fused=True)
+                gsub.run(wait=True)
+                Sk, fk, ck = gsub.coarse_grain()
+                times.append(time.perf_counter() - t0)
+            te = sum(times[1:]) / 3
+            st_g = gbsub.sub_get_stats(gsub.ctx)
+            gen = {"recipe": "device generator (single-precision recipe), seed %d, same population"
+                             % seed,
+                   "n_resolved": st_g.n_resolved, "iterations": st_g.iterations, **res_gen,
+                   "simulate": {"value": whole_job_rate(ws, N, te), "unit": "sources/s",
+                                "ms_per_step": te * 1e3, "h2d_bytes_per_step": 0,
+                                "d2h_bytes_per_step": 100 * 24,
+                                "api": "sub_load_generated(fused) + sub_run + sub_coarse_grain"}}
+            gsub.close()
+        except Exception as exc:  # reported, not fatal
+            gen = {"error": str(exc)}
+
     # ---------------------------------------------------------------- end to end (host buffers)
     e2e = None
     if not args.no_e2e:
@@ -510,7 +555,7 @@ def main():
                   "resolved_per_iteration": [int(x) for x in sub.history()],
                   "prepass_ms": pre_ms, "loop_ms": loop_ms},
         "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "coarse_grain": cg,
+        "coarse_grain": cg, "generated": gen,
         "gpu_launches": launches, "parity": parity,
     }
     line["clocks"] = clk.summary()

@@ -4,7 +4,10 @@
 // definition: every number a source needs is a pure function of (seed, source index,
 // stream), so any source can be generated, or generated again, on its own.
 // Distributions (the synthetic stand-in for the paper's population catalogs):
-//   f    : truncated power law p(f) ~ f^-gamma on [1e-4, 1e-2] Hz, by inverse CDF
+//   f    : truncated power law p(f) ~ f^-gamma on [1e-4, 1e-2] Hz, by inverse CDF in a form
+//          without cancellation: f = f0 (rho + u (1 - rho))^(1/(1-gamma)), f0 the end of
+//          highest density and rho = (f1/f0)^(1-gamma) < 1, so the sparse tail comes from
+//          small u (log-uniform within 1e-3 of gamma = 1)
 //   A    : 1e-23 X (f / 1e-3 Hz)^(2/3), X ~ Gamma(shape, 1) (Marsaglia-Tsang, with a
 //          polar-method normal per attempt)
 //   fdot : (96/5) pi^(8/3) Mc^(5/3) f^(11/3), Mc ~ U(0.2, 0.8) G Msun / c^3 (the GW-driven
@@ -21,8 +24,9 @@ namespace gbsub {
 
 struct GenParams {
   unsigned k0, k1;       // seed (low, high word)
-  int power;             // 1: power law (gamma != 1); 0: log-uniform
-  float a, b, inv_e;     // power law: f = exp(inv_e log(a + u (b - a)))
+  int power;             // 1: power law; 0: log-uniform (gamma within 1e-3 of 1)
+  float lf0, rho, omr;   // power law: f = exp(lf0 + inv_e log(rho + u omr)), omr = 1 - rho
+  float inv_e;
   float lmin, span;      // log-uniform: f = exp(lmin + u span)
   float d, c;            // Marsaglia-Tsang constants of Gamma(shape, 1)
   float pref, log1e3;    // (96/5) pi^(8/3); log(1e-3)
@@ -107,7 +111,7 @@ __device__ __forceinline__ void gen_source(const GenParams& p, long long s, doub
   const float u = gen_u32f(x[0]);
   float fs;
   if (p.power)
-    fs = gen_exp(__fmul_rn(p.inv_e, gen_log(__fadd_rn(p.a, __fmul_rn(u, __fsub_rn(p.b, p.a))))));
+    fs = gen_exp(__fadd_rn(p.lf0, __fmul_rn(p.inv_e, gen_log(__fadd_rn(p.rho, __fmul_rn(u, p.omr))))));
   else
     fs = gen_exp(__fadd_rn(p.lmin, __fmul_rn(u, p.span)));
   const float mc = __fmul_rn(__fadd_rn((float)0.2, __fmul_rn((float)0.6, gen_u32f(x[2]))),

@@ -594,9 +594,11 @@ __global__ void k_gen_setup(CatalogRef* ref, long long n, unsigned long long see
   g.k1 = (unsigned)(seed >> 32);
   const float e = __double2float_rn(__dsub_rn(1.0, gamma));
   const float lmin = gen_log(__double2float_rn(1e-4)), lmax = gen_log(__double2float_rn(1e-2));
-  g.power = fabs(__dsub_rn(gamma, 1.0)) >= 1e-6 ? 1 : 0;
-  g.a = g.power ? gen_exp(__fmul_rn(e, lmin)) : 0.0f;
-  g.b = g.power ? gen_exp(__fmul_rn(e, lmax)) : 0.0f;
+  g.power = fabs(__dsub_rn(gamma, 1.0)) >= 1e-3 ? 1 : 0;
+  const float lf0 = e < 0.0f ? lmin : lmax, lf1 = e < 0.0f ? lmax : lmin;
+  g.lf0 = lf0;
+  g.rho = g.power ? gen_exp(__fmul_rn(e, __fsub_rn(lf1, lf0))) : 0.0f;
+  g.omr = __fsub_rn(1.0f, g.rho);
   g.inv_e = g.power ? __fdiv_rn(1.0f, e) : 0.0f;
   g.lmin = lmin;
   g.span = __fsub_rn(lmax, lmin);

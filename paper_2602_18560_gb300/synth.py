@@ -229,18 +229,24 @@ def u32f(a):
 
 
 def single_constants(pop: Population):
-    """Per-population constants of the single-precision recipe (all in float32)."""
+    """Per-population constants of the single-precision recipe (all in float32).  The
+    inverse CDF is f = f0 (rho + u (1 - rho))^(1/e), e = 1 - gamma, with f0 the end where
+    the density is highest and rho = (f1/f0)^e < 1: the sparse tail comes from small u,
+    where the uniform keeps its full relative precision, and nothing cancels.  Within 1e-3
+    of gamma = 1 the density is taken as log-uniform."""
     e = _F(1.0 - pop.gamma)
     lmin, lmax = plog32(_F(F_MIN)), plog32(_F(F_MAX))
-    power = abs(pop.gamma - 1.0) >= 1e-6
-    a = pexp32(e * lmin) if power else _F(0.0)
-    b = pexp32(e * lmax) if power else _F(0.0)
+    power = abs(pop.gamma - 1.0) >= 1e-3
+    lf0, lf1 = (lmin, lmax) if e < 0 else (lmax, lmin)
+    rho = pexp32(e * (lf1 - lf0)) if power else _F(0.0)
+    omr = _F(1.0) - rho
     inv_e = _F(1.0) / e if power else _F(0.0)
     span = lmax - lmin  # log-uniform case
     d = _F(pop.shape) - _F(1.0 / 3.0)
     c = _F(1.0) / np.sqrt(_F(9.0) * d)
     pref = _F(19.2) * pexp32(_F(8.0 / 3.0) * plog32(_F(math.pi)))
-    return dict(power=power, a=_F(a), b=_F(b), inv_e=_F(inv_e), lmin=_F(lmin), span=_F(span),
+    return dict(power=power, lf0=_F(lf0), rho=_F(rho), omr=_F(omr), inv_e=_F(inv_e),
+                lmin=_F(lmin), span=_F(span),
                 d=_F(d), c=_F(c), pref=_F(pref), log1e3=_F(plog32(_F(1e-3))))
 
 
@@ -265,7 +271,7 @@ def catalog_single(n: int, seed: int, pop: Population | None = None, start: int 
         x0, x1, x2, x3 = philox4x32_10(lo, hi, _STREAM_FM, 0, k0, k1)
         u = u32f(x0)
         if k["power"]:
-            fs = pexp32(k["inv_e"] * plog32(k["a"] + u * (k["b"] - k["a"])))
+            fs = pexp32(k["lf0"] + k["inv_e"] * plog32(k["rho"] + u * k["omr"]))
         else:
             fs = pexp32(k["lmin"] + u * k["span"])
         mc = (_F(0.2) + _F(0.6) * u32f(x2)) * gm
