@@ -56,7 +56,8 @@ __host__ __device__ __forceinline__ void philox4x32_10(unsigned c[4], unsigned k
 
 #ifdef __CUDACC__
 __device__ __forceinline__ float gen_u32f(unsigned x) {
-  return __fdiv_rn(__fadd_rn(__uint2float_rn(x), 0.5f), 4294967296.0f);
+  // (x + 1/2) / 2^32: dividing by a power of two is the exact product with its inverse
+  return __fmul_rn(__fadd_rn(__uint2float_rn(x), 0.5f), 2.3283064365386963e-10f);
 }
 
 __device__ __forceinline__ float gen_log(float x) {
@@ -109,11 +110,11 @@ __device__ __forceinline__ void gen_source(const GenParams& p, long long s, doub
   unsigned x[4] = {lo, hi, kStreamFM, 0u};
   philox4x32_10(x, p.k0, p.k1);
   const float u = gen_u32f(x[0]);
-  float fs;
-  if (p.power)
-    fs = gen_exp(__fadd_rn(p.lf0, __fmul_rn(p.inv_e, gen_log(__fadd_rn(p.rho, __fmul_rn(u, p.omr))))));
-  else
-    fs = gen_exp(__fadd_rn(p.lmin, __fmul_rn(u, p.span)));
+  // log f is the exponent that f comes from (no second logarithm)
+  const float lf = p.power
+                       ? __fadd_rn(p.lf0, __fmul_rn(p.inv_e, gen_log(__fadd_rn(p.rho, __fmul_rn(u, p.omr)))))
+                       : __fadd_rn(p.lmin, __fmul_rn(u, p.span));
+  const float fs = gen_exp(lf);
   const float mc = __fmul_rn(__fadd_rn((float)0.2, __fmul_rn((float)0.6, gen_u32f(x[2]))),
                              (float)4.925490947e-6);
   float X = p.d;
@@ -138,7 +139,6 @@ __device__ __forceinline__ void gen_source(const GenParams& p, long long s, doub
       break;
     }
   }
-  const float lf = gen_log(fs);
   const float fd = __fmul_rn(p.pref, gen_exp(__fadd_rn(__fmul_rn((float)(5.0 / 3.0), gen_log(mc)),
                                                       __fmul_rn((float)(11.0 / 3.0), lf))));
   const float a = __fmul_rn(__fmul_rn((float)1e-23, X),

@@ -270,10 +270,12 @@ def catalog_single(n: int, seed: int, pop: Population | None = None, start: int 
         hi = (idx >> 32).astype(np.uint64)
         x0, x1, x2, x3 = philox4x32_10(lo, hi, _STREAM_FM, 0, k0, k1)
         u = u32f(x0)
+        # log f is the exponent that f comes from (no second logarithm)
         if k["power"]:
-            fs = pexp32(k["lf0"] + k["inv_e"] * plog32(k["rho"] + u * k["omr"]))
+            lf = k["lf0"] + k["inv_e"] * plog32(k["rho"] + u * k["omr"])
         else:
-            fs = pexp32(k["lmin"] + u * k["span"])
+            lf = k["lmin"] + u * k["span"]
+        fs = pexp32(lf)
         mc = (_F(0.2) + _F(0.6) * u32f(x2)) * gm
         # Gamma(shape, 1): Marsaglia-Tsang, a polar-method normal per attempt
         X = np.full(idx.shape, k["d"], dtype=np.float32)
@@ -295,7 +297,6 @@ def catalog_single(n: int, seed: int, pop: Population | None = None, start: int 
             acc = ok & (plog32(ua) < _F(0.5) * z * z + k["d"] - k["d"] * v + k["d"] * plog32(v))
             X[todo[acc]] = (k["d"] * v)[acc]
             todo = todo[~acc]
-        lf = plog32(fs)
         f[s:e] = fs
         fdot[s:e] = k["pref"] * pexp32(_F(5.0 / 3.0) * plog32(mc) + _F(11.0 / 3.0) * lf)
         A[s:e] = (_F(1e-23) * X) * pexp32(_F(2.0 / 3.0) * (lf - k["log1e3"]))
