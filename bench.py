@@ -386,15 +386,18 @@ def main():
                       "GB/s": bytes_run / (ms_run * 1e-3) / 1e9}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_run"])
     hbm, hbm_kind = peaks()
-    tr = {}
+    tr_all = {}
     prof_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof_path):
         try:
             with open(prof_path) as fh:
                 tr_all = json.load(fh).get(w.name, {})
-            tr = {k: v for k, v in tr_all.items() if v.get("kernel_source_sha256") == source_digest()}
         except Exception:
-            tr = {}
+            tr_all = {}
+    # DRAM traffic only from a capture of the current sources; instruction counts per unit
+    # from the latest capture, flagged when the sources have changed since
+    digest = source_digest()
+    tr = {k: v for k, v in tr_all.items() if v.get("kernel_source_sha256") == digest}
     kd = kernels[dom]
     per_launch_ms = kd["ms_per_run"] / kd["launches_per_run"]
     bytes_launch = kd["algorithmic_bytes_per_run"] / kd["launches_per_run"]
@@ -405,7 +408,7 @@ def main():
         u0 = tr[dom].get("units_first_launch")
         traffic = (t0 * (kd["units_per_run"] / kd["launches_per_run"]) / u0
                    if (u0 and kd["units_per_run"] is not None) else t0)
-    if dom in ("prepass", "snr", "prefix", "mean") or dom not in tr:
+    if dom in ("prepass", "snr", "prefix", "mean") or "warp_inst_per_unit" not in tr_all.get(dom, {}):
         roofline = {"bound": "hbm", "kernel": dom, "achieved": bytes_launch / (per_launch_ms * 1e-3) / 1e9,
                     "peak": hbm, "unit": "GB/s", "peak_kind": hbm_kind}
         roofline["frac"] = roofline["achieved"] / hbm
@@ -415,13 +418,16 @@ def main():
         nsm = torch.cuda.get_device_properties(0).multi_processor_count
         fmax = clk.summary().get("sm_max_mhz") or 2070.0
         peak_issue = nsm * 4 * fmax * 1e6 / 1e9
-        inst_launch = tr[dom]["warp_inst_per_unit"] * kd["units_per_run"] / kd["launches_per_run"]
+        inst_launch = (tr_all[dom]["warp_inst_per_unit"] * kd["units_per_run"]
+                       / kd["launches_per_run"])
         roofline = {"bound": "alu", "kernel": dom,
                     "achieved": inst_launch / (per_launch_ms * 1e-3) / 1e9,
                     "peak": peak_issue, "unit": "G warp-instructions/s",
                     "peak_kind": "derived: %d SMs x 4 schedulers x %.0f MHz" % (nsm, fmax),
                     "hbm_view": {"GB/s": bytes_launch / (per_launch_ms * 1e-3) / 1e9,
-                                 "frac": bytes_launch / (per_launch_ms * 1e-3) / 1e9 / hbm}}
+                                 "frac": bytes_launch / (per_launch_ms * 1e-3) / 1e9 / hbm},
+                    "instructions_from": "ncu capture of the current sources" if dom in tr else
+                                         "ncu capture of earlier sources (stale)"}
         roofline["frac"] = roofline["achieved"] / peak_issue
     pre_algo = algorithmic_bytes("prepass", N, nb, nlive, est)
     whole_bytes = sum(v["algorithmic_bytes_per_run"] for v in kernels.values()) + N
