@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--workload", default="nb3e7_4yr")
     ap.add_argument("--estimator", choices=list(EST), default="median_mean")
     ap.add_argument("--window", type=int, default=1000)
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
+                    help="fp64 by default; mixed by default in batch mode (batched mixed "
+                         "precision against sequential FP64 runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", choices=["single", "batch", "serve", "study"], default="single",
@@ -56,7 +58,10 @@ def parse():
                          "the mean-vs-median estimator study")
     ap.add_argument("--jobs", type=int, default=2000, help="serve mode: jobs")
     ap.add_argument("--rate", type=float, default=200.0, help="serve mode: jobs/s offered")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "mixed" if args.mode == "batch" else "fp64"
+    return args
 
 
 
