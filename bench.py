@@ -207,6 +207,44 @@ def unit_bytes(kernel, Kc, est):
     return 0
 
 
+def dominant_roofline(dom, kd, tr_all, digest, hbm, hbm_kind, nsm, fmax_mhz):
+    """Roofline of the dominant kernel, per average launch.  kd: its ms_per_run,
+    launches_per_run, units_per_run (None for one-unit kernels) and algorithmic bytes per
+    run; tr_all: profiles/traffic.json for the workload (ncu DRAM bytes and warp instructions
+    per unit of a full first launch, with the digest of the sources captured).
+    The catalog pass and the chunk kernels: algorithmic bytes over the measured HBM peak.
+    The sort and the median: warp instructions over the issue rate (one per scheduler per
+    clock), with their bytes as a secondary view.  traffic: the capture's DRAM bytes scaled
+    to an average launch's units, only when the capture is of the current sources."""
+    fresh = tr_all.get(dom, {}).get("kernel_source_sha256") == digest
+    per_launch_ms = kd["ms_per_run"] / kd["launches_per_run"]
+    bytes_launch = kd["algorithmic_bytes_per_run"] / kd["launches_per_run"]
+    units_launch = (kd["units_per_run"] / kd["launches_per_run"]
+                    if kd.get("units_per_run") is not None else None)
+    gbs = bytes_launch / (per_launch_ms * 1e-3) / 1e9
+    traffic = None
+    if fresh:
+        t0 = tr_all[dom]["dram_bytes_per_launch"]
+        u0 = tr_all[dom].get("units_first_launch")
+        traffic = t0 * units_launch / u0 if (u0 and units_launch is not None) else t0
+    inst = tr_all.get(dom, {}).get("warp_inst_per_unit")
+    if dom in ("sort", "median") and inst is not None and units_launch is not None:
+        peak = nsm * 4 * fmax_mhz * 1e6 / 1e9
+        achieved = inst * units_launch / (per_launch_ms * 1e-3) / 1e9
+        out = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+               "unit": "G warp-instructions/s", "frac": achieved / peak,
+               "peak_kind": "derived: %d SMs x 4 schedulers x %.0f MHz" % (nsm, fmax_mhz),
+               "hbm_view": {"GB/s": gbs, "frac": gbs / hbm},
+               "instructions_from": "ncu capture of the current sources" if fresh else
+                                    "ncu capture of earlier sources (stale)"}
+    else:
+        out = {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": hbm, "unit": "GB/s",
+               "frac": gbs / hbm, "peak_kind": hbm_kind}
+    out.update({"traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
+                "ms_per_launch": per_launch_ms})
+    return out
+
+
 def loop_units(kernel, work, est):
     """Work items a loop kernel was handed over a run (sub_get_work), None for the others."""
     lists = {2: {"sort": "changed", "median": "tiles", "prefix": "within1", "mean": "within2"},
@@ -403,42 +441,13 @@ def main():
     # from the latest capture, flagged when the sources have changed since
     digest = source_digest()
     tr = {k: v for k, v in tr_all.items() if v.get("kernel_source_sha256") == digest}
-    kd = kernels[dom]
-    per_launch_ms = kd["ms_per_run"] / kd["launches_per_run"]
-    bytes_launch = kd["algorithmic_bytes_per_run"] / kd["launches_per_run"]
-    # DRAM traffic of the first (full) launch from ncu, scaled by the units of an average launch
-    traffic = None
-    if dom in tr:
-        t0 = tr[dom]["dram_bytes_per_launch"]
-        u0 = tr[dom].get("units_first_launch")
-        traffic = (t0 * (kd["units_per_run"] / kd["launches_per_run"]) / u0
-                   if (u0 and kd["units_per_run"] is not None) else t0)
-    if dom in ("prepass", "snr", "prefix", "mean") or "warp_inst_per_unit" not in tr_all.get(dom, {}):
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": bytes_launch / (per_launch_ms * 1e-3) / 1e9,
-                    "peak": hbm, "unit": "GB/s", "peak_kind": hbm_kind}
-        roofline["frac"] = roofline["achieved"] / hbm
-    else:
-        # sort and median: shared-memory and integer work on an L2-resident spectrum, bound by
-        # instruction issue (one warp instruction per scheduler per clock)
-        nsm = torch.cuda.get_device_properties(0).multi_processor_count
-        fmax = clk.summary().get("sm_max_mhz") or 2070.0
-        peak_issue = nsm * 4 * fmax * 1e6 / 1e9
-        inst_launch = (tr_all[dom]["warp_inst_per_unit"] * kd["units_per_run"]
-                       / kd["launches_per_run"])
-        roofline = {"bound": "alu", "kernel": dom,
-                    "achieved": inst_launch / (per_launch_ms * 1e-3) / 1e9,
-                    "peak": peak_issue, "unit": "G warp-instructions/s",
-                    "peak_kind": "derived: %d SMs x 4 schedulers x %.0f MHz" % (nsm, fmax),
-                    "hbm_view": {"GB/s": bytes_launch / (per_launch_ms * 1e-3) / 1e9,
-                                 "frac": bytes_launch / (per_launch_ms * 1e-3) / 1e9 / hbm},
-                    "instructions_from": "ncu capture of the current sources" if dom in tr else
-                                         "ncu capture of earlier sources (stale)"}
-        roofline["frac"] = roofline["achieved"] / peak_issue
+    roofline = dominant_roofline(
+        dom, kernels[dom], tr_all, digest, hbm, hbm_kind,
+        torch.cuda.get_device_properties(0).multi_processor_count,
+        clk.summary().get("sm_max_mhz") or 2070.0)
     pre_algo = algorithmic_bytes("prepass", N, nb, nlive, est)
     whole_bytes = sum(v["algorithmic_bytes_per_run"] for v in kernels.values()) + N
-    roofline.update({"traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
-                     "ms_per_launch": per_launch_ms,
-                     "catalog_pass": {"ms": pre_ms, "GB/s": pre_algo / (pre_ms * 1e-3) / 1e9,
+    roofline.update({"catalog_pass": {"ms": pre_ms, "GB/s": pre_algo / (pre_ms * 1e-3) / 1e9,
                                       "frac": pre_algo / (pre_ms * 1e-3) / 1e9 / hbm,
                                       "traffic": tr.get("prepass", {}).get("dram_bytes_per_launch")},
                      "whole_run": {"algorithmic_bytes": whole_bytes,

@@ -57,3 +57,40 @@ def test_single_process_helpers():
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
     assert bench.whole_job_rate(1, 10, 2.0) == 5.0
     assert bench.replica_seed(7, 0) == 7
+
+
+def test_roofline_of_the_dominant_kernel():
+    sys.path.insert(0, ROOT)
+    import bench
+    tr = {"median": {"dram_bytes_per_launch": 1.2e7, "units_first_launch": 1222,
+                     "warp_inst_per_unit": 7.0e4, "kernel_source_sha256": "abc"},
+          "prepass": {"dram_bytes_per_launch": 8.1e8, "kernel_source_sha256": "abc"}}
+    med = {"ms_per_run": 0.5, "launches_per_run": 17.0, "units_per_run": 2432,
+           "algorithmic_bytes_per_run": 7.0e7}
+    r = bench.dominant_roofline("median", med, tr, "abc", 6700.0, "of measured", 152, 2070.0)
+    assert r["bound"] == "alu" and r["peak"] == pytest.approx(152 * 4 * 2.07)
+    per_launch_s = 0.5e-3 / 17
+    assert r["achieved"] == pytest.approx(7.0e4 * 2432 / 17 / per_launch_s / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["traffic"] == pytest.approx(1.2e7 * (2432 / 17) / 1222)
+    assert r["hbm_view"]["GB/s"] == pytest.approx(7.0e7 / 17 / per_launch_s / 1e9)
+    # a capture of other sources: same bound and instructions, no traffic, flagged
+    stale = bench.dominant_roofline("median", med, tr, "new", 6700.0, "of measured", 152, 2070.0)
+    assert stale["bound"] == "alu" and stale["traffic"] is None
+    assert "stale" in stale["instructions_from"]
+    pre = {"ms_per_run": 0.5, "launches_per_run": 1.0, "units_per_run": None,
+           "algorithmic_bytes_per_run": 7.6e8}
+    p = bench.dominant_roofline("prepass", pre, tr, "abc", 6700.0, "of measured", 152, 2070.0)
+    assert p["bound"] == "hbm" and p["achieved"] == pytest.approx(7.6e8 / 0.5e-3 / 1e9)
+    assert p["traffic"] == 8.1e8 and p["frac"] == pytest.approx(p["achieved"] / 6700.0)
+
+
+def test_loop_units_follow_the_estimator_lists():
+    sys.path.insert(0, ROOT)
+    import bench
+    work = {"changed": 10, "within1": 20, "within2": 30, "tiles": 15}
+    assert [bench.loop_units(k, work, 2) for k in ("sort", "median", "prefix", "mean")] == [
+        10, 15, 20, 30]
+    assert [bench.loop_units(k, work, 0) for k in ("prefix", "mean")] == [10, 20]
+    assert bench.loop_units("median", work, 1) == 15 and bench.loop_units("snr", work, 2) is None
+    assert bench.unit_bytes("median", 1024, 2) == 28 * 1024
