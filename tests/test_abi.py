@@ -52,6 +52,20 @@ def test_invalid_parameters_rejected_before_any_device_call():
         assert ei.value.code == gbsub.EINVAL
 
 
+def test_calls_without_a_context_are_rejected():
+    # every call checks its context first and touches no device without one
+    import ctypes as C
+    L = gbsub.lib()
+    buf = (C.c_double * 4)()
+    n64 = (C.c_int64 * 4)()
+    assert L.sub_load_generated(None, 10, 1, 3.0, 2.0, 1) == gbsub.EINVAL
+    assert L.sub_get_catalog(None, buf, buf, buf, 0, 1, gbsub.HOST) == gbsub.EINVAL
+    assert L.sub_coarse_grain(None, None, 0, 100, buf, buf, n64, gbsub.HOST) == gbsub.EINVAL
+    assert L.sub_get_work(None, n64, 4) == gbsub.EINVAL
+    assert L.sub_load_catalog(None, buf, buf, buf, 1, gbsub.HOST_MAPPED) == gbsub.EINVAL
+    assert L.sub_run(None, None) == gbsub.EINVAL
+
+
 def test_struct_layouts_match_the_c_header(tmp_path):
     # sizes and field offsets of every public struct as the C compiler lays them out
     import shutil
