@@ -645,10 +645,10 @@ def run_batch(args, ws, rank, local_rank):
     for s in seq:
         s.close()
 
-    # the batch: mixed precision (or fp64), autotuned grid divisor, one graph launch
+    # the batch: mixed precision (or fp64), autotuned launch settings, one graph launch
     subs = contexts(prec)
     batch = gbsub.Batch(subs)
-    best, tuning = autotune.tune_batch(batch, subs)
+    settings, tuning = autotune.tune_batch(batch, subs)
     for _ in range(max(3, args.warmup)):
         batch.run()
     if pg:
@@ -704,7 +704,7 @@ def run_batch(args, ws, rank, local_rank):
                    "parallelism": "replicas" if ws > 1 else "single"},
         "baseline_sequential_fp64": {"catalogs_per_s": 64 / seq_s, "ms_per_64": seq_s * 1e3,
                                      "speedup_of_batch": value / ws / (64 / seq_s)},
-        "autotune": {"grid_div": best, "ms_by_grid_div": tuning},
+        "autotune": {"settings": settings, "ms_by_setting": tuning},
         "accuracy_vs_fp64": {"S_gal_max_rel_err": worst, "resolved_disagreement": ndiff,
                              "resolved_total": nres,
                              "tolerance": {"S_gal_rel": 1e-5,

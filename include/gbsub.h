@@ -320,6 +320,19 @@ void sub_batch_destroy(sub_batch* b);
  * Errors: SUB_EINVAL. */
 int sub_set_grid_div(sub_ctx* ctx, int32_t div);
 
+/* Launch settings that leave every result unchanged bit for bit (for autotuners):
+ *   SUB_TUNE_GRID_DIV       persistent grids at 1/value of the GPU (1 .. 64), as
+ *                           sub_set_grid_div
+ *   SUB_TUNE_SORT_E         elements per thread of the chunk sort: 2, 4 or 8 with
+ *                           kpad / value in 32 .. 1024 (kpad: the power of two >= the chunk
+ *                           length), or 0 for the automatic choice
+ *   SUB_TUNE_MEDIAN_THREADS threads per median tile: a multiple of 32 up to 512, or 0
+ * The context's graph is rebuilt by its next run.  Errors: SUB_EINVAL. */
+#define SUB_TUNE_GRID_DIV 0
+#define SUB_TUNE_SORT_E 1
+#define SUB_TUNE_MEDIAN_THREADS 2
+int sub_set_tuning(sub_ctx* ctx, int32_t knob, int32_t value);
+
 /* Test hooks: failures made on purpose, for tests of the error paths.  The catalog pass
  * waits on its staged copies with a bound of about a second; with
  * SUB_TEST_SKIP_CATALOG_COPIES it starts none, every wait runs out, the loop stops and

@@ -132,7 +132,7 @@ static int validate(const sub_params* p, int64_t* k_lo, int64_t* n) {
 }
 
 static SmoothPlan make_plan(int W, int64_t n) {
-  SmoothPlan pl;
+  SmoothPlan pl = {};
   pl.W = W;
   int kc = ((W + 31) / 32) * 32;
   if (kc < 32) kc = 32;
@@ -681,15 +681,46 @@ void gbsub::ctx_set_test_flags(sub_ctx* c, int flags) {
   c->test_flags = flags;
 }
 
+// Persistent grids from the plan's launch settings, at 1/grid_div of the GPU.
+static void replan(sub_ctx* c) {
+  const int div = c->grid_div;
+  plan_grids(c->plan);
+  int* res[] = {&c->plan.res_sort, &c->plan.res_median, &c->plan.res_prefix, &c->plan.res_mean};
+  for (int* r : res) *r = (*r / div) > 0 ? *r / div : 1;
+  c->nsm_run = c->nsm / div > 0 ? c->nsm / div : 1;
+}
+
 void gbsub::ctx_set_grid_div(sub_ctx* c, int div) {
   if (div < 1) div = 1;
   if (div == c->grid_div) return;
   drop_graph(c);
   c->grid_div = div;
-  plan_grids(c->plan);
-  int* res[] = {&c->plan.res_sort, &c->plan.res_median, &c->plan.res_prefix, &c->plan.res_mean};
-  for (int* r : res) *r = (*r / div) > 0 ? *r / div : 1;
-  c->nsm_run = c->nsm / div > 0 ? c->nsm / div : 1;
+  replan(c);
+}
+
+int gbsub::ctx_set_tuning(sub_ctx* c, int knob, int value) {
+  if (knob == SUB_TUNE_GRID_DIV) {
+    if (value < 1 || value > 64) return SUB_EINVAL;
+    ctx_set_grid_div(c, value);
+    return SUB_OK;
+  }
+  if (knob == SUB_TUNE_SORT_E) {
+    const bool ok = value == 0 || ((value == 2 || value == 4 || value == 8) &&
+                                   c->plan.kpad / value >= 32 && c->plan.kpad / value <= 1024);
+    if (!ok) return SUB_EINVAL;
+    if (value == c->plan.sort_e) return SUB_OK;
+    drop_graph(c);
+    c->plan.sort_e = value;
+  } else if (knob == SUB_TUNE_MEDIAN_THREADS) {
+    if (!(value == 0 || (value % 32 == 0 && value >= 32 && value <= 512))) return SUB_EINVAL;
+    if (value == c->plan.median_th) return SUB_OK;
+    drop_graph(c);
+    c->plan.median_th = value;
+  } else {
+    return SUB_EINVAL;
+  }
+  replan(c);
+  return SUB_OK;
 }
 
 extern "C" int sub_run(sub_ctx* c, sub_stats* st) {

@@ -96,6 +96,7 @@ int ctx_fill_stats(sub_ctx* c, sub_stats* st);
 cudaError_t ctx_add_run_nodes(sub_ctx* c, cudaGraph_t g, cudaGraphNode_t* last);
 // Grid divisor of the persistent kernels (1 = the whole GPU).
 void ctx_set_grid_div(sub_ctx* c, int div);
+int ctx_set_tuning(sub_ctx* c, int knob, int value);  // SUB_OK or SUB_EINVAL
 // Buffers for catalogs of up to cap sources and the run's graph, ahead of the first catalog.
 int ctx_prepare(sub_ctx* c, int64_t cap);
 // Test hooks (SUB_TEST_*) baked into the next graph.

@@ -1038,7 +1038,10 @@ static void launch_sort_as(void (*kern)(SpecIn, long long, SmoothPlan, K*, uint1
   kern<<<bl, th, smem, st>>>(in, n, pl, (K*)skey, srank, d);
 }
 
-static int sort_per_thread(const SmoothPlan& pl) { return pl.kpad <= 2048 ? 2 : pl.kpad / 1024; }
+static int sort_per_thread(const SmoothPlan& pl) {
+  if (pl.sort_e) return pl.sort_e;
+  return pl.kpad <= 2048 ? 2 : pl.kpad / 1024;
+}
 static int sort_threads(const SmoothPlan& pl) { return pl.kpad / sort_per_thread(pl); }
 static size_t sort_smem(const SmoothPlan& pl) {
   const size_t kb = pl.fp32_keys ? 4 : 8;
@@ -1305,6 +1308,7 @@ __global__ void __launch_bounds__(512, 2) k_median_wm(
 }
 
 static int median_threads(const SmoothPlan& pl) {
+  if (pl.median_th) return pl.median_th;
   int t = ((pl.Kc / 2 + 31) / 32) * 32;
   if (t < 32) t = 32;
   if (t > 512) t = 512;

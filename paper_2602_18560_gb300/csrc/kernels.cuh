@@ -70,6 +70,8 @@ struct SmoothPlan {
   int fp32_keys;  // median on the FP32-rounded values (mixed precision): 4-byte keys
   double key_scale;  // power of two the values are scaled by before rounding to FP32
   int res_sort, res_median, res_prefix, res_mean;  // CTAs resident at once (plan_grids)
+  int sort_e;     // elements per sorting thread (2, 4, 8), 0: chosen from kpad
+  int median_th;  // threads per median tile (multiple of 32, <= 512), 0: chosen from Kc
 };
 
 // Source of an estimator's input: the run's fixed-point spectrum (P_k = S_k Q_k 2^-96) or

@@ -94,7 +94,7 @@ extern "C" int sub_running_mean_noalloc(const double* x, double* out, int64_t n,
     }
     base = g_addr[dev];
   }
-  SmoothPlan pl;
+  SmoothPlan pl = {};
   pl.W = window;
   pl.Kc = ((window + 31) / 32) * 32;
   if (pl.Kc < 32) pl.Kc = 32;

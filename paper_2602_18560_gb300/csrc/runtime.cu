@@ -201,6 +201,13 @@ extern "C" int sub_set_grid_div(sub_ctx* c, int32_t div) {
   return SUB_OK;
 }
 
+extern "C" int sub_set_tuning(sub_ctx* c, int32_t knob, int32_t value) {
+  if (!c) return SUB_EINVAL;
+  const int rc = ctx_set_tuning(c, knob, value);
+  if (rc) ctx_set_err(c, "launch setting %d = %d is not allowed for this context", knob, value);
+  return rc;
+}
+
 // ============================================================================ server
 
 namespace {

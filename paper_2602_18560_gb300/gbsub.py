@@ -96,7 +96,7 @@ EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_load_gen
            "sub_destroy",
            "sub_last_error", "sub_running_mean_noalloc", "sub_get_power", "sub_batch_create",
            "sub_batch_run", "sub_batch_last_ms", "sub_batch_last_error", "sub_batch_destroy",
-           "sub_set_grid_div", "sub_test_hooks", "sub_server_params_default", "sub_server_create",
+           "sub_set_grid_div", "sub_set_tuning", "sub_test_hooks", "sub_server_params_default", "sub_server_create",
            "sub_server_submit", "sub_server_poll", "sub_server_info", "sub_server_last_error",
            "sub_server_prewarm",
            "sub_server_destroy")
@@ -149,6 +149,7 @@ def lib(build_if_missing: bool = True):
             "sub_batch_last_error": (ctypes.c_char_p, [P]),
             "sub_batch_destroy": (None, [P]),
             "sub_set_grid_div": (i32, [P, i32]),
+            "sub_set_tuning": (i32, [P, i32, i32]),
             "sub_test_hooks": (i32, [P, i32]),
             "sub_server_params_default": (i32, [ctypes.POINTER(sub_server_params)]),
             "sub_server_create": (i32, [ctypes.POINTER(sub_server_params), ctypes.POINTER(P)]),
@@ -475,6 +476,14 @@ class Subtraction:
 
 def sub_set_grid_div(ctx, div: int):
     return _check(ctx, lib().sub_set_grid_div(ctx, int(div)))
+
+
+TUNE_GRID_DIV, TUNE_SORT_E, TUNE_MEDIAN_THREADS = 0, 1, 2
+
+
+def sub_set_tuning(ctx, knob: int, value: int):
+    """A launch setting that leaves results unchanged (TUNE_*; value 0: automatic)."""
+    return _check(ctx, lib().sub_set_tuning(ctx, int(knob), int(value)))
 
 
 TEST_SKIP_CATALOG_COPIES = 1

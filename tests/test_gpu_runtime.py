@@ -89,6 +89,29 @@ def test_grid_divisor_does_not_change_results():
             gbsub.sub_set_grid_div(s.ctx, 0)
 
 
+def test_launch_settings_do_not_change_results():
+    T, A, f, fdot = jobs(1, seed=5, n_lo=3e5, n_hi=3e5)[0]
+    for precision in (gbsub.FP64, gbsub.MIXED):
+        kw = dict(window=1000, estimator=gbsub.MEDIAN_MEAN, precision=precision)
+        ref = solo(T, A, f, fdot, **kw)
+        with gbsub.Subtraction(T_obs=T, **kw) as s:
+            s.load(A, f, fdot)
+            for knob, value in ((gbsub.TUNE_SORT_E, 4), (gbsub.TUNE_SORT_E, 8),
+                                (gbsub.TUNE_MEDIAN_THREADS, 256),
+                                (gbsub.TUNE_MEDIAN_THREADS, 64), (gbsub.TUNE_GRID_DIV, 3)):
+                gbsub.sub_set_tuning(s.ctx, knob, value)
+                same((s.run(), s.spectrum(), s.resolved()), ref)
+            for knob, value in ((gbsub.TUNE_SORT_E, 3), (gbsub.TUNE_SORT_E, 16),
+                                (gbsub.TUNE_MEDIAN_THREADS, 100),
+                                (gbsub.TUNE_MEDIAN_THREADS, 1024), (gbsub.TUNE_GRID_DIV, 0), (9, 1)):
+                with pytest.raises(gbsub.SubError):
+                    gbsub.sub_set_tuning(s.ctx, knob, value)
+    # a narrow window: kpad = 64 leaves only two elements per sorting thread
+    with gbsub.Subtraction(T_obs=T, window=30, estimator=gbsub.MEDIAN) as s:
+        with pytest.raises(gbsub.SubError):
+            gbsub.sub_set_tuning(s.ctx, gbsub.TUNE_SORT_E, 4)
+
+
 def serve(js, budget, max_inflight, precision=gbsub.FP64):
     results = {}
     outs = {}
