@@ -6,6 +6,22 @@ sub_get_spectrum, sub_get_resolved_mask, sub_destroy, ...); ``Subtraction`` wrap
 a context for convenience.  Buffers are numpy arrays (host memory) or torch CUDA
 tensors (device memory, passed by data_ptr()).  There is no fallback: if the
 library is missing or a call fails, an exception is raised.
+
+Typical use::
+
+    from paper_2602_18560_gb300 import gbsub, synth
+    with gbsub.Subtraction(T_obs=4 * synth.YEAR, window=1000,
+                           estimator=gbsub.MEDIAN_MEAN) as s:
+        s.load(A, f, fdot)                   # or s.load(..., mapped=True) for pinned
+                                             # host arrays read in place, or
+                                             # s.load_generated(n, seed, population)
+        stats = s.run()                      # iterations, resolved count, ...
+        S_gal = s.spectrum()                 # per bin, from k_lo / T_obs upwards
+        resolved = s.resolved()              # one byte per source
+        S_k, f_k, N_k = s.coarse_grain()     # 100 log-spaced bin averages
+
+Many catalogs at once: ``Batch`` (one graph launch, ``autotune.tune_batch``);
+a request loop: ``Server`` (submit/poll, memory budget, pooled contexts).
 """
 from __future__ import annotations
 
