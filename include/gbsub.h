@@ -400,6 +400,13 @@ int sub_server_submit(sub_server* s, int64_t job_id, double T_obs, const double*
                       const double* f, const double* fdot, int64_t n, double* S_gal,
                       int64_t cap, uint8_t* mask);
 
+/* Queue a job whose catalog is drawn on the device (sub_load_generated, fused): n sources
+ * of the population (gamma, shape) with this seed, so no catalog crosses the host link.
+ * S_gal and mask as for sub_server_submit.  Errors: SUB_EINVAL, SUB_ESTATE. */
+int sub_server_submit_generated(sub_server* s, int64_t job_id, double T_obs, int64_t n,
+                                uint64_t seed, double gamma, double shape, double* S_gal,
+                                int64_t cap, uint8_t* mask);
+
 /* Move up to cap finished jobs into out, waiting up to timeout_ms for the first one
  * (0: no wait).  Returns how many were written. */
 int32_t sub_server_poll(sub_server* s, sub_job_result* out, int32_t cap, int32_t timeout_ms);

@@ -113,7 +113,8 @@ EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_load_gen
            "sub_last_error", "sub_running_mean_noalloc", "sub_get_power", "sub_batch_create",
            "sub_batch_run", "sub_batch_last_ms", "sub_batch_last_error", "sub_batch_destroy",
            "sub_set_grid_div", "sub_set_tuning", "sub_test_hooks", "sub_server_params_default", "sub_server_create",
-           "sub_server_submit", "sub_server_poll", "sub_server_info", "sub_server_last_error",
+           "sub_server_submit", "sub_server_submit_generated", "sub_server_poll",
+           "sub_server_info", "sub_server_last_error",
            "sub_server_prewarm",
            "sub_server_destroy")
 KERNELS = ("prepass", "sort", "median", "prefix", "mean", "snr", "control")
@@ -170,6 +171,8 @@ def lib(build_if_missing: bool = True):
             "sub_server_params_default": (i32, [ctypes.POINTER(sub_server_params)]),
             "sub_server_create": (i32, [ctypes.POINTER(sub_server_params), ctypes.POINTER(P)]),
             "sub_server_submit": (i32, [P, i64, ctypes.c_double, P, P, P, i64, P, i64, P]),
+            "sub_server_submit_generated": (i32, [P, i64, ctypes.c_double, i64, ctypes.c_uint64,
+                                                  ctypes.c_double, ctypes.c_double, P, i64, P]),
             "sub_server_poll": (i32, [P, ctypes.POINTER(sub_job_result), i32, i32]),
             "sub_server_info": (i32, [P, ctypes.POINTER(sub_server_stats)]),
             "sub_server_prewarm": (i32, [P, ctypes.c_double, i64, i32]),
@@ -596,6 +599,24 @@ class Server:
         if rc != OK:
             raise SubError(rc, lib().sub_server_last_error(self.s).decode())
         self._keep[int(job_id)] = (A, f, fdot, S_gal_out, mask_out)
+
+    def submit_generated(self, job_id, T_obs, n, seed, pop=None, S_gal_out=None,
+                         mask_out=None):
+        """Queue a job whose catalog (n sources of population pop, this seed) is drawn on
+        the device; the result buffers are host arrays kept referenced until it returns."""
+        pop = pop if pop is not None else _default_population()
+        ps, ws_, ncap = _ptr(S_gal_out, np.float64)
+        pm, wm, nm = _ptr(mask_out, np.uint8)
+        if (S_gal_out is not None and ws_ != HOST) or (mask_out is not None and wm != HOST):
+            raise ValueError("result buffers must be host memory")
+        if mask_out is not None and nm < n:
+            raise ValueError("mask buffer smaller than the catalog")
+        rc = lib().sub_server_submit_generated(self.s, int(job_id), float(T_obs), int(n),
+                                               int(seed) & (2**64 - 1), float(pop.gamma),
+                                               float(pop.shape), ps, ncap, pm)
+        if rc != OK:
+            raise SubError(rc, lib().sub_server_last_error(self.s).decode())
+        self._keep[int(job_id)] = (S_gal_out, mask_out)
 
     def poll(self, timeout_ms=0, cap=256):
         """Finished jobs: a list of dicts (job_id, status, stats, latency_ms, queue_ms,

@@ -312,3 +312,30 @@ def test_work_counts_follow_the_dirty_chunks():
         assert w["changed"] <= w["tiles"] <= 2 * w["changed"]
         s.run()
         assert s.work() == w
+
+
+def test_server_generated_jobs_equal_each_catalog_alone():
+    # jobs given as population parameters: the catalog is drawn on the device, and every
+    # result equals the same generated catalog run alone on a plain context
+    pops = [synth.population_draw(81, i) for i in range(5)]
+    sizes = [30_000, 250_000, 1, 0, 120_000]
+    T = 2 * synth.YEAR
+    nb = int(np.floor(1e-2 * T)) - int(np.ceil(1e-4 * T)) + 1
+    outs = []
+    with gbsub.Server(max_inflight=3, window=1000, estimator=gbsub.MEDIAN_MEAN) as srv:
+        for i, (n, pop) in enumerate(zip(sizes, pops)):
+            outs.append((np.zeros(nb), np.zeros(max(n, 1), dtype=np.uint8)))
+            srv.submit_generated(i, T, n, 900 + i, pop, *outs[-1])
+        got = []
+        while len(got) < len(sizes):
+            got += srv.poll(timeout_ms=2000)
+        with pytest.raises(gbsub.SubError):
+            srv.submit_generated(99, T, 10, 1, synth.Population(20.0, 2.0))
+    assert all(r["status"] in (gbsub.OK, gbsub.ENOTCONVERGED) for r in got)
+    for i, (n, pop) in enumerate(zip(sizes, pops)):
+        with gbsub.Subtraction(T_obs=T, window=1000, estimator=gbsub.MEDIAN_MEAN) as s:
+            s.load_generated(n, 900 + i, pop, fused=True)
+            s.run()
+            sg, m = s.spectrum(), s.resolved()
+        assert np.array_equal(outs[i][0].view(np.uint64), sg.view(np.uint64))
+        assert np.array_equal(outs[i][1][:n], m)
