@@ -266,6 +266,20 @@ def cpu_oracle_sample(A, f, fdot, T, est, W, iters_hint):
     return dt, est_total, r
 
 
+def single_config(w, args, ws):
+    """The single-catalog workload, the same for both arms of the bench."""
+    nb = int(math.floor(1e-2 * w.T_obs)) - int(math.ceil(1e-4 * w.T_obs)) + 1
+    N = w.n_sources
+    return {"workload": "%s: N_b=%d, T_obs=%g yr, band 0.1-10 mHz, %d bins, power-law "
+                        "gamma=%.3f, Gamma shape=%.3f" % (w.name, N, w.T_obs / synth.YEAR, nb,
+                                                          w.pop.gamma, w.pop.shape),
+            "estimator": args.estimator, "window": args.window, "rho_th": 7.0,
+            "kappa": 1 / 7.0, "precision": args.precision,
+            "l2": ("inputs larger than L2 (catalog %d MB)" if 24 * N > 129 * 2**20 else
+                   "catalog of %d MB fits in L2: not flushed between steps") % (24 * N // 2**20),
+            "parallelism": "replicas" if ws > 1 else "single"}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -296,7 +310,7 @@ def run_reference(args, ws, rank):
             "value": value, "unit": "sources/s", "n_gpus": ws, "steps": steps,
             "warmup": warm, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "estimator": args.estimator, "window": args.window},
+            "config": single_config(w, args, ws),
             "cpu_baseline": {"value": value, "unit": "sources/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "sources/s", "h2d_bytes_per_step": 0,
@@ -566,13 +580,7 @@ def main():
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-        "config": {"workload": "%s: N_b=%d, T_obs=%g yr, band 0.1-10 mHz, %d bins, power-law "
-                               "gamma=%.3f, Gamma shape=%.3f" % (w.name, N, w.T_obs / synth.YEAR,
-                                                                 nb, w.pop.gamma, w.pop.shape),
-                   "estimator": args.estimator, "window": args.window, "rho_th": 7.0,
-                   "kappa": 1 / 7.0, "precision": args.precision,
-                   "l2": "inputs larger than L2 (catalog %d MB)" % (24 * N // 2**20),
-                   "parallelism": "replicas" if ws > 1 else "single"},
+        "config": single_config(w, args, ws),
         "stats": {"iterations": st.iterations, "converged": bool(st.converged),
                   "n_candidates": st.n_candidates, "n_live": st.n_live,
                   "n_exact_snr": st.n_exact, "n_resolved": st.n_resolved,
