@@ -53,6 +53,8 @@ def parse():
                          "precision against sequential FP64 runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="single mode: skip the batch record")
+    ap.add_argument("--no-serve", action="store_true", help="single mode: skip the serve record")
     ap.add_argument("--mode", choices=["single", "batch", "serve", "study"], default="single",
                     help="single catalog (default), 64 catalogs in one launch, serving, or "
                          "the mean-vs-median estimator study")
@@ -208,14 +210,15 @@ def unit_bytes(kernel, Kc, est):
 
 
 def dominant_roofline(dom, kd, tr_all, digest, hbm, hbm_kind, nsm, fmax_mhz):
-    """Roofline of the dominant kernel, per average launch.  kd: its ms_per_run,
-    launches_per_run, units_per_run (None for one-unit kernels) and algorithmic bytes per
-    run; tr_all: profiles/traffic.json for the workload (ncu DRAM bytes and warp instructions
-    per unit of a full first launch, with the digest of the sources captured).
-    The catalog pass and the chunk kernels: algorithmic bytes over the measured HBM peak.
-    The sort and the median: warp instructions over the issue rate (one per scheduler per
-    clock), with their bytes as a secondary view.  traffic: the capture's DRAM bytes scaled
-    to an average launch's units, only when the capture is of the current sources."""
+    """Roofline of the dominant kernel, per average launch, in the algorithmic bytes of the
+    work it was handed (reads of its inputs plus writes of its outputs) over the measured HBM
+    peak.  kd: its ms_per_run, launches_per_run, units_per_run (None for one-unit kernels)
+    and algorithmic bytes per run; tr_all: profiles/traffic.json for the workload (ncu DRAM
+    bytes and warp instructions per unit of a captured launch, with the digest of the
+    sources captured).  traffic: the capture's DRAM bytes scaled to an average launch's
+    units, only when the capture is of the current sources.  The sort and the median are
+    bound by instruction issue on an L2-resident spectrum, so their warp instructions over
+    the issue rate (one per scheduler per clock) are given beside, as issue_view."""
     fresh = tr_all.get(dom, {}).get("kernel_source_sha256") == digest
     per_launch_ms = kd["ms_per_run"] / kd["launches_per_run"]
     bytes_launch = kd["algorithmic_bytes_per_run"] / kd["launches_per_run"]
@@ -227,21 +230,21 @@ def dominant_roofline(dom, kd, tr_all, digest, hbm, hbm_kind, nsm, fmax_mhz):
         t0 = tr_all[dom]["dram_bytes_per_launch"]
         u0 = tr_all[dom].get("units_first_launch")
         traffic = t0 * units_launch / u0 if (u0 and units_launch is not None) else t0
+    out = {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": hbm, "unit": "GB/s",
+           "frac": gbs / hbm, "peak_kind": hbm_kind, "traffic": traffic,
+           "traffic_from": ("ncu capture of the current sources" if fresh else
+                            "none of the current sources"),
+           "algorithmic_bytes_per_launch": bytes_launch, "ms_per_launch": per_launch_ms}
     inst = tr_all.get(dom, {}).get("warp_inst_per_unit")
     if dom in ("sort", "median") and inst is not None and units_launch is not None:
         peak = nsm * 4 * fmax_mhz * 1e6 / 1e9
         achieved = inst * units_launch / (per_launch_ms * 1e-3) / 1e9
-        out = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-               "unit": "G warp-instructions/s", "frac": achieved / peak,
-               "peak_kind": "derived: %d SMs x 4 schedulers x %.0f MHz" % (nsm, fmax_mhz),
-               "hbm_view": {"GB/s": gbs, "frac": gbs / hbm},
-               "instructions_from": "ncu capture of the current sources" if fresh else
-                                    "ncu capture of earlier sources (stale)"}
-    else:
-        out = {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": hbm, "unit": "GB/s",
-               "frac": gbs / hbm, "peak_kind": hbm_kind}
-    out.update({"traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
-                "ms_per_launch": per_launch_ms})
+        out["issue_view"] = {
+            "achieved": achieved, "peak": peak, "unit": "G warp-instructions/s",
+            "frac": achieved / peak,
+            "peak_kind": "derived: %d SMs x 4 schedulers x %.0f MHz" % (nsm, fmax_mhz),
+            "instructions_from": "ncu capture of the current sources" if fresh else
+                                 "ncu capture of earlier sources (stale)"}
     return out
 
 
@@ -253,17 +256,86 @@ def loop_units(kernel, work, est):
     return work[lists[kernel]] if kernel in lists else None
 
 
-def cpu_oracle_sample(A, f, fdot, T, est, W, iters_hint):
-    """The oracle as it stands, one thread: a max_iter = 1 run on the full catalog
-    (the pre-filter, one iteration and the final re-estimate), scaled to a whole run
-    of `iters_hint` iterations as t * iters / 2."""
+def host_cpu():
+    """Model name and core count of the host the bench runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"cpu_model": model, "cores": os.cpu_count()}
+
+
+def _oracle_child(cat_path, T, est, W, out_path, core):
+    """Spawned process: the oracle as it stands, one thread pinned to one core, on the whole
+    catalog until it converges; its result and wall time go to out_path."""
+    try:
+        os.sched_setaffinity(0, {core})
+    except Exception:
+        pass
     import oracle
     oracle.lib()
+    d = np.load(cat_path)
+    A, f, fdot = d["A"], d["f"], d["fdot"]
     t0 = time.perf_counter()
-    r = oracle.run(oracle.make_params(T_obs=T, estimator=est, window=W, max_iter=1), A, f, fdot)
+    r = oracle.run(oracle.make_params(T_obs=T, estimator=est, window=W), A, f, fdot)
     dt = time.perf_counter() - t0
-    est_total = dt * max(1, iters_hint) / 2.0
-    return dt, est_total, r
+    np.savez(out_path, S_gal=r["S_gal"], resolved=r["resolved"], seconds=dt,
+             iterations=r["iterations"], n_resolved=r["n_resolved"],
+             converged=int(r["converged"]))
+
+
+class OracleRun:
+    """The oracle on the whole workload, to convergence, in a spawned process on one host
+    core while the GPU legs run (it takes a minute or two; timing it alone would add that to
+    the bench)."""
+
+    def __init__(self, A, f, fdot, T, est, W):
+        import multiprocessing as mp
+        self.dir = tempfile.mkdtemp(prefix="gbsub_oracle_")
+        self.cat = os.path.join(self.dir, "cat.npz")
+        self.out = os.path.join(self.dir, "out.npz")
+        np.savez(self.cat, A=A, f=f, fdot=fdot)
+        ncore = os.cpu_count() or 1
+        self.core = ncore - 1
+        ctx = mp.get_context("spawn")
+        self.proc = ctx.Process(target=_oracle_child,
+                                args=(self.cat, T, est, W, self.out, self.core), daemon=True)
+        self.proc.start()
+
+    def result(self, timeout=1800):
+        self.proc.join(timeout)
+        try:
+            if self.proc.is_alive():
+                self.proc.terminate()
+                return None
+            if self.proc.exitcode != 0 or not os.path.exists(self.out):
+                return None
+            d = np.load(self.out)
+            return {k: d[k] for k in d.files}
+        finally:
+            for name in (self.cat, self.out):
+                try:
+                    os.unlink(name)
+                except OSError:
+                    pass
+            try:
+                os.rmdir(self.dir)
+            except OSError:
+                pass
 
 
 def single_config(w, args, ws):
@@ -281,38 +353,35 @@ def single_config(w, args, ws):
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: there is no reference program, only the paper, so the FP64 oracle
+    as it stands is timed on the host: the whole workload to convergence, one thread, one
+    step (a run takes a minute or two on one core, so the step count is capped at one and
+    no warm-up run is made: the oracle keeps no state between runs)."""
     if rank != 0:
         return
     w = synth.workload(args.workload)
     A, f, fdot = synth.catalog(w.n_sources, w.seed, w.pop)
     est = EST[args.estimator]
-    iters = 16
+    import oracle
+    oracle.lib()
     try:
-        with open(GOLDEN) as fh:
-            g = json.load(fh)
-        key = {2: "median_mean", 0: "mean"}.get(est)
-        if key and g["workload"] == w.name:
-            iters = g["estimators"][key]["iterations"]
+        os.sched_setaffinity(0, {(os.cpu_count() or 1) - 1})
     except Exception:
         pass
-    times = []
-    steps = min(args.steps, 3)  # each oracle step is a bounded sample of ~10-20 s
-    warm = min(args.warmup, 1)
-    for i in range(warm + steps):
-        dt, tot, _ = cpu_oracle_sample(A, f, fdot, w.T_obs, est, args.window, iters)
-        if i >= warm:
-            times.append(tot)
-    t = sum(times) / len(times)
+    t0 = time.perf_counter()
+    r = oracle.run(oracle.make_params(T_obs=w.T_obs, estimator=est, window=args.window),
+                   A, f, fdot)
+    t = time.perf_counter() - t0
     value = w.n_sources / t
-    sample = ("oracle (1 thread) with max_iter=1 on the full %s catalog, i.e. pre-filter + one "
-              "iteration + final re-estimate, scaled by iterations/2 = %d/2" % (w.name, iters))
+    sample = ("the whole %s catalog to convergence (%d iterations, %d resolved), one thread "
+              "pinned to one core, %.1f s" % (w.name, r["iterations"], r["n_resolved"], t))
     line = {"impl": "reference", "metric": "sources subtracted/sec to convergence",
-            "value": value, "unit": "sources/s", "n_gpus": ws, "steps": steps,
-            "warmup": warm, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "value": value, "unit": "sources/s", "n_gpus": ws, "steps": 1,
+            "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": single_config(w, args, ws),
             "cpu_baseline": {"value": value, "unit": "sources/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_cpu()},
             "e2e": {"value": value, "unit": "sources/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -352,6 +421,10 @@ def main():
     A, f, fdot = synth.catalog(w.n_sources, seed, w.pop)
     N = w.n_sources
     est = EST[args.estimator]
+    # the oracle on this catalog, to convergence, on one host core while the GPU legs run
+    orc = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        orc = OracleRun(A, f, fdot, w.T_obs, est, args.window)
     stream = torch.cuda.Stream()
     prm = gbsub.sub_params_default(T_obs=w.T_obs, window=args.window, estimator=est,
                                    precision=0 if args.precision == "fp64" else 1)
@@ -562,14 +635,59 @@ def main():
                           "api": "sub_load_catalog(SUB_HOST, pinned): three copies, then the run",
                           "same_bits_as_resident_run": same_c}}
 
+    # ---------------------------------------------------------------- FP32 screen, measured
+    screen = None
+    try:
+        chk = sub.snr_check()
+        ex = chk["exact"]
+        ok = ex > 0
+        err = np.abs(chk["screen"][ok].astype(np.float64) / ex[ok] - 1.0)
+        bound = 2.2e-6 + 2e-7 * chk["nbins"][ok]
+        screen = {"candidates": int(ok.sum()), "max_rel_err": float(err.max()) if ok.any() else 0.0,
+                  "max_err_over_bound": float((err / bound).max()) if ok.any() else 0.0,
+                  "bound": "2.2e-6 + 2e-7 per bin (the exact FP64 recomputation takes every "
+                           "decision within twice it)"}
+    except Exception as exc:  # reported, not fatal
+        screen = {"error": str(exc)}
+
+    # ---------------------------------------------------------------- batched and served records
+    batch = serve = None
+    if ws == 1 and not args.no_batch:
+        try:
+            batch = batch_record(args, est, steps=max(5, min(args.steps, 20)))
+        except Exception as exc:  # reported, not fatal
+            batch = {"error": repr(exc)}
+    if ws == 1 and not args.no_serve:
+        try:
+            serve = serve_record(args, est, njobs=min(args.jobs, 2000), rate=args.rate)
+        except Exception as exc:  # reported, not fatal
+            serve = {"error": repr(exc)}
+
     # ---------------------------------------------------------------- CPU baseline (oracle)
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        dt, tot, _ = cpu_oracle_sample(A, f, fdot, w.T_obs, est, args.window, st.iterations)
-        cpu = {"value": N / tot, "unit": "sources/s", "cores": 1, "kind": "oracle",
-               "sample": "oracle (1 thread) with max_iter=1 on the full catalog: pre-filter, one "
-                         "iteration and the final re-estimate took %.1f s; scaled to the run's %d "
-                         "iterations as t*%d/2" % (dt, st.iterations, st.iterations)}
+    if orc is not None:
+        r = orc.result()
+        if r is None:
+            cpu = {"error": "the oracle run did not finish"}
+        else:
+            t_orc = float(r["seconds"])
+            cpu = {"value": N / t_orc, "unit": "sources/s", "cores": 1, "kind": "oracle",
+                   "sample": "the whole catalog to convergence (%d iterations, %d resolved), one "
+                             "thread pinned to host core %d, %.1f s, run while the GPU legs ran"
+                             % (int(r["iterations"]), int(r["n_resolved"]), orc.core, t_orc),
+                   "host": host_cpu()}
+            # parity of the timed run against this oracle run, on every bin
+            ref = r["S_gal"]
+            nz = ref != 0
+            full = {"against": "the oracle run above (every bin)",
+                    "S_gal_max_rel_err": float(np.max(np.abs(sg[nz] - ref[nz]) / ref[nz]))
+                    if nz.any() else 0.0,
+                    "zeros_match": bool(np.all(sg[~nz] == 0)),
+                    "resolved_disagreement": int(np.sum(res.astype(bool) != r["resolved"])),
+                    "iterations_match": int(r["iterations"]) == st.iterations}
+            if parity is None:
+                parity = {}
+            parity["full_oracle_run"] = full
 
     # per run: work lists, catalog pass, replica fold; then the iterations (and a final
     # estimate when max_iter stops the loop)
@@ -583,10 +701,12 @@ def main():
         "config": single_config(w, args, ws),
         "stats": {"iterations": st.iterations, "converged": bool(st.converged),
                   "n_candidates": st.n_candidates, "n_live": st.n_live,
-                  "n_exact_snr": st.n_exact, "n_resolved": st.n_resolved,
+                  "n_exact_snr": st.n_exact, "n_near_threshold": st.n_near,
+                  "n_uncertain_fp32": st.n_uncertain, "n_resolved": st.n_resolved,
                   "resolved_per_iteration": [int(x) for x in sub.history()],
                   "prepass_ms": pre_ms, "loop_ms": loop_ms},
         "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "fp32_screen": screen, "batch": batch, "serve": serve,
         "coarse_grain": cg, "generated": gen,
         "gpu_launches": launches, "parity": parity,
     }
@@ -616,228 +736,225 @@ def batch_specs(rank):
     return specs
 
 
-def run_batch(args, ws, rank, local_rank):
-    specs = batch_specs(rank)
-    cats = synth.catalogs_parallel([(n, sd, pop) for n, sd, pop, _ in specs])
+def batch_record(args, est, steps, rank=0):
+    """64 catalogs drawn on the device (materialised once), three ways: 64 sequential plain
+    FP64 runs (the per-catalog path), one FP64 batch launch and one mixed-precision batch
+    launch, each batch with autotuned launch settings.  Rates in catalogs/s; the batches'
+    results against the sequential FP64 runs."""
     import torch
-    torch.cuda.set_device(local_rank)
-    pg = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-        pg = dist
     from paper_2602_18560_gb300 import autotune, gbsub
-    est = EST[args.estimator]
-    prec = 0 if args.precision == "fp64" else 1
+    specs = batch_specs(rank)
+    ntot = sum(n for n, _, _, _ in specs)
 
     def contexts(precision):
         subs = []
-        for (n, sd, pop, T), (A, f, fd) in zip(specs, cats):
-            s = gbsub.Subtraction(T_obs=T, window=args.window, estimator=est, precision=precision)
-            s.load(A, f, fd)
+        for n, sd, pop, T in specs:
+            s = gbsub.Subtraction(T_obs=T, window=args.window, estimator=est,
+                                  precision=precision)
+            s.load_generated(n, sd, pop, fused=False)
             subs.append(s)
         return subs
 
-    # 64 sequential plain-FP64 runs (the per-catalog GPU path), catalogs resident
-    seq = contexts(0)
-    for s in seq:
+    out = {"workload": "64 catalogs drawn on the device, N_b log-uniform in [1e5, 1e7] (total "
+                       "%d sources), T_obs = 4 yr, populations gamma~U(3,4.5), shape~U(1.5,3)"
+                       % ntot,
+           "launch": "one CUDA graph per batch, launch settings autotuned per arm",
+           "l2": "inputs larger than L2 (catalogs %d MB)" % (24 * ntot // 2**20)}
+    fp = contexts(gbsub.FP64)
+    for s in fp:
         s.run()
     torch.cuda.synchronize()
     reps = 3
     t0 = time.perf_counter()
     for _ in range(reps):
-        for s in seq:
+        for s in fp:
             gbsub.sub_run(s.ctx, wait=True)
     seq_s = (time.perf_counter() - t0) / reps
-    seq_ref = [(s.spectrum(), s.resolved()) for s in seq]
-    for s in seq:
-        s.close()
+    ref = [(s.spectrum(), s.resolved()) for s in fp]
+    out["sequential_fp64"] = {"catalogs_per_s": 64 / seq_s, "ms_per_64": seq_s * 1e3,
+                              "api": "sub_run per catalog, one after another"}
+    arms = {}
+    for name, subs in (("fp64", fp), ("mixed", contexts(gbsub.MIXED))):
+        b = gbsub.Batch(subs)
+        settings, tuning = autotune.tune_batch(b, subs)
+        for _ in range(3):
+            b.run()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            sts = b.run()
+            times.append(b.last_ms)
+        ms = sum(times) / len(times)
+        worst, ndiff, nres, same = 0.0, 0, 0, True
+        for sub, (sg_ref, m_ref) in zip(subs, ref):
+            sg, m = sub.spectrum(), sub.resolved()
+            same = same and np.array_equal(sg.view(np.uint64), sg_ref.view(np.uint64)) \
+                and np.array_equal(m, m_ref)
+            nz = sg_ref != 0
+            if nz.any():
+                worst = max(worst, float(np.max(np.abs(sg[nz] - sg_ref[nz]) / sg_ref[nz])))
+            ndiff += int(np.sum(m != m_ref))
+            nres += int(m_ref.sum())
+        arms[name] = {"catalogs_per_s": 64 / (ms * 1e-3), "ms_per_batch": ms,
+                      "speedup_over_sequential_fp64": seq_s * 1e3 / ms,
+                      "settings": settings, "ms_by_setting": tuning,
+                      "iterations_min": min(st.iterations for st in sts),
+                      "iterations_max": max(st.iterations for st in sts),
+                      "vs_sequential_fp64": {"bit_identical": same, "S_gal_max_rel_err": worst,
+                                             "resolved_disagreement": ndiff,
+                                             "resolved_total": nres,
+                                             "n_uncertain_fp32": int(sum(st.n_uncertain
+                                                                         for st in sts))}}
+        b.close()
+        if subs is not fp:
+            for sub in subs:
+                sub.close()
+    for sub in fp:
+        sub.close()
+    out.update(arms)
+    out["tolerance"] = {"fp64": "bit-identical to the sequential FP64 runs",
+                        "mixed": {"S_gal_rel": 1e-5, "resolved_disagreement_frac": 1e-4}}
+    return out
 
-    # the batch: mixed precision (or fp64), autotuned launch settings, one graph launch
-    subs = contexts(prec)
-    batch = gbsub.Batch(subs)
-    settings, tuning = autotune.tune_batch(batch, subs)
-    for _ in range(max(3, args.warmup)):
-        batch.run()
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    times = []
+
+def run_batch(args, ws, rank, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    est = EST[args.estimator]
     with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
-            sts = batch.run()
-            times.append(batch.last_ms)
-    ms = sum(times) / len(times)
-    ms = max_over_ranks(ms, pg, "cuda")
-    value = whole_job_rate(ws, 64, ms * 1e-3)
-
-    # accuracy of the batch against the sequential FP64 runs (whose oracle parity the
-    # tests establish)
-    worst, ndiff, nres = 0.0, 0, 0
-    for s, (sg_ref, m_ref) in zip(subs, seq_ref):
-        sg = s.spectrum()
-        nz = sg_ref != 0
-        if nz.any():
-            worst = max(worst, float(np.max(np.abs(sg[nz] - sg_ref[nz]) / sg_ref[nz])))
-        ndiff += int(np.sum(s.resolved() != m_ref))
-        nres += int(m_ref.sum())
-    ntot = sum(n for n, _, _, _ in specs)
-    iters = [st.iterations for st in sts]
-    batch.close()
-    for s in subs:
-        s.close()
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        # the oracle on the smallest catalog of the batch, scaled by size to the batch's mean
-        k = int(np.argmin([n for n, _, _, _ in specs]))
-        A, f, fd = cats[k]
-        dt, tot, _ = cpu_oracle_sample(A, f, fd, specs[k][3], est, args.window, iters[k])
-        per_src = tot / specs[k][0]
-        cpu = {"value": 1.0 / (per_src * ntot / 64), "unit": "catalogs/s", "cores": 1,
-               "kind": "oracle",
-               "sample": "oracle (1 thread) max_iter=1 run on the batch's smallest catalog "
-                         "(N=%d, %.1f s), scaled to its %d iterations and linearly in N to the "
-                         "batch's mean size" % (specs[k][0], dt, iters[k])}
-    line = {
-        "metric": "batched catalogs/s", "value": value, "unit": "catalogs/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == 0 else "f64+f32", "data": "synthetic",
-        "config": {"workload": "64 catalogs per GPU, N_b log-uniform in [1e5, 1e7] "
-                               "(total %d sources), T_obs = 4 yr, populations drawn "
-                               "gamma~U(3,4.5), shape~U(1.5,3)" % ntot,
-                   "estimator": args.estimator, "window": args.window,
-                   "precision": args.precision, "launch": "one CUDA graph per batch",
-                   "l2": "inputs larger than L2 (catalogs %d MB)" % (24 * ntot // 2**20),
-                   "parallelism": "replicas" if ws > 1 else "single"},
-        "baseline_sequential_fp64": {"catalogs_per_s": 64 / seq_s, "ms_per_64": seq_s * 1e3,
-                                     "speedup_of_batch": value / ws / (64 / seq_s)},
-        "autotune": {"settings": settings, "ms_by_setting": tuning},
-        "accuracy_vs_fp64": {"S_gal_max_rel_err": worst, "resolved_disagreement": ndiff,
-                             "resolved_total": nres,
-                             "tolerance": {"S_gal_rel": 1e-5,
-                                           "resolved_disagreement_frac": 1e-4}},
-        "stats": {"iterations_min": min(iters), "iterations_max": max(iters)},
-        "cpu_baseline": cpu, "e2e": None, "gpu_launches": None,
-    }
-    line["clocks"] = clk.summary()
+        rec = batch_record(args, est, args.steps, rank)
+    head = rec["mixed" if args.precision == "mixed" else "fp64"]
+    ms = head["ms_per_batch"]
+    if ws > 1:
+        import torch.distributed as dist
+        ms = max_over_ranks(ms, dist, "cuda")
+    line = {"metric": "batched catalogs/s", "value": whole_job_rate(ws, 64, ms * 1e-3),
+            "unit": "catalogs/s", "n_gpus": ws, "steps": args.steps, "warmup": 3,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic (drawn on the device)",
+            "config": {"workload": rec["workload"], "estimator": args.estimator,
+                       "window": args.window, "precision": args.precision,
+                       "l2": rec["l2"], "parallelism": "replicas" if ws > 1 else "single"},
+            "batch": rec, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+            "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if pg:
-        pg.destroy_process_group()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 # ============================================================================ serving
 
-def run_serve(args, ws, rank, local_rank):
-    """Poisson arrivals at --rate jobs/s, --jobs jobs, N log-uniform in [1e5, 3e7], T_obs from
-    {1, 2, 4} yr; each job's catalog is the first N sources of one of 8 pool catalogs, each
-    with its own population drawn from the full-scale ranges."""
-    npool = 8
-    pool_pops = [synth.population_draw(SERVE_SEED, 1000 + k) for k in range(npool)]
-    nmax = 30_000_000
-    cats = synth.catalogs_parallel([(nmax, SERVE_SEED * 1000003 + k, pool_pops[k])
-                                    for k in range(npool)])
+def serve_jobs(njobs, rank=0):
+    """(n, T_obs, seed, population) of every job: N log-uniform in [1e5, 3e7], T_obs from
+    {1, 2, 4} yr, each job's population drawn from the full-scale ranges."""
     jobs = []
-    for i in range(args.jobs):
-        n, T, _ = synth.job_draw(SERVE_SEED, 2000 * rank + i)
-        jobs.append((min(n, nmax), T, i % npool))
-    rng = np.random.default_rng(SERVE_SEED + rank)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, args.jobs))
+    for i in range(njobs):
+        j = 100000 * rank + i
+        n, T, _ = synth.job_draw(SERVE_SEED, j)
+        jobs.append((min(n, 30_000_000), T, SERVE_SEED * 1000003 + j,
+                     synth.population_draw(SERVE_SEED, j)))
+    return jobs
+
+
+def serve_record(args, est, njobs, rate, rank=0):
+    """Served subtraction jobs whose catalogs are drawn on the device from each job's own
+    population parameters: Poisson arrivals at `rate` jobs/s (p50/p99 latency from the
+    scheduled arrival to the results in pinned host buffers), and the same jobs all offered
+    at once (the largest sustainable rate, catalogs/s), in FP64 and in mixed precision."""
     import torch
-    torch.cuda.set_device(local_rank)
-    pg = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-        pg = dist
     from paper_2602_18560_gb300 import gbsub
-    pinned = [tuple(torch.from_numpy(x).pin_memory().numpy() for x in c) for c in cats]
-    del cats
+    jobs = serve_jobs(njobs, rank)
+    rng = np.random.default_rng(SERVE_SEED + rank)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, njobs))
     nslots = 48
+    nmax = max(n for n, _, _, _ in jobs)
     nb_max = int(np.floor(1e-2 * 4 * synth.YEAR)) - int(np.ceil(1e-4 * 4 * synth.YEAR)) + 1
     outs = [(torch.empty(nb_max, dtype=torch.float64).pin_memory().numpy(),
              torch.empty(nmax, dtype=torch.uint8).pin_memory().numpy()) for _ in range(nslots)]
-    est = EST[args.estimator]
 
-    def serve_once(precision):
+    def serve_once(precision, paced):
         free = list(range(nslots))
-        held = {}
-        lat, done, first_arr = {}, 0, None
+        held, lat, submit_at = {}, {}, {}
+        done, i, t_end = 0, 0, None
         srv = gbsub.Server(hbm_budget=120 * 10**9, max_inflight=32, max_contexts=24,
                            window=args.window, estimator=est, precision=precision)
-        # contexts (device memory, tables, graphs) are made before traffic arrives
         for years in (1, 2, 4):
             srv.prewarm(years * synth.YEAR, nmax, 8)
         t_base = time.perf_counter()
-        submit_at = {}
-        i = 0
-        t_end = None
-        while done < len(jobs):
+        arr = arrivals if paced else np.zeros(njobs)
+        while done < njobs:
             now = time.perf_counter() - t_base
-            while i < len(jobs) and arrivals[i] <= now and free:
-                n, T, k = jobs[i]
+            while i < njobs and arr[i] <= now and free:
+                n, T, sd, pop = jobs[i]
                 slot = free.pop()
                 sg, m = outs[slot]
-                A, f, fd = pinned[k]
                 nb = int(np.floor(1e-2 * T)) - int(np.ceil(1e-4 * T)) + 1
-                srv.submit(i, T, A[:n], f[:n], fd[:n], sg[:nb], m[:n])
+                srv.submit_generated(i, T, n, sd, pop, sg[:nb], m[:max(n, 1)])
                 submit_at[i] = time.perf_counter() - t_base
                 held[i] = slot
                 i += 1
                 now = time.perf_counter() - t_base
-            for r in srv.poll(timeout_ms=0 if i < len(jobs) else 5):
+            for r in srv.poll(timeout_ms=0 if i < njobs else 5):
                 j = r["job_id"]
                 if r["status"] not in (0, gbsub.ENOTCONVERGED):
                     raise RuntimeError("job %d failed with %d" % (j, r["status"]))
-                lat[j] = (submit_at[j] - arrivals[j]) * 1e3 + r["latency_ms"]
+                lat[j] = (submit_at[j] - arr[j]) * 1e3 + r["latency_ms"]
                 free.append(held.pop(j))
                 done += 1
                 t_end = time.perf_counter() - t_base
-            if i < len(jobs) and (not free or arrivals[i] > now):
-                time.sleep(min(1e-4, max(0.0, arrivals[i] - now)) if free else 1e-4)
+            if i < njobs and (not free or arr[i] > now):
+                time.sleep(min(1e-4, max(0.0, arr[i] - now)) if free else 1e-4)
         info = srv.info()
         srv.close()
-        v = np.array([lat[j] for j in range(len(jobs))])
+        v = np.array([lat[j] for j in range(njobs)])
         return {"p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99)),
-                "mean_ms": float(v.mean()), "catalogs_per_s": len(jobs) / t_end,
-                "wall_s": t_end, "peak_device_bytes": info["peak_device_bytes"],
+                "mean_ms": float(v.mean()), "catalogs_per_s": njobs / t_end, "wall_s": t_end,
+                "peak_device_bytes": info["peak_device_bytes"],
                 "contexts_created": info["contexts_created"]}
 
+    out = {"workload": "%d jobs, catalogs drawn on the device, N_b log-uniform in [1e5, 3e7] "
+                       "(total %d sources), T_obs in {1, 2, 4} yr, each job's population "
+                       "gamma~U(3,4.5), shape~U(1.5,3)" % (njobs, sum(n for n, _, _, _ in jobs)),
+           "admission": "120 GB budget, 32 in flight, a pool of 24 contexts (8 per T_obs) "
+                        "prewarmed before traffic",
+           "latency": "scheduled arrival -> results in pinned host buffers",
+           "offered_jobs_per_s": rate}
+    for name, prec in (("fp64", gbsub.FP64), ("mixed", gbsub.MIXED)):
+        out[name] = {"paced": serve_once(prec, True), "saturated": serve_once(prec, False)}
+        out[name]["max_sustainable_catalogs_per_s"] = out[name]["saturated"]["catalogs_per_s"]
+    return out
+
+
+def run_serve(args, ws, rank, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    est = EST[args.estimator]
     with ClockSampler(local_rank) as clk:
-        res = {"mixed" if args.precision == "mixed" else "fp64":
-               serve_once(0 if args.precision == "fp64" else 1)}
-        other = "fp64" if args.precision == "mixed" else "mixed"
-        res[other] = serve_once(1 if other == "mixed" else 0)
-    head = res[args.precision if args.precision == "mixed" else "fp64"]
-    ntot = sum(n for n, _, _ in jobs)
-    line = {
-        "metric": "served p50/p99 latency", "value": head["p99_ms"], "unit": "ms (p99)",
-        "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "n_gpus": ws,
-        "steps": args.jobs, "warmup": 0, "ms_per_step": head["mean_ms"],
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-        "config": {"workload": "%d jobs, Poisson %.0f jobs/s offered, N_b log-uniform in "
-                               "[1e5, 3e7] (total %d sources), T_obs in {1, 2, 4} yr, 8 "
-                               "populations from gamma~U(3,4.5), shape~U(1.5,3)"
-                               % (args.jobs, args.rate, ntot),
-                   "estimator": args.estimator, "window": args.window,
-                   "precision": args.precision,
-                   "admission": "120 GB budget, 32 in flight, a pool of 24 contexts (8 per "
-                                "T_obs) prewarmed before traffic",
-                   "latency": "scheduled arrival -> results in pinned host buffers",
-                   "parallelism": "replicas" if ws > 1 else "single"},
-        "serving": res, "cpu_baseline": None,
-        "e2e": {"value": head["p99_ms"], "unit": "ms (p99)",
-                "h2d_bytes_per_step": 24 * ntot // args.jobs,
-                "d2h_bytes_per_step": None},
-        "gpu_launches": None,
-    }
-    line["clocks"] = clk.summary()
+        rec = serve_record(args, est, args.jobs, args.rate, rank)
+    head = rec["mixed" if args.precision == "mixed" else "fp64"]["paced"]
+    line = {"metric": "served p50/p99 latency", "value": head["p99_ms"], "unit": "ms (p99)",
+            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "n_gpus": ws,
+            "steps": args.jobs, "warmup": 0, "ms_per_step": head["mean_ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic (drawn on the device)",
+            "config": {"workload": rec["workload"], "estimator": args.estimator,
+                       "window": args.window, "precision": args.precision,
+                       "admission": rec["admission"], "latency": rec["latency"],
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "serving": rec, "cpu_baseline": None,
+            "e2e": {"value": head["p99_ms"], "unit": "ms (p99)", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": None},
+            "gpu_launches": None, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if pg:
-        pg.destroy_process_group()
+
 
 def run_study(args, ws, rank, local_rank):
     """Mean vs median estimators (App. E, Table III): the same catalog of the workload's

@@ -104,6 +104,13 @@ typedef struct {
                           /* (rho <= rho_0 because S_n >= S_instr; the others are    */
                           /* never tested again)                                     */
   int64_t n_exact;        /* SNR decisions recomputed in FP64 (SUB_FP64)             */
+  int64_t n_near;         /* SNR decisions taken in FP64 (SUB_FP64, SUB_FP64_STRICT) */
+                          /* on a rho with |rho - rho_th| / rho_th < 1e-9, counted   */
+                          /* over (candidate, iteration): the decisions that FP64    */
+                          /* rounding order alone could flip.  0 in SUB_MIXED.       */
+  int64_t n_uncertain;    /* SUB_MIXED: FP32 decisions whose value lies inside the   */
+                          /* FP32 screen's error bound around rho_th^2 (FP64 could   */
+                          /* decide them differently).  0 in the FP64 modes.         */
 } sub_stats;
 
 typedef struct sub_ctx sub_ctx;
@@ -258,6 +265,22 @@ int sub_get_work(sub_ctx* ctx, int64_t* work, int32_t n);
 int sub_profile(sub_ctx* ctx, float ms[SUB_K_COUNT], int32_t launches[SUB_K_COUNT],
                 sub_stats* stats);
 
+/* Both evaluations of rho^2 (Eqs. SNR inner product / inner product; App. D) for every kept
+ * candidate (rho_0 > rho_th, see sub_stats.n_live) against the S_gal of the last run, for
+ * measuring the FP32 screen that SUB_FP64 decides on first:
+ *   src[i]         : the candidate's index in the catalog
+ *   rho2_screen[i] : rho^2 in FP32 as the screen evaluates it (through 1 / (1 + S_gal/S_instr)
+ *                    of the last estimate, in FP32)
+ *   rho2_exact[i]  : rho^2 in FP64, summed in the oracle's order (the value SUB_FP64 decides
+ *                    on when the screen cannot)
+ *   nbins[i]       : bins of the band the screen summed (its error bound grows with them)
+ * All four are host arrays of cap entries; *n_out (may be null) receives the count.  The
+ * call allocates and frees a temporary device buffer of 24 bytes per candidate and
+ * synchronises.  Errors: SUB_EINVAL (cap below the count, null output), SUB_ESTATE (no run
+ * yet), SUB_ENOMEM, SUB_EBUDGET, SUB_ECUDA. */
+int sub_snr_check(sub_ctx* ctx, int64_t* src, float* rho2_screen, double* rho2_exact,
+                  int32_t* nbins, int64_t cap, int64_t* n_out);
+
 /* Largest inputs of sub_running_mean_noalloc (the size of its static scratch). */
 #define SUB_NOALLOC_MAX_BINS 1310720
 #define SUB_NOALLOC_MAX_WINDOW 8192
@@ -276,9 +299,11 @@ int sub_profile(sub_ctx* ctx, float ms[SUB_K_COUNT], int32_t launches[SUB_K_COUN
  * Scratch lives in one static device array of about 21 MB that every GPU loading
  * the library holds until the process exits.  The first call on a device (with
  * that device current) looks up the array's device address; make that first call
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents: calls that overlap on the GPU race and must be serialised by
- * the caller.  Sizes beyond the limits return SUB_EINVAL with a message in
+ * before any stream capture.  The address is kept for the life of the process, so a
+ * caller that resets a device (cudaDeviceReset) must not call this entry point on
+ * that device afterwards; devices 0 .. 127 only.  All calls share the array and it
+ * keeps the last call's contents: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Sizes beyond the limits return SUB_EINVAL with a message in
  * sub_last_error(NULL); CUDA failures return SUB_ECUDA. */
 int sub_running_mean_noalloc(const double* x, double* out, int64_t n, int32_t window,
                              void* stream);

@@ -650,6 +650,8 @@ static int fill_stats(sub_ctx* c, sub_stats* st) {
     st->reserved = 0;
     st->n_live = (int64_t)r.nlive;
     st->n_exact = (int64_t)r.nexact;
+    st->n_near = (int64_t)r.nnear;
+    st->n_uncertain = (int64_t)r.nuncertain;
   }
   return status;
 }
@@ -931,6 +933,37 @@ extern "C" int sub_profile(sub_ctx* c, float ms[SUB_K_COUNT], int32_t launches[S
     if (launches) launches[k] = c->prof_n[k];
   }
   return fill_stats(c, st);
+}
+
+extern "C" int sub_snr_check(sub_ctx* c, int64_t* src, float* rho2_screen, double* rho2_exact,
+                             int32_t* nbins, int64_t cap, int64_t* n_out) {
+  if (!c) return SUB_EINVAL;
+  if (!c->ran) { set_err(c, "no run yet"); return SUB_ESTATE; }
+  CU(cudaMemcpyAsync(c->h_rs, c->rs, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream), c);
+  CU(cudaStreamSynchronize(c->stream), c);
+  const int64_t m = (int64_t)c->h_rs->nlive;
+  if (n_out) *n_out = m;
+  if (cap < m) { set_err(c, "cap %lld < kept candidates %lld", (long long)cap, (long long)m); return SUB_EINVAL; }
+  if (m == 0) return SUB_OK;
+  if (!src || !rho2_screen || !rho2_exact || !nbins) { set_err(c, "null output"); return SUB_EINVAL; }
+  void* buf = nullptr;
+  int rc = dalloc(c, &buf, (size_t)m * 24);
+  if (rc) return rc;
+  long long* d_src = (long long*)buf;
+  double* d_ex = (double*)(d_src + m);
+  float* d_sc = (float*)(d_ex + m);
+  int* d_k = (int*)(d_sc + m);
+  launch_snr_check(c->cd, m, c->grid, tables_of(c), c->Sg, c->inv_f, c->rs, d_src, d_sc, d_ex, d_k,
+                   c->stream);
+  cudaError_t e = cudaGetLastError();
+  if (!e) e = cudaMemcpyAsync(src, d_src, (size_t)m * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaMemcpyAsync(rho2_exact, d_ex, (size_t)m * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaMemcpyAsync(rho2_screen, d_sc, (size_t)m * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaMemcpyAsync(nbins, d_k, (size_t)m * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  dfree(c, buf);
+  if (e) { set_err(c, "sub_snr_check: %s", cudaGetErrorString(e)); return SUB_ECUDA; }
+  return SUB_OK;
 }
 
 extern "C" int64_t sub_device_bytes(const sub_ctx* c) { return c ? c->bytes : 0; }

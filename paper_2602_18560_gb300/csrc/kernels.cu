@@ -1617,14 +1617,32 @@ __device__ __forceinline__ float screen_part(const Cands& cd, long long c, const
   return r2;
 }
 
+// Margin of the screen: the FP32 value is within this relative distance of the FP64 one
+// (the bound above, doubled, for kcount bins).
+__device__ __forceinline__ float screen_margin(int kcount) {
+  return 1e-5f + 4e-7f * (float)kcount;
+}
+
 // Decision from the FP32 value: 1 resolve, 0 keep, -1 too close to rho_th to tell (the
 // caller then computes rho^2 exactly).
 __device__ __forceinline__ int screen_decide(float r2, int kcount, float th2f, int mode) {
   if (mode == 1) return r2 > th2f ? 1 : 0;
-  float m = 1e-5f + 4e-7f * (float)kcount;
+  float m = screen_margin(kcount);
   if (mode == 0 && r2 > th2f * (1.0f + m)) return 1;
   if (mode == 0 && r2 < th2f * (1.0f - m)) return 0;
   return -1;
+}
+
+// An FP32 decision (mixed precision) that the FP64 value could take the other way.
+__device__ __forceinline__ bool screen_uncertain(float r2, int kcount, float th2f) {
+  const float m = screen_margin(kcount);
+  return r2 <= th2f * (1.0f + m) && r2 >= th2f * (1.0f - m);
+}
+
+// An FP64 value of rho^2 with |rho - rho_th| / rho_th < 1e-9, i.e. |rho^2 / rho_th^2 - 1|
+// below 2e-9 (to first order): a decision that the order of the FP64 roundings could flip.
+__device__ __forceinline__ bool near_threshold(double r2, double th2) {
+  return fabs(__dsub_rn(r2, th2)) < __dmul_rn(2e-9, th2);
 }
 
 // Remove the parts of candidate c that the catalog pass deposited: bins k0 + off,
@@ -1675,7 +1693,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const float th2f = (float)th2;
-  unsigned local_new = 0, local_exact = 0;
+  unsigned local_new = 0, local_exact = 0, local_near = 0, local_unc = 0;
   // group grp holds candidates grp, grp + ngroups, grp + 2 ngroups, ...: candidates that
   // sit together in the list (the catalog pass emits the long sweeps of its FP64 path in
   // runs) are spread over many warps
@@ -1702,9 +1720,12 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
       int kcount;
       const float r2 = screen_part(cd, c, pk, g, tb, inv_f, 0, 1, kcount);
       int dec = screen_decide(r2, kcount, th2f, mode);
+      if (mode == 1 && screen_uncertain(r2, kcount, th2f)) ++local_unc;
       if (dec < 0) {
         ++local_exact;
-        dec = rho2_exact(g, tb, Sg, cd.a2[c], cd.lo[c], cd.hi[c]) > th2;
+        const double ex = rho2_exact(g, tb, Sg, cd.a2[c], cd.lo[c], cd.hi[c]);
+        if (near_threshold(ex, th2)) ++local_near;
+        dec = ex > th2;
       }
       if (dec) {
         cd.res[c] = 1;
@@ -1725,12 +1746,15 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
         kcount += __shfl_xor_sync(0xFFFFFFFFu, kcount, o);
       }
       int dec = screen_decide(r2, kcount, th2f, mode);
+      if (mode == 1 && lane == 0 && screen_uncertain(r2, kcount, th2f)) ++local_unc;
       if (dec < 0) {
         // the oracle's order of summation, on one lane
         int ex = 0;
         if (lane == 0) {
           ++local_exact;
-          ex = rho2_exact(g, tb, Sg, cd.a2[cw], cd.lo[cw], cd.hi[cw]) > th2;
+          const double v = rho2_exact(g, tb, Sg, cd.a2[cw], cd.lo[cw], cd.hi[cw]);
+          if (near_threshold(v, th2)) ++local_near;
+          ex = v > th2;
         }
         dec = __shfl_sync(0xFFFFFFFFu, ex, 0);
       }
@@ -1747,11 +1771,46 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
   for (int o = 16; o > 0; o >>= 1) {
     local_new += __shfl_xor_sync(0xFFFFFFFFu, local_new, o);
     local_exact += __shfl_xor_sync(0xFFFFFFFFu, local_exact, o);
+    local_near += __shfl_xor_sync(0xFFFFFFFFu, local_near, o);
+    local_unc += __shfl_xor_sync(0xFFFFFFFFu, local_unc, o);
   }
   if (lane == 0) {
     if (local_new) atomicAdd(&rs->count_new, (unsigned long long)local_new);
     if (local_exact) atomicAdd(&rs->nexact, (unsigned long long)local_exact);
+    if (local_near) atomicAdd(&rs->nnear, (unsigned long long)local_near);
+    if (local_unc) atomicAdd(&rs->nuncertain, (unsigned long long)local_unc);
   }
+}
+
+// Both evaluations of rho^2 for every kept candidate against the current S_gal: the FP32
+// screen (what the loop decides on first) and the FP64 value in the oracle's order of
+// summation, with the bins the screen summed.  A measurement of the screen's error.
+__global__ void __launch_bounds__(256) k_snr_check(Cands cd, Grid g, Tables tb,
+                                                   const double* __restrict__ Sg,
+                                                   const float* __restrict__ inv_f,
+                                                   const RunState* rs,
+                                                   long long* __restrict__ src,
+                                                   float* __restrict__ screen,
+                                                   double* __restrict__ exact,
+                                                   int* __restrict__ kcount_out) {
+  const long long nlive = (long long)rs->nlive;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nlive;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int4 pk = cd.pk[c];
+    int kcount = 0;
+    screen[c] = screen_part(cd, c, pk, g, tb, inv_f, 0, 1, kcount);
+    exact[c] = rho2_exact(g, tb, Sg, cd.a2[c], cd.lo[c], cd.hi[c]);
+    src[c] = cd.src[c];
+    kcount_out[c] = kcount;
+  }
+}
+
+void launch_snr_check(Cands cd, long long ncap, const Grid& g, const Tables& tb, const double* Sg,
+                      const float* inv_f, const RunState* rs, long long* src, float* screen,
+                      double* exact, int* kcount, cudaStream_t st) {
+  long long want = (ncap + 255) / 256;
+  int bl = (int)(want < 4096 ? (want < 1 ? 1 : want) : 4096);
+  k_snr_check<<<bl, 256, 0, st>>>(cd, g, tb, Sg, inv_f, rs, src, screen, exact, kcount);
 }
 
 void launch_snr_resolve(Cands cd, long long ncap, const Grid& g, const Tables& tb,

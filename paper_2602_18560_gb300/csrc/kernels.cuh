@@ -37,6 +37,8 @@ struct RunState {
   unsigned long long relchg_bits;   // max relative change of S_n (conv_rtol)
   unsigned long long next_tile;  // catalog tiles handed out so far (catalog pass)
   unsigned long long work[4];    // work-list items the loop kernels were handed (by list)
+  unsigned long long nnear;      // FP64 decisions with |rho^2 / rho_th^2 - 1| < 2e-9
+  unsigned long long nuncertain; // FP32 decisions (mixed precision) inside the screen's bound
   unsigned err;
   unsigned pad;
 };
@@ -229,6 +231,13 @@ void launch_snr_resolve(Cands cd, long long ncap, const Grid& g, const Tables& t
                         const double* Sg, const float* inv_f, double th2, double rtol, int mixed,
                         unsigned char* resolved, unsigned long long* acc, RunState* rs,
                         Dirty d, int Kc, int sg_radius, int nsm, cudaStream_t st);
+
+// For each kept candidate c < rs->nlive (ncap: capacity): its catalog index, its rho^2 as the
+// FP32 screen evaluates it against the current S_gal (through inv_f) with the count of bins
+// summed, and its rho^2 in FP64 in the oracle's order of summation.
+void launch_snr_check(Cands cd, long long ncap, const Grid& g, const Tables& tb, const double* Sg,
+                      const float* inv_f, const RunState* rs, long long* src, float* screen,
+                      double* exact, int* kcount, cudaStream_t st);
 
 // Work lists of the set the next iteration reads (set rs->iter & 1).
 void launch_build_lists(Dirty d, int* lists, int* counts, RunState* rs, cudaStream_t st);

@@ -70,11 +70,17 @@ extern "C" int sub_running_mean_noalloc(const double* x, double* out, int64_t n,
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 128) {
+  if (e != cudaSuccess) {
     snprintf(msg, sizeof(msg), "sub_running_mean_noalloc: cudaGetDevice failed: %s",
              cudaGetErrorString(e));
     set_global_error(msg);
     return SUB_ECUDA;
+  }
+  if (dev < 0 || dev >= 128) {
+    snprintf(msg, sizeof(msg), "sub_running_mean_noalloc: device %d is beyond the 128 devices "
+             "this entry point keeps addresses for", dev);
+    set_global_error(msg);
+    return SUB_EINVAL;
   }
   unsigned long long* base = nullptr;
   {

@@ -69,6 +69,7 @@ class sub_stats(ctypes.Structure):
         ("n_resolved", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("k_lo", ctypes.c_int64),
         ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("n_live", ctypes.c_int64), ("n_exact", ctypes.c_int64),
+        ("n_near", ctypes.c_int64), ("n_uncertain", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -108,7 +109,7 @@ EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_load_gen
            "sub_get_catalog", "sub_run", "sub_get_stats",
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
            "sub_get_tables", "sub_get_timing", "sub_get_work", "sub_coarse_grain", "sub_profile",
-           "sub_device_bytes",
+           "sub_device_bytes", "sub_snr_check",
            "sub_destroy",
            "sub_last_error", "sub_running_mean_noalloc", "sub_get_power", "sub_batch_create",
            "sub_batch_run", "sub_batch_last_ms", "sub_batch_last_error", "sub_batch_destroy",
@@ -157,6 +158,7 @@ def lib(build_if_missing: bool = True):
             "sub_coarse_grain": (i32, [P, P, i32, i32, P, P, P, i32]),
             "sub_profile": (i32, [P, P, P, ctypes.POINTER(sub_stats)]),
             "sub_device_bytes": (i64, [P]),
+            "sub_snr_check": (i32, [P, P, P, P, P, i64, ctypes.POINTER(i64)]),
             "sub_destroy": (None, [P]),
             "sub_last_error": (ctypes.c_char_p, [P]),
             "sub_running_mean_noalloc": (i32, [P, P, i64, i32, P]),
@@ -401,6 +403,23 @@ def sub_device_bytes(ctx) -> int:
     return lib().sub_device_bytes(ctx)
 
 
+def sub_snr_check(ctx):
+    """rho^2 of every kept candidate against the last run's S_gal, two ways: the FP32 screen
+    and FP64 in the oracle's order.  Returns dict of numpy arrays src, screen, exact, nbins."""
+    n = ctypes.c_int64()
+    _check(ctx, lib().sub_snr_check(ctx, None, None, None, None, 0, ctypes.byref(n)),
+           allow=(EINVAL,))
+    m = n.value
+    src = np.empty(m, dtype=np.int64)
+    sc = np.empty(m, dtype=np.float32)
+    ex = np.empty(m, dtype=np.float64)
+    nb = np.empty(m, dtype=np.int32)
+    if m:
+        ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in (src, sc, ex, nb)]
+        _check(ctx, lib().sub_snr_check(ctx, *ptrs, m, ctypes.byref(n)))
+    return {"src": src, "screen": sc, "exact": ex, "nbins": nb}
+
+
 def sub_destroy(ctx):
     if ctx:
         lib().sub_destroy(ctx)
@@ -465,6 +484,9 @@ class Subtraction:
 
     def coarse_grain(self, x=None, nbins=100, add_instr=False):
         return sub_coarse_grain(self.ctx, x, nbins, add_instr)
+
+    def snr_check(self):
+        return sub_snr_check(self.ctx)
 
     def profile(self):
         return sub_profile(self.ctx)

@@ -39,7 +39,7 @@ def test_params_default_and_struct_layout():
     assert p.window == 2000 and p.rho_th == 7.0 and abs(p.kappa - 1 / 7) < 1e-16
     assert p.T_obs == 4 * gbsub.YEAR and p.tdi2 == 1 and p.estimator == gbsub.MEAN
     assert ctypes.sizeof(gbsub.sub_params) == 80
-    assert ctypes.sizeof(gbsub.sub_stats) == 72
+    assert ctypes.sizeof(gbsub.sub_stats) == 88
 
 
 def test_invalid_parameters_rejected_before_any_device_call():

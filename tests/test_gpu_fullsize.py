@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize_nb3e7_4yr.json")
-EST = {"median_mean": gbsub.MEDIAN_MEAN, "mean": gbsub.MEAN}
+EST = {"median_mean": gbsub.MEDIAN_MEAN, "mean": gbsub.MEAN, "median": gbsub.MEDIAN}
 
 
 def decode_indices(text):
@@ -65,7 +65,7 @@ def sampled_rel_err(sg, g, est_name, keep=None):
     return float(np.max(np.abs(got[~zero] - ref[~zero]) / ref[~zero]))
 
 
-@pytest.mark.parametrize("est_name", ["median_mean", "mean"])
+@pytest.mark.parametrize("est_name", ["median_mean", "mean", "median"])
 def test_fullsize_fp64_matches_stored_oracle(full, est_name):
     g = full[0]
     e = g["estimators"][est_name]

@@ -2,6 +2,8 @@
 bit for bit, as the same catalog run alone on a plain context (whose parity with the
 oracle the other GPU tests establish), whatever else shares the GPU with it; the server
 keeps to its memory budget."""
+import types
+
 import numpy as np
 import pytest
 
@@ -339,3 +341,115 @@ def test_server_generated_jobs_equal_each_catalog_alone():
             sg, m = s.spectrum(), s.resolved()
         assert np.array_equal(outs[i][0].view(np.uint64), sg.view(np.uint64))
         assert np.array_equal(outs[i][1][:n], m)
+
+
+# ---------------------------------------------------------------- against the oracle
+# The tests above compare batches and served jobs with the same catalogs run alone on plain
+# contexts.  These compare them with the FP64 oracle directly, in FP64 (S_gal within 1e-10,
+# the resolved set identical except for near-threshold decisions) and in mixed precision
+# (S_gal within 1e-5, fewer than 0.01% of the resolved sources decided differently, and only
+# decisions the FP32 value could not settle).  The band is cut to 0.1-2 mHz so that the
+# oracle finishes in seconds.
+
+F_NARROW = 2e-3
+
+
+def oracle_jobs():
+    """Catalogs with flat populations (many sources at the top of the cut band) that take
+    several iterations: 7, 2 and 4."""
+    specs = ((synth.YEAR, 600_000, 2.5, synth.Population(2.0, 2.0)),
+             (synth.YEAR, 300_000, 3.0, synth.Population(2.5, 2.5)),
+             (2 * synth.YEAR, 1_000_000, 2.5, synth.Population(2.5, 2.0)))
+    out = []
+    for i, (T, n, scale, pop) in enumerate(specs):
+        A, f, fdot = synth.catalog(n, 9100 + i, pop)
+        out.append((T, A * scale, f, fdot))
+    return out
+
+
+# generated jobs (T_obs, n, seed, population): 8, 4 and 2 iterations
+GENERATED = ((synth.YEAR, 1_000_000, 9200, synth.Population(2.0, 2.0)),
+             (synth.YEAR, 700_000, 9201, synth.Population(2.0, 2.0)),
+             (synth.YEAR, 500_000, 9202, synth.Population(2.2, 2.0)))
+
+
+@pytest.fixture(scope="module")
+def oracle_refs():
+    import oracle
+    js = oracle_jobs()
+    refs = [oracle.run(oracle.make_params(T_obs=T, window=1000, estimator=gbsub.MEDIAN_MEAN,
+                                          f_max=F_NARROW), A, f, fdot)
+            for T, A, f, fdot in js]
+    return js, refs
+
+
+def against_oracle(ref, st, sg, res, precision):
+    res = np.asarray(res).astype(bool)
+    nz = ref["S_gal"] != 0
+    assert np.all(sg[~nz] == 0)
+    err = float(np.max(np.abs(sg[nz] / ref["S_gal"][nz] - 1.0))) if nz.any() else 0.0
+    ndiff = int(np.sum(res != ref["resolved"]))
+    nres = max(1, int(ref["resolved"].sum()))
+    if precision == gbsub.MIXED:
+        assert err <= 1e-5, err
+        assert ndiff / nres < 1e-4 and ndiff <= st.n_uncertain, (ndiff, nres, st.n_uncertain)
+    else:
+        assert err <= 1e-10, err
+        assert ndiff <= st.n_near, (ndiff, st.n_near)
+        if ndiff == 0:
+            assert st.iterations == ref["iterations"]
+    assert ref["n_resolved"] > 10
+
+
+def test_batch_matches_the_oracle(oracle_refs):
+    js, refs = oracle_refs
+    subs, kinds = [], []
+    for (T, A, f, fdot), ref in zip(js, refs):
+        for prec in (gbsub.FP64, gbsub.MIXED):
+            s = gbsub.Subtraction(T_obs=T, window=1000, estimator=gbsub.MEDIAN_MEAN,
+                                  f_max=F_NARROW, precision=prec)
+            s.load(A, f, fdot)
+            subs.append(s)
+            kinds.append((ref, prec))
+    try:
+        with gbsub.Batch(subs) as b:
+            for _ in range(2):
+                sts = b.run()
+                for s, st, (ref, prec) in zip(subs, sts, kinds):
+                    against_oracle(ref, st, s.spectrum(), s.resolved(), prec)
+    finally:
+        for s in subs:
+            s.close()
+
+
+@pytest.mark.parametrize("precision", [gbsub.FP64, gbsub.MIXED])
+def test_served_jobs_match_the_oracle(oracle_refs, precision):
+    import oracle
+    js, refs = oracle_refs
+    outs, results = {}, {}
+    # three host-array jobs and three generated ones (their catalogs are the host recipe's)
+    gen = GENERATED
+    with gbsub.Server(max_inflight=4, window=1000, estimator=gbsub.MEDIAN_MEAN,
+                      precision=precision, f_max=F_NARROW) as srv:
+        for i, (T, A, f, fdot) in enumerate(js):
+            nb = int(np.floor(F_NARROW * T)) - int(np.ceil(1e-4 * T)) + 1
+            outs[i] = (np.zeros(nb), np.zeros(len(A), dtype=np.uint8))
+            srv.submit(i, T, A, f, fdot, *outs[i])
+        for k, (T, n, seed, pop) in enumerate(gen):
+            i = len(js) + k
+            nb = int(np.floor(F_NARROW * T)) - int(np.ceil(1e-4 * T)) + 1
+            outs[i] = (np.zeros(nb), np.zeros(n, dtype=np.uint8))
+            srv.submit_generated(i, T, n, seed, pop, *outs[i])
+        while len(results) < len(outs):
+            for r in srv.poll(timeout_ms=2000):
+                results[r["job_id"]] = r
+    for k, (T, n, seed, pop) in enumerate(gen):
+        A, f, fdot = synth.catalog_single(n, seed, pop)
+        refs = refs + [oracle.run(oracle.make_params(T_obs=T, window=1000,
+                                                     estimator=gbsub.MEDIAN_MEAN,
+                                                     f_max=F_NARROW), A, f, fdot)]
+    for i, ref in enumerate(refs):
+        r = results[i]
+        assert r["status"] in (gbsub.OK, gbsub.ENOTCONVERGED), r
+        against_oracle(ref, types.SimpleNamespace(**r["stats"]), outs[i][0], outs[i][1],
+                       precision)

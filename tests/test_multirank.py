@@ -68,16 +68,21 @@ def test_roofline_of_the_dominant_kernel():
     med = {"ms_per_run": 0.5, "launches_per_run": 17.0, "units_per_run": 2432,
            "algorithmic_bytes_per_run": 7.0e7}
     r = bench.dominant_roofline("median", med, tr, "abc", 6700.0, "of measured", 152, 2070.0)
-    assert r["bound"] == "alu" and r["peak"] == pytest.approx(152 * 4 * 2.07)
+    # algorithmic bytes of the work handed out, per average launch, over the HBM peak
     per_launch_s = 0.5e-3 / 17
-    assert r["achieved"] == pytest.approx(7.0e4 * 2432 / 17 / per_launch_s / 1e9)
+    assert r["bound"] == "hbm" and r["peak"] == 6700.0
+    assert r["achieved"] == pytest.approx(7.0e7 / 17 / per_launch_s / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["traffic"] == pytest.approx(1.2e7 * (2432 / 17) / 1222)
-    assert r["hbm_view"]["GB/s"] == pytest.approx(7.0e7 / 17 / per_launch_s / 1e9)
-    # a capture of other sources: same bound and instructions, no traffic, flagged
+    # the issue rate beside it: warp instructions over one per scheduler per clock
+    iv = r["issue_view"]
+    assert iv["peak"] == pytest.approx(152 * 4 * 2.07)
+    assert iv["achieved"] == pytest.approx(7.0e4 * 2432 / 17 / per_launch_s / 1e9)
+    assert iv["frac"] == pytest.approx(iv["achieved"] / iv["peak"])
+    # a capture of other sources: no traffic, and the instruction counts flagged
     stale = bench.dominant_roofline("median", med, tr, "new", 6700.0, "of measured", 152, 2070.0)
-    assert stale["bound"] == "alu" and stale["traffic"] is None
-    assert "stale" in stale["instructions_from"]
+    assert stale["bound"] == "hbm" and stale["traffic"] is None
+    assert "stale" in stale["issue_view"]["instructions_from"]
     pre = {"ms_per_run": 0.5, "launches_per_run": 1.0, "units_per_run": None,
            "algorithmic_bytes_per_run": 7.6e8}
     p = bench.dominant_roofline("prepass", pre, tr, "abc", 6700.0, "of measured", 152, 2070.0)
