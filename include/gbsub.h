@@ -369,7 +369,9 @@ int sub_test_hooks(sub_ctx* ctx, int32_t flags);
 /* ------------------------------------------------------------------ serving
  * A request loop for subtraction jobs as a sampler emits them.  Jobs are queued in
  * arrival order and admitted while fewer than max_inflight run and a device-memory budget
- * allows; each admitted job runs on a pooled context (one per T_obs and catalog size
+ * allows; when the job at the head has to wait, a later job that an idle pooled context can
+ * take is admitted past it (it takes nothing the head could use).  Each admitted job runs
+ * on a pooled context (one per T_obs and catalog size
  * class, created on demand, the least recently used idle ones destroyed when the budget
  * needs room) on its own stream, so jobs overlap on the GPU (continuous batching).  A
  * job's latency runs from sub_server_submit to its results being in the caller's
@@ -418,7 +420,9 @@ int sub_server_create(const sub_server_params* p, sub_server** out);
 
 /* Queue a job and return at once.  A, f, fdot: host arrays of n sources (pinned memory
  * makes the copies asynchronous); S_gal: host buffer of cap >= n_bins(T_obs) doubles, or
- * null; mask: host buffer of n bytes (1 = resolved), or null.  All must stay valid and
+ * null; mask: host buffer of n bytes (1 = resolved), or null.  Results go straight into
+ * page-locked buffers; pageable ones receive them from page-locked staging when the job
+ * completes (one host copy more).  All must stay valid and
  * untouched until the job's result comes out of sub_server_poll.  A job larger than the
  * whole budget ends with SUB_EBUDGET.  Errors: SUB_EINVAL, SUB_ESTATE (server stopping). */
 int sub_server_submit(sub_server* s, int64_t job_id, double T_obs, const double* A,

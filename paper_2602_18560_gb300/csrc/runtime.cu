@@ -6,7 +6,8 @@
 // run side by side overlap on the SMs.
 //
 // A server accepts subtraction jobs as they arrive (host catalogs and host result buffers),
-// admits them in arrival order while a device-memory budget and an in-flight limit allow,
+// admits them in arrival order while a device-memory budget and an in-flight limit allow
+// (a job that an idle pooled context can take starts past a head that has to wait),
 // runs each on a pooled context with its own stream (jobs overlap on the GPU: continuous
 // batching), and hands back each job's statistics with its latency from submission to
 // results in the caller's buffers.  Completion is observed by a host function enqueued
@@ -232,7 +233,32 @@ struct Slot {
   bool busy = false;
   Job job;
   uint64_t last_use = 0;
+  // Page-locked staging of the results, for callers whose buffers are pageable: a copy from
+  // the device into pageable memory returns only once it is done, which would hold the
+  // worker (and every other job's admission) until this job's whole run had finished.
+  double* h_sg = nullptr;
+  uint8_t* h_mask = nullptr;
+  int64_t h_sg_cap = 0, h_mask_cap = 0;
+  bool stage_sg = false, stage_mask = false;  // this job's results go through the staging
 };
+
+void free_staging(Slot* sl) {
+  if (sl->h_sg) cudaFreeHost(sl->h_sg);
+  if (sl->h_mask) cudaFreeHost(sl->h_mask);
+  sl->h_sg = nullptr;
+  sl->h_mask = nullptr;
+  sl->h_sg_cap = sl->h_mask_cap = 0;
+}
+
+// True for host memory the GPU can copy into asynchronously (page-locked or registered).
+bool page_locked(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
 
 }  // namespace
 
@@ -301,14 +327,16 @@ static Slot* make_slot(sub_server* s, double T_obs, int64_t cap, int* status);
 // A context for job j: an idle one with the same T_obs and room for the catalog, else a new
 // one if the budget allows (idle contexts are destroyed, least recently used first, to make
 // room).  Returns null when the job must wait for running jobs to finish.
-static Slot* acquire_slot(sub_server* s, const Job& j, int* fail_status) {
+// With idle_only, only an idle pooled context is taken (no context is created or replaced):
+// the rule for jobs admitted past a queue head that has to wait.
+static Slot* acquire_slot(sub_server* s, const Job& j, int* fail_status, bool idle_only) {
   *fail_status = SUB_OK;
   Slot* best = nullptr;
   for (Slot* sl : s->slots) {
     if (sl->busy || sl->ctx->p.T_obs != j.T_obs || sl->ctx->cap_N < j.n) continue;
     if (!best || sl->ctx->cap_N < best->ctx->cap_N) best = sl;
   }
-  if (best) return best;
+  if (best || idle_only) return best;
   if (s->p.max_contexts > 0 && (int)s->slots.size() >= s->p.max_contexts) {
     // At the pool limit a job that a busy context could take waits for it: replacing an
     // idle context of another observation time would only move the shortage there, and
@@ -323,6 +351,7 @@ static Slot* acquire_slot(sub_server* s, const Job& j, int* fail_status) {
     if (!victim) return nullptr;
     s->pool_bytes -= sub_device_bytes(victim->ctx);
     sub_destroy(victim->ctx);
+    free_staging(victim);
     s->slots.erase(std::find(s->slots.begin(), s->slots.end(), victim));
     delete victim;
   }
@@ -339,6 +368,7 @@ static Slot* acquire_slot(sub_server* s, const Job& j, int* fail_status) {
     if (!victim) return nullptr;
     s->pool_bytes -= sub_device_bytes(victim->ctx);
     sub_destroy(victim->ctx);
+    free_staging(victim);
     s->slots.erase(std::find(s->slots.begin(), s->slots.end(), victim));
     delete victim;
   }
@@ -359,11 +389,31 @@ static int launch_job(sub_server* s, Slot* sl, Job& j) {
   rc = sub_run(c, nullptr);
   if (rc) return rc;
   cudaError_t e = cudaSuccess;
-  if (j.sg_out) e = cudaMemcpyAsync(j.sg_out, c->Sg, (size_t)c->grid.nb * 8,
-                                    cudaMemcpyDeviceToHost, c->stream);
+  // results go straight into page-locked caller buffers, else through the slot's staging
+  // (finalize copies them on): either way this thread only enqueues
+  sl->stage_sg = j.sg_out && !page_locked(j.sg_out);
+  sl->stage_mask = j.mask_out && j.n > 0 && !page_locked(j.mask_out);
+  const int64_t nb = c->grid.nb;
+  if (sl->stage_sg && sl->h_sg_cap < nb) {
+    if (sl->h_sg) cudaFreeHost(sl->h_sg);
+    sl->h_sg = nullptr;
+    sl->h_sg_cap = 0;
+    e = cudaHostAlloc((void**)&sl->h_sg, (size_t)nb * 8, cudaHostAllocDefault);
+    if (!e) sl->h_sg_cap = nb;
+  }
+  if (!e && sl->stage_mask && sl->h_mask_cap < j.n) {
+    if (sl->h_mask) cudaFreeHost(sl->h_mask);
+    sl->h_mask = nullptr;
+    sl->h_mask_cap = 0;
+    e = cudaHostAlloc((void**)&sl->h_mask, (size_t)j.n, cudaHostAllocDefault);
+    if (!e) sl->h_mask_cap = j.n;
+  }
+  if (!e && j.sg_out)
+    e = cudaMemcpyAsync(sl->stage_sg ? sl->h_sg : j.sg_out, c->Sg, (size_t)nb * 8,
+                        cudaMemcpyDeviceToHost, c->stream);
   if (!e && j.mask_out && j.n > 0)
-    e = cudaMemcpyAsync(j.mask_out, c->resolved, (size_t)j.n, cudaMemcpyDeviceToHost,
-                        c->stream);
+    e = cudaMemcpyAsync(sl->stage_mask ? sl->h_mask : j.mask_out, c->resolved, (size_t)j.n,
+                        cudaMemcpyDeviceToHost, c->stream);
   sl->busy = true;
   sl->job = j;
   sl->last_use = ++s->tick;
@@ -379,6 +429,14 @@ static void finalize(sub_server* s, Slot* sl) {
   sub_stats st;
   std::memset(&st, 0, sizeof(st));
   int status = ctx_fill_stats(sl->ctx, &st);
+  if (sl->stage_sg) {
+    std::memcpy(sl->job.sg_out, sl->h_sg, (size_t)sl->ctx->grid.nb * 8);
+    sl->job.t_done = Clock::now();
+  }
+  if (sl->stage_mask) {
+    std::memcpy(sl->job.mask_out, sl->h_mask, (size_t)sl->job.n);
+    sl->job.t_done = Clock::now();
+  }
   float gpu_ms = 0.0f;
   float pre = 0.0f, loop = 0.0f;
   if (sub_get_timing(sl->ctx, &pre, &loop, &gpu_ms) != SUB_OK) gpu_ms = 0.0f;
@@ -405,19 +463,29 @@ static void worker_main(sub_server* s) {
       if (s->stop && s->inflight == 0 && fin.empty()) break;
     }
     for (Slot* sl : fin) finalize(s, sl);
+    // Admission in arrival order.  When the job at the head has to wait (for memory, or
+    // for a busy context it alone fits), later jobs that an idle pooled context can take
+    // start past it: they use no memory or context the head could have had (an idle context
+    // that fits the head would have gone to the head), so it is not delayed by them.
+    size_t pos = 0;  // queue position to try next (jobs before it wait)
     for (;;) {
       Job j;
       {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (s->stop || s->queue.empty() || s->inflight >= s->p.max_inflight) break;
-        j = s->queue.front();
+        if (s->stop || pos >= s->queue.size() || s->inflight >= s->p.max_inflight) break;
+        j = s->queue[pos];
       }
       int fail = SUB_OK;
-      Slot* sl = acquire_slot(s, j, &fail);
-      if (!sl && fail == SUB_OK) break;  // wait for memory to free up
+      Slot* sl = acquire_slot(s, j, &fail, pos > 0);
+      if (!sl && fail == SUB_OK) {
+        ++pos;  // this job waits; a later one may fit an idle context
+        if (pos > 256) break;
+        continue;
+      }
       {
+        // only this thread removes jobs, and submissions only append: j is still at pos
         std::lock_guard<std::mutex> lk(s->mu);
-        s->queue.pop_front();
+        s->queue.erase(s->queue.begin() + (std::ptrdiff_t)pos);
         if (sl) s->inflight += 1;
       }
       j.t_admit = Clock::now();
@@ -654,6 +722,7 @@ extern "C" void sub_server_destroy(sub_server* s) {
   if (s->worker.joinable()) s->worker.join();
   for (Slot* sl : s->slots) {
     sub_destroy(sl->ctx);
+    free_staging(sl);
     delete sl;
   }
   delete s;

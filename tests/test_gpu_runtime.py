@@ -453,3 +453,63 @@ def test_served_jobs_match_the_oracle(oracle_refs, precision):
         assert r["status"] in (gbsub.OK, gbsub.ENOTCONVERGED), r
         against_oracle(ref, types.SimpleNamespace(**r["stats"]), outs[i][0], outs[i][1],
                        precision)
+
+
+def test_small_job_starts_past_a_waiting_head():
+    # a pool of two contexts at its limit: a large context (busy with a long job) and a small
+    # one.  A second large job must wait for the large context; a small job behind it starts
+    # at once on the idle small context instead of waiting behind the head.
+    T = 4 * synth.YEAR
+    nb = int(np.floor(1e-2 * T)) - int(np.ceil(1e-4 * T)) + 1
+    pop = synth.population_draw(2, 0)
+    sizes = {1: 30_000_000, 2: 30_000_000, 3: 50_000}
+    outs = {i: (np.zeros(nb), np.zeros(n, dtype=np.uint8)) for i, n in sizes.items()}
+    with gbsub.Server(max_inflight=4, max_contexts=2, window=1000,
+                      estimator=gbsub.MEDIAN_MEAN) as srv:
+        srv.prewarm(T, 30_000_000, 1)
+        srv.prewarm(T, 50_000, 1)
+        for i, n in sizes.items():
+            srv.submit_generated(i, T, n, 700 + i, pop, *outs[i])
+        got = {}
+        while len(got) < 3:
+            for r in srv.poll(timeout_ms=2000):
+                got[r["job_id"]] = r
+        assert srv.info()["contexts_created"] == 2
+    assert all(r["status"] in (gbsub.OK, gbsub.ENOTCONVERGED) for r in got.values())
+    # job 2 waited for job 1's context; job 3 did not wait for job 2
+    assert got[2]["queue_ms"] > 0.5 * (got[1]["latency_ms"] - got[1]["queue_ms"])
+    assert got[3]["queue_ms"] < got[2]["queue_ms"]
+    for i, n in sizes.items():
+        with gbsub.Subtraction(T_obs=T, window=1000, estimator=gbsub.MEDIAN_MEAN) as s:
+            s.load_generated(n, 700 + i, pop, fused=True)
+            s.run()
+            assert np.array_equal(outs[i][0].view(np.uint64), s.spectrum().view(np.uint64))
+            assert np.array_equal(outs[i][1], s.resolved())
+
+
+def test_jobs_with_pageable_result_buffers_overlap():
+    # results into pageable host memory go through page-locked staging, so the worker does
+    # not wait for one job's results before it starts the next: two long jobs run at once
+    T = 4 * synth.YEAR
+    nb = int(np.floor(1e-2 * T)) - int(np.ceil(1e-4 * T)) + 1
+    pop = synth.population_draw(2, 0)
+    n = 30_000_000
+    with gbsub.Server(max_inflight=2, window=1000, estimator=gbsub.MEDIAN_MEAN) as srv:
+        srv.prewarm(T, n, 2)
+        for rnd in range(2):   # the first round sets up each context's staging
+            outs = {i: (np.zeros(nb), np.zeros(n, dtype=np.uint8)) for i in (0, 1)}
+            for i in (0, 1):
+                srv.submit_generated(10 * rnd + i, T, n, 800 + i, pop, *outs[i])
+            got = {}
+            while len(got) < 2:
+                for r in srv.poll(timeout_ms=2000):
+                    got[r["job_id"] - 10 * rnd] = r
+    assert all(r["status"] in (gbsub.OK, gbsub.ENOTCONVERGED) for r in got.values())
+    # the second job was admitted well before the first one had finished
+    assert got[1]["queue_ms"] < 0.5 * got[0]["latency_ms"]
+    for i in (0, 1):
+        with gbsub.Subtraction(T_obs=T, window=1000, estimator=gbsub.MEDIAN_MEAN) as s:
+            s.load_generated(n, 800 + i, pop, fused=True)
+            s.run()
+            assert np.array_equal(outs[i][0].view(np.uint64), s.spectrum().view(np.uint64))
+            assert np.array_equal(outs[i][1], s.resolved())
