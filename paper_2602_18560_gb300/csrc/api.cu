@@ -169,6 +169,17 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
     c->grid.mT = (unsigned long long)std::ldexp(m, 53);
     c->grid.eT = ex - 53;
     c->grid.T2f = (float)(p->T_obs * p->T_obs);
+    // the same with the trailing zero bits of the mantissa dropped: whole seconds of
+    // observation time leave at most 32 bits, and f T then takes two 32-bit products
+    unsigned long long tq = c->grid.mT;
+    int etq = c->grid.eT;
+    while (tq && !(tq & 1ull)) {
+      tq >>= 1;
+      ++etq;
+    }
+    c->grid.short_t = (tq > 0 && tq < (1ull << 32)) ? 1 : 0;
+    c->grid.tq = c->grid.short_t ? (unsigned)tq : 0u;
+    c->grid.etq = etq;
   }
   c->plan = make_plan(p->window, n);
   c->plan.fp32_keys = p->precision == SUB_MIXED ? 1 : 0;  // FP32 median selection

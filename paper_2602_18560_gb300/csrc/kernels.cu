@@ -327,14 +327,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
-// Sources whose sweep the FP32 bound cannot keep in one bin go through the FP64 path.
-// They are rare (well under 1%), but one such lane would hold its whole warp on the slow
-// FP64 pipe, so each CTA queues them in shared memory and runs them a full CTA at a time.
-constexpr int kPrepassThreads = 256;
-constexpr int kPreTile = 512;                          // sources per staged tile
-constexpr int kPreStages = 3;                          // tiles in flight per CTA
-constexpr int kPrePer = kPreTile / kPrepassThreads;    // sources per thread per tile
-constexpr int kSlowCap = kPrepassThreads + kPreTile;   // queue entries (drained at >= 256)
+// Sources whose sweep the FP32 bound cannot keep in one bin go through the FP64 path.  They
+// are rare (well under 1%), but one such lane would hold its whole warp on the slow FP64
+// pipe, so each warp queues them in shared memory and runs them 32 at a time.
+//
+// Layout of a CTA: kPreConsumers consumer warps and one producer warp.  The producer takes
+// tiles of kPreTile sources from a global counter (CTAs that run faster take more tiles) and
+// streams each into one of kPreStages shared-memory stages with bulk asynchronous copies of
+// A, f and fdot (cp.async.bulk, completion counted in bytes on the stage's "full" mbarrier).
+// Each consumer warp takes its own kPreTile / kPreConsumers sources of the stage and, done,
+// arrives on the stage's "empty" mbarrier; the producer refills a stage once every consumer
+// warp has arrived.  No CTA-wide barrier runs in the steady state, so a warp that meets a
+// slow source delays no other warp.
+constexpr int kPreConsumers = 8;
+constexpr int kPrepassThreads = (kPreConsumers + 1) * 32;
+constexpr int kPreTile = 1024;                                // sources per staged tile
+constexpr int kPreStages = 4;                                 // tiles in flight per CTA
+constexpr int kPreWarpSrc = kPreTile / kPreConsumers;         // sources per consumer warp
+constexpr int kPrePer = kPreWarpSrc / 32;                     // sources per lane per tile
+constexpr int kSlowWarpCap = 64;                              // queue of a warp (drained at 32)
 constexpr size_t kPrepassSmem = (size_t)kPreStages * kPreTile * 3 * sizeof(double);
 
 // Sweeps longer than this many bins are walked by a whole warp (loud high-frequency sources
@@ -351,126 +362,231 @@ __device__ __noinline__ double3 gen_source_at(const CatalogRef* __restrict__ cat
   return r;
 }
 
-__device__ __forceinline__ void prepass_drain(const CatalogRef* __restrict__ cat,
-                                              const double* __restrict__ A,
-                                              const double* __restrict__ f,
-                                              const double* __restrict__ fdot, const Grid& g,
-                                              const Tables& tb, u64 tk_bits, u64 tl_bits,
-                                              unsigned long long* __restrict__ acc, Cands& cd,
-                                              RunState* rs, const long long* q, int cnt,
-                                              unsigned long long& nkappa) {
+// f T + 1/2 split into its integer part k and the top 24 bits of its fraction, from the
+// exact product when T's mantissa has at most 32 significant bits (T = tq 2^etq; whole
+// seconds of observation time qualify).  The mantissa of f is split in 21 + 32 bits, so the
+// product is two 32 x 32 -> 64-bit multiplies.  Exact f T, not its FP64 rounding: the two
+// differ by less than 2^-33 bins in the band, and the caller keeps a source on this path
+// only when the fraction is at least 2^-20 from a cell edge, where both give the same bin.
+// False for f not positive normal, or f T outside the range handled here.
+__device__ __forceinline__ bool ft_bin_short(double f, unsigned tq, int etq, long long* k,
+                                             unsigned* frac24) {
+  const u64 b = (u64)__double_as_longlong(f);
+  const int e = (int)(b >> 52);  // sign bit included: a negative f fails the range test
+  if (e <= 0 || e >= 0x7FF) return false;
+  const u64 mf = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const u64 p0 = (u64)(unsigned)mf * tq;           // low 32 bits of mf times tq
+  const u64 p1 = (u64)(unsigned)(mf >> 32) * tq;   // high 21 bits of mf times tq
+  const u64 hi = p1 + (p0 >> 32);                  // f T = (hi 2^32 + lo) 2^(e - 1075 + etq)
+  const int G = 1075 - etq - e - 32;               // fraction bits of f T within hi
+  if (G < 24 || G > 62) return false;
+  const u64 x = hi + (1ull << (G - 1));            // + 1/2
+  *k = (long long)(x >> G);
+  *frac24 = (unsigned)(x >> (G - 24)) & 0xFFFFFFu;
+  return true;
+}
+
+// The common case of one source without any FP64 arithmetic beyond A^2: its bin k0 and the
+// FP32 certificate that the whole sweep [f T, f T + fdot T^2] stays inside cell k0 (else the
+// FP64 path takes it).
+__device__ __forceinline__ bool single_bin(double fs, double fds, const Grid& g, long long* k0) {
+  unsigned fr24 = 0;
+  bool ok;
+  if (g.short_t) {
+    ok = ft_bin_short(fs, g.tq, g.etq, k0, &fr24);
+  } else {
+    int fb;
+    ok = ft_bin(fs, g.mT, g.eT, k0, &fr24, &fb);
+  }
+  if (!ok) return false;
+  const float du = __fmul_rn(dbl_to_f32_signed(fds), g.T2f);
+  const float phi = __fmul_rn((float)fr24, 5.9604644775390625e-8f);             // 2^-24
+  const float m = __fadd_rn(9.5367431640625e-7f, __fmul_rn(4e-7f, fabsf(du)));  // 2^-20 + ...
+  const float x = __fadd_rn(phi, du);
+  return (x >= m) && (x < __fsub_rn(1.0f, m));
+}
+
+// The FP64 path of up to 32 queued sources q[0 .. cnt) of one warp (lane i takes entry i;
+// sweeps longer than kSlowLaneBins by the whole warp).
+__device__ __forceinline__ void prepass_drain_warp(const CatalogRef* __restrict__ cat,
+                                                   const double* __restrict__ A,
+                                                   const double* __restrict__ f,
+                                                   const double* __restrict__ fdot,
+                                                   const Grid& g, const Tables& tb, u64 tk_bits,
+                                                   u64 tl_bits, unsigned long long* __restrict__ acc,
+                                                   Cands& cd, RunState* rs, const long long* q,
+                                                   int cnt, unsigned long long& nkappa) {
   const int lane = threadIdx.x & 31;
-  // every thread takes entries tid, tid + blockDim.x, ...
-  for (int base = 0; base < cnt; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const bool valid = i < cnt;
-    long long s = valid ? q[i] : 0;
-    double a2 = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
-    bool wide = false;
-    if (valid) {
-      double a;
-      if (cat->staged == kCatGenerated) {
-        const double3 gsrc = gen_source_at(cat, s);
-        a = gsrc.x;
-        fs = gsrc.y;
-        fds = gsrc.z;
-      } else {
-        a = A[s];
-        fs = f[s];
-        fds = fdot[s];
-      }
-      a2 = __dmul_rn(a, a);
-      wide = slow_span(fs, fds, g) > kSlowLaneBins;
-      if (!wide) r = prepass_slow(a2, fs, fds, g, tb, acc, &rs->err);
+  const bool valid = lane < cnt;
+  long long s = valid ? q[lane] : 0;
+  double a2 = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
+  bool wide = false;
+  if (valid) {
+    double a;
+    if (cat->staged == kCatGenerated) {
+      const double3 gsrc = gen_source_at(cat, s);
+      a = gsrc.x;
+      fs = gsrc.y;
+      fds = gsrc.z;
+    } else {
+      a = A[s];
+      fs = f[s];
+      fds = fdot[s];
     }
-    prepass_decide(r, tk_bits, tl_bits, valid && !wide, s, a2, fs, fds, g, cd, rs, nkappa);
-    unsigned pending = __ballot_sync(0xFFFFFFFFu, wide);
-    while (pending) {
-      const int src = __ffs(pending) - 1;
-      pending &= pending - 1;
-      const long long sw_s = __shfl_sync(0xFFFFFFFFu, s, src);
-      const double sw_a2 = __shfl_sync(0xFFFFFFFFu, a2, src);
-      const double sw_f = __shfl_sync(0xFFFFFFFFu, fs, src);
-      const double sw_fd = __shfl_sync(0xFFFFFFFFu, fds, src);
-      const double rw = prepass_slow_warp(sw_a2, sw_f, sw_fd, g, tb, acc, &rs->err);
-      prepass_decide(rw, tk_bits, tl_bits, lane == 0, sw_s, sw_a2, sw_f, sw_fd, g, cd, rs,
-                     nkappa);
-    }
+    a2 = __dmul_rn(a, a);
+    wide = slow_span(fs, fds, g) > kSlowLaneBins;
+    if (!wide) r = prepass_slow(a2, fs, fds, g, tb, acc, &rs->err);
+  }
+  prepass_decide(r, tk_bits, tl_bits, valid && !wide, s, a2, fs, fds, g, cd, rs, nkappa);
+  unsigned pending = __ballot_sync(0xFFFFFFFFu, wide);
+  while (pending) {
+    const int src = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const long long sw_s = __shfl_sync(0xFFFFFFFFu, s, src);
+    const double sw_a2 = __shfl_sync(0xFFFFFFFFu, a2, src);
+    const double sw_f = __shfl_sync(0xFFFFFFFFu, fs, src);
+    const double sw_fd = __shfl_sync(0xFFFFFFFFu, fds, src);
+    const double rw = prepass_slow_warp(sw_a2, sw_f, sw_fd, g, tb, acc, &rs->err);
+    prepass_decide(rw, tk_bits, tl_bits, lane == 0, sw_s, sw_a2, sw_f, sw_fd, g, cd, rs,
+                   nkappa);
   }
 }
 
-__global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Wait for phase `parity` of the barrier; false once *abort is set by another warp of the CTA,
+// or after about a second (2^31 clocks), or after 2^24 polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity,
+                                                const int* abort) {
+  const uint32_t a = smem_addr(bar);
+  const long long t0 = clock64();
+  for (int i = 0; i < (1 << 24); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((i & 63) == 63) {
+      if (*(volatile const int*)abort) return false;
+      if (clock64() - t0 > (2LL << 30)) return false;
+      __nanosleep(256);
+    }
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kPrepassThreads, 2) k_prepass(
     const CatalogRef* __restrict__ cat, Grid g, Tables tb, double thr_kappa, double thr_live,
     unsigned long long* __restrict__ acc, AccReplicas rep, Cands cd, RunState* rs,
     int test_flags) {
   extern __shared__ __align__(128) double pre_tiles[];  // [stage][A | f | fdot][kPreTile]
-  __shared__ __align__(8) uint64_t bar[kPreStages];
+  __shared__ __align__(8) uint64_t full[kPreStages], empty[kPreStages];
   __shared__ long long stage_tile[kPreStages];  // tile held by each stage
-  __shared__ int stage_copying[kPreStages];     // its copies were started
+  __shared__ long long slow_q[kPreConsumers][kSlowWarpCap];
+  __shared__ int abort_flag;
   const double* __restrict__ A = cat->A;
   const double* __restrict__ f = cat->f;
   const double* __restrict__ fdot = cat->fdot;
   const long long N = cat->n;
   const bool use_tma = cat->staged == kCatDevice;
   const bool generated = cat->staged == kCatGenerated;
-  __shared__ long long slow_q[kSlowCap];
-  __shared__ int slow_n;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const long long ntiles = (N + kPreTile - 1) / kPreTile;
+  // full tiles of device memory come through TMA; the ragged one, and every tile of a catalog
+  // in host memory or generated, through plain loads (or the generator)
+  const long long nfull = use_tma ? N / kPreTile : 0;
+  if (tid == 0) {
+    for (int k = 0; k < kPreStages; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kPreConsumers);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  __syncthreads();
+
+  if (warp == kPreConsumers) {
+    // ------------------------------------------------ producer (one lane)
+    if (lane != 0) return;
+    // bit k of copying: the copies of stage k's latest tile were started, in its use of
+    // parity bit k of copy_par (they complete that phase of full[k])
+    unsigned copying = 0, copy_par = 0;  // bit k: stage k
+    for (long long i = 0;; ++i) {
+      const int stage = (int)(i % kPreStages);
+      const unsigned use = (unsigned)(i / kPreStages);
+      if (use > 0) {
+        // every consumer warp has let go of the stage's previous tile
+        if (!mbar_wait_abort(&empty[stage], (use - 1) & 1, &abort_flag)) {
+          atomicOr(&rs->err, ERR_TIMEOUT);
+          *(volatile int*)&abort_flag = 1;
+          break;
+        }
+        copying &= ~(1u << stage);  // the consumers waited for those copies
+      }
+      const long long t = (long long)atomicAdd(&rs->next_tile, 1ull);
+      stage_tile[stage] = t;
+      if (t < nfull && !(test_flags & 1)) {
+        copying |= 1u << stage;
+        copy_par = (copy_par & ~(1u << stage)) | ((use & 1u) << stage);
+        double* d = pre_tiles + (size_t)stage * 3 * kPreTile;
+        const size_t off = (size_t)t * kPreTile;
+        mbar_expect_tx(&full[stage], 3u * kPreTile * (unsigned)sizeof(double));
+        bulk_g2s(d, A + off, kPreTile * sizeof(double), &full[stage]);
+        bulk_g2s(d + kPreTile, f + off, kPreTile * sizeof(double), &full[stage]);
+        bulk_g2s(d + 2 * kPreTile, fdot + off, kPreTile * sizeof(double), &full[stage]);
+      } else if (t >= nfull) {
+        mbar_arrive(&full[stage]);  // a ragged, mapped or generated tile, or the end
+      }
+      // (with the test hook a full tile gets no copy and no arrival: its waits run out)
+      if (t >= ntiles) break;
+    }
+    if (*(volatile int*)&abort_flag) {
+      // the consumers gave up: wait (bounded) for every copy this CTA started before its
+      // shared memory goes away
+      for (int k = 0; k < kPreStages; ++k)
+        if ((copying >> k) & 1u) mbar_wait(&full[k], (copy_par >> k) & 1u);
+    }
+    return;
+  }
+
+  // -------------------------------------------------- consumers
   // thresholds on r >= 0 compared as the integer bits of non-negative doubles
   const u64 tk_bits = (u64)__double_as_longlong(thr_kappa);
   const u64 tl_bits = (u64)__double_as_longlong(thr_live);
   unsigned long long nkappa = 0;
-  const long long ntiles = (N + kPreTile - 1) / kPreTile;
-  // full tiles of device memory come through TMA; the ragged one, and every tile of a catalog
-  // in host memory, through plain loads
-  const long long nfull = use_tma ? N / kPreTile : 0;
-  // Thread 0 takes the next tile from the global counter (CTAs that run faster take more
-  // tiles) and, when it is full, starts its copy into `stage`.
-  auto fetch = [&](int stage) {
-    const long long t = (long long)atomicAdd(&rs->next_tile, 1ull);
-    stage_tile[stage] = t;
-    stage_copying[stage] = 0;
-    if (t < nfull && !(test_flags & 1)) {
-      stage_copying[stage] = 1;
-      double* d = pre_tiles + (size_t)stage * 3 * kPreTile;
-      const size_t off = (size_t)t * kPreTile;
-      mbar_expect_tx(&bar[stage], 3u * kPreTile * (unsigned)sizeof(double));
-      bulk_g2s(d, A + off, kPreTile * sizeof(double), &bar[stage]);
-      bulk_g2s(d + kPreTile, f + off, kPreTile * sizeof(double), &bar[stage]);
-      bulk_g2s(d + 2 * kPreTile, fdot + off, kPreTile * sizeof(double), &bar[stage]);
-    }
-  };
-  if (tid == 0) {
-    for (int k = 0; k < kPreStages; ++k) mbar_init(&bar[k], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    slow_n = 0;
-    for (int k = 0; k < kPreStages; ++k) fetch(k);
-  }
-  __syncthreads();
-  bool failed = false;
-  long long i = 0;
-  for (;; ++i) {
+  long long* myq = slow_q[warp];
+  int qn = 0;  // entries of the warp's queue (the same in every lane)
+  for (long long i = 0;; ++i) {
     const int stage = (int)(i % kPreStages);
-    // written by thread 0 at least one barrier ago; tiles only grow, so once a stage holds
-    // a tile past the end no copy is outstanding in any stage
+    const unsigned use = (unsigned)(i / kPreStages);
+    const bool ok = mbar_wait_abort(&full[stage], use & 1, &abort_flag);
+    if (!__all_sync(0xFFFFFFFFu, ok)) {
+      if (lane == 0) {
+        atomicOr(&rs->err, ERR_TIMEOUT);
+        *(volatile int*)&abort_flag = 1;
+      }
+      return;
+    }
     const long long t = stage_tile[stage];
     if (t >= ntiles) break;
     const bool staged = t < nfull;
-    bool ok = true;
-    if (staged) ok = mbar_wait(&bar[stage], (unsigned)((i / kPreStages) & 1));
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
     const double* sA = pre_tiles + (size_t)stage * 3 * kPreTile;
     const double* sF = sA + kPreTile;
     const double* sD = sF + kPreTile;
-    // every load of the tile first: from host memory each one takes a microsecond or more
+    const int base = warp * kPreWarpSrc + lane;
+    // every load of the lane's sources first: from host memory each one takes a
+    // microsecond or more
     double av[kPrePer], fv[kPrePer], dv[kPrePer];
 #pragma unroll
     for (int k = 0; k < kPrePer; ++k) {
-      const int idx = tid + k * kPrepassThreads;
+      const int idx = base + 32 * k;
       const long long s = t * kPreTile + idx;
       av[k] = fv[k] = dv[k] = 0.0;
       if (staged) {
@@ -490,39 +606,27 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
         }
       }
     }
+    // the stage may be refilled once every warp has its values in registers
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[stage]);
 #pragma unroll
     for (int k = 0; k < kPrePer; ++k) {
-      const int idx = tid + k * kPrepassThreads;
-      const long long s = t * kPreTile + idx;
+      const long long s = t * kPreTile + base + 32 * k;
       bool valid = false, slow = false;
-      double a2 = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
+      double a2 = 0.0, r = 0.0;
+      const double fs = fv[k], fds = dv[k];
       if (s < N) {
-        const double a = av[k];
-        fs = fv[k];
-        fds = dv[k];
-        a2 = __dmul_rn(a, a);
-        // Common case without FP64: bin of f T + 1/2 exactly, and an FP32 bound on the
-        // sweep fdot T^2 proving that f T + fdot T^2 + 1/2 stays in the same bin (the FP64
-        // path takes every case the bound cannot settle).
-        long long k0;
-        unsigned fr24;
-        int fb;
-        bool single = false;
-        if (ft_bin(fs, g.mT, g.eT, &k0, &fr24, &fb)) {
-          float du = __fmul_rn(dbl_to_f32_signed(fds), g.T2f);
-          float phi = __fmul_rn((float)fr24, 5.9604644775390625e-8f);  // 2^-24
-          float m = __fadd_rn(9.5367431640625e-7f, __fmul_rn(4e-7f, fabsf(du)));  // 2^-20 + ...
-          float x = __fadd_rn(phi, du);
-          single = (x >= m) && (x < __fsub_rn(1.0f, m));
-        }
+        a2 = __dmul_rn(av[k], av[k]);
+        long long k0 = 0;
+        bool single = single_bin(fs, fds, g, &k0);
         if (single && !finite3(a2, fs, fds)) {
           single = false;  // a non-finite amplitude or frequency derivative: refused below
         }
         if (single) {
           valid = true;
-          long long j = k0 - g.k_lo;
+          const long long j = k0 - g.k_lo;
           if (j >= 0 && j < g.nb) {
-            double q = __dmul_rn(a2, tb.gq[j]);
+            const double q = __dmul_rn(a2, tb.gq[j]);
             if (j < rep.nbins)
               deposit_rep(rep, j, (int)(s & (kAccReplicas - 1)), q, &rs->err);
             else
@@ -535,35 +639,25 @@ __global__ void __launch_bounds__(kPrepassThreads, 4) k_prepass(
           atomicOr(&rs->err, ERR_INPUT);  // the source is skipped; the run reports it
         }
       }
-      if (slow) slow_q[atomicAdd(&slow_n, 1)] = s;
+      // append the warp's slow sources to its queue
+      const unsigned sm = __ballot_sync(0xFFFFFFFFu, slow);
+      if (slow) myq[qn + __popc(sm & ((1u << lane) - 1u))] = s;
+      qn += __popc(sm);
       prepass_decide(r, tk_bits, tl_bits, valid, s, a2, fs, fds, g, cd, rs, nkappa);
-    }
-    __syncthreads();  // the stage is consumed; the queue count is final
-    if (tid == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      fetch(stage);
-    }
-    const int cnt = slow_n;
-    if (cnt >= kPrepassThreads) {
-      prepass_drain(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, slow_q, cnt, nkappa);
-      __syncthreads();
-      if (tid == 0) slow_n = 0;
-      __syncthreads();
+      if (qn >= 32) {
+        __syncwarp();
+        prepass_drain_warp(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, myq, 32,
+                           nkappa);
+        __syncwarp();
+        if (lane < qn - 32) myq[lane] = myq[32 + lane];
+        qn -= 32;
+        __syncwarp();
+      }
     }
   }
-  if (failed) {
-    // a copy never arrived: flag it, and wait (bounded) for every copy this CTA started
-    // before its shared memory goes away
-    if (tid == 0) {
-      atomicOr(&rs->err, ERR_TIMEOUT);
-      for (long long k = i; k < i + kPreStages; ++k)
-        if (stage_copying[k % kPreStages])
-          mbar_wait(&bar[k % kPreStages], (unsigned)((k / kPreStages) & 1));
-    }
-    __syncthreads();
-    return;
-  }
-  prepass_drain(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, slow_q, slow_n, nkappa);
+  __syncwarp();
+  if (qn > 0)
+    prepass_drain_warp(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, myq, qn, nkappa);
   for (int o = 16; o > 0; o >>= 1) nkappa += __shfl_xor_sync(0xFFFFFFFFu, nkappa, o);
   if (lane == 0 && nkappa) atomicAdd(&rs->ncand, nkappa);
 }
@@ -572,7 +666,7 @@ void launch_prepass(const CatalogRef* cat, long long cap, const Grid& g, const T
                     double thr_kappa, double thr_live, unsigned long long* acc, AccReplicas rep,
                     Cands cd, RunState* rs, int nsm, int test_flags, cudaStream_t st) {
   long long tiles = (cap + kPreTile - 1) / kPreTile;
-  long long lim = (long long)nsm * 4;  // resident CTAs (launch bounds, shared memory)
+  long long lim = (long long)nsm * 2;  // resident CTAs (launch bounds, shared memory)
   int bl = (int)(tiles < lim ? (tiles < 1 ? 1 : tiles) : lim);
   k_prepass<<<bl, kPrepassThreads, kPrepassSmem, st>>>(cat, g, tb, thr_kappa, thr_live, acc,
                                                        rep, cd, rs, test_flags);

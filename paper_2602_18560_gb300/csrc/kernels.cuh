@@ -51,6 +51,9 @@ struct Grid {
   unsigned long long mT; // T_obs = mT 2^eT, mT the 53-bit integer mantissa
   int eT;
   float T2f;             // T_obs^2 in FP32
+  unsigned tq;           // T_obs = tq 2^etq with tq odd, when it fits in 32 bits (short_t)
+  int etq;
+  int short_t;
 };
 
 // Per-bin tables, built once per context.
