@@ -496,6 +496,8 @@ def main():
             a[0] += t
             a[1] += n
     work = sub.work()  # work items of the (deterministic) profiling runs
+    # per loop iteration of the last profiling run: the device time of its kernels
+    per_iter = [sum(d.values()) for d in sub.profile_iterations()]
     nb = st.n_bins
     nlive = st.n_live
     Kc = 32 * ((args.window + 31) // 32)
@@ -704,6 +706,9 @@ def main():
                   "n_exact_snr": st.n_exact, "n_near_threshold": st.n_near,
                   "n_uncertain_fp32": st.n_uncertain, "n_resolved": st.n_resolved,
                   "resolved_per_iteration": [int(x) for x in sub.history()],
+                  "iteration_ms_host_driven": [round(x, 4) for x in per_iter],
+                  "late_iteration_ms_median": (float(np.median(per_iter[2:]))
+                                               if len(per_iter) > 2 else None),
                   "prepass_ms": pre_ms, "loop_ms": loop_ms},
         "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "fp32_screen": screen, "batch": batch, "serve": serve,

@@ -281,6 +281,12 @@ int sub_profile(sub_ctx* ctx, float ms[SUB_K_COUNT], int32_t launches[SUB_K_COUN
 int sub_snr_check(sub_ctx* ctx, int64_t* src, float* rho2_screen, double* rho2_exact,
                   int32_t* nbins, int64_t cap, int64_t* n_out);
 
+/* The last sub_profile's device time per loop iteration and kernel: ms[i * SUB_K_COUNT + k]
+ * for iteration i + 1 (the catalog pass is not included) and kernel k, for min(cap,
+ * iterations) iterations.  Returns the number of iterations profiled (0 before any
+ * sub_profile), or SUB_EINVAL. */
+int sub_get_profile_iterations(sub_ctx* ctx, float* ms, int32_t cap);
+
 /* Largest inputs of sub_running_mean_noalloc (the size of its static scratch). */
 #define SUB_NOALLOC_MAX_BINS 1310720
 #define SUB_NOALLOC_MAX_WINDOW 8192

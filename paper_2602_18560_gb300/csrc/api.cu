@@ -273,7 +273,8 @@ static int reserve_sources(sub_ctx* c, int64_t n) {
   if (n > c->cap_N || c->A == nullptr) {
     drop_graph(c);
     dfree(c, c->A); dfree(c, c->f); dfree(c, c->fdot); dfree(c, c->resolved);
-    void* cds[] = {c->cd.src, c->cd.pk, c->cd.len, c->cd.a2, c->cd.lo, c->cd.hi, c->cd.res};
+    void* cds[] = {c->cd.src, c->cd.pk, c->cd.len, c->cd.a2, c->cd.amp, c->cd.lo, c->cd.hi,
+                   c->cd.res};
     for (void* q : cds) dfree(c, q);
     c->A = c->f = c->fdot = nullptr;
     c->resolved = nullptr;
@@ -287,7 +288,8 @@ static int reserve_sources(sub_ctx* c, int64_t n) {
         (rc = dalloc(c, (void**)&c->fdot, m * 8)) || (rc = dalloc(c, (void**)&c->resolved, m)) ||
         (rc = dalloc(c, (void**)&c->cd.src, m * 8)) || (rc = dalloc(c, (void**)&c->cd.pk, m * 16)) ||
         (rc = dalloc(c, (void**)&c->cd.len, m * 4)) ||
-        (rc = dalloc(c, (void**)&c->cd.a2, m * 8)) || (rc = dalloc(c, (void**)&c->cd.lo, m * 8)) ||
+        (rc = dalloc(c, (void**)&c->cd.a2, m * 8)) || (rc = dalloc(c, (void**)&c->cd.amp, m * 8)) ||
+        (rc = dalloc(c, (void**)&c->cd.lo, m * 8)) ||
         (rc = dalloc(c, (void**)&c->cd.hi, m * 8)) || (rc = dalloc(c, (void**)&c->cd.res, m))) {
       return rc;
     }
@@ -457,6 +459,11 @@ struct KTimer {
     cudaEventElapsedTime(&ms, c->ev_k[0], c->ev_k[1]);
     c->prof_ms[k] += ms;
     c->prof_n[k] += 1;
+    if (c->prof_iter >= 0) {
+      if ((int)c->prof_iter_ms.size() < (c->prof_iter + 1) * SUB_K_COUNT)
+        c->prof_iter_ms.resize((size_t)(c->prof_iter + 1) * SUB_K_COUNT, 0.f);
+      c->prof_iter_ms[(size_t)c->prof_iter * SUB_K_COUNT + k] += ms;
+    }
   }
 };
 
@@ -618,10 +625,13 @@ static int build_graph(sub_ctx* c) {
 }
 
 static int run_host_loop(sub_ctx* c) {
+  c->prof_iter = -1;
+  c->prof_iter_ms.clear();
   CU(cudaEventRecord(c->ev_start, c->stream), c);
   CU(enqueue_pre(c, c->stream), c);
   CU(cudaEventRecord(c->ev_pre, c->stream), c);
   for (int it = 0; it <= c->p.max_iter + 1; ++it) {
+    c->prof_iter = it;
     CU(enqueue_body(c, c->stream, 0ull, 0), c);
     CU(cudaMemcpyAsync(c->h_rs, c->rs, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream), c);
     CU(cudaStreamSynchronize(c->stream), c);
@@ -975,6 +985,14 @@ extern "C" int sub_snr_check(sub_ctx* c, int64_t* src, float* rho2_screen, doubl
   dfree(c, buf);
   if (e) { set_err(c, "sub_snr_check: %s", cudaGetErrorString(e)); return SUB_ECUDA; }
   return SUB_OK;
+}
+
+extern "C" int sub_get_profile_iterations(sub_ctx* c, float* ms, int32_t cap) {
+  if (!c || (cap > 0 && !ms)) return SUB_EINVAL;
+  const int m = (int)(c->prof_iter_ms.size() / SUB_K_COUNT);
+  const int w = m < cap ? m : cap;
+  for (int i = 0; i < w * SUB_K_COUNT; ++i) ms[i] = c->prof_iter_ms[(size_t)i];
+  return m;
 }
 
 extern "C" int64_t sub_device_bytes(const sub_ctx* c) { return c ? c->bytes : 0; }

@@ -109,6 +109,46 @@ __device__ __forceinline__ void q_parts(double q, u64* c0, u64* c1, u64* c2) {
   *c2 = v.hi;
 }
 
+// Fixed-point units of the deposit of a single-bin source, Q = A^2 gq (units of 2^-96 of the
+// bin's S_instr; gq = 2^96 (T/5) R / S_instr), from the integer mantissas: the top 64 bits
+// of A's mantissa squared, times gq's, the products truncated.  Q is within 2^-61 of the
+// exact A^2 gq (the FP64 product RN(RN(A A) gq) is within 2^-52) and takes no FP64
+// instruction, which on this GPU run at a small fraction of the integer rate.
+//   c1, c2 : the parts the spectrum words take (bits 32-63 and 64-127 of Q)
+//   qbits  : Q as the bits of a double (mantissa truncated), for comparisons with the bits
+//            of non-negative doubles
+// Returns false when Q >= 2^127 (beyond the fixed-point range).  A finite (its sign does not
+// matter), gq > 0 finite; A or gq zero or subnormal gives Q = 0.
+__device__ __forceinline__ bool q_single(double A, double gq, u64* c1, u64* c2, u64* qbits) {
+  const u64 ba = (u64)__double_as_longlong(A), bg = (u64)__double_as_longlong(gq);
+  const int ea = (int)((ba >> 52) & 0x7FF), eg = (int)((bg >> 52) & 0x7FF);
+  *c1 = 0ull;
+  *c2 = 0ull;
+  *qbits = 0ull;
+  if (ea == 0 || eg == 0) return true;
+  const u64 a = ((ba & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;
+  const u64 g = ((bg & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;
+  const u64 a2 = __umul64hi(a, a);  // in [2^62, 2^64)
+  const u64 p = __umul64hi(a2, g);  // in [2^61, 2^64)
+  const int sh = 2 * ea + eg - 3130;  // Q = p 2^sh
+  const int lz = __clzll((long long)p);
+  const int E = sh + 63 - lz;         // Q in [2^E, 2^(E+1))
+  if (E >= 127) return false;
+  if (E >= -1022) *qbits = ((u64)(E + 1023) << 52) | ((p << (lz + 1)) >> 12);
+  const int t = sh - 32;              // Q / 2^32 = p 2^t
+  if (t >= 32) {
+    *c2 = p << (t - 32);
+  } else if (t >= 0) {
+    *c1 = (u64)((unsigned)p << t);
+    *c2 = p >> (32 - t);
+  } else if (t > -64) {
+    const u64 y = p >> (-t);
+    *c1 = y & 0xFFFFFFFFull;
+    *c2 = y >> 32;
+  }
+  return true;
+}
+
 // f * T rounded to nearest (ties to even), computed exactly in integer arithmetic, returned
 // as x = u + 1/2 split into its integer part k and the top 24 bits of its fraction.  T is
 // given by its 53-bit integer mantissa mT and exponent eT (T = mT 2^eT).  Returns false when

@@ -79,6 +79,8 @@ struct sub_ctx {
   cudaEvent_t ev_k[2] = {nullptr, nullptr};
   float prof_ms[SUB_K_COUNT];
   int prof_n[SUB_K_COUNT];
+  std::vector<float> prof_iter_ms;  // per profiled iteration, per kernel (SUB_K_*)
+  int prof_iter = -1;               // iteration being profiled (-1: the catalog pass)
   bool profiling = false;
 };
 

@@ -104,6 +104,18 @@ __device__ __forceinline__ void remove_q(unsigned long long* acc, long long j, d
   if (c2) atomicAdd(a + 2, (u64)(0ull - c2));
 }
 
+// The two parts of a single-bin deposit (q_single) added to, or taken from, bin j.
+__device__ __forceinline__ void add_parts(unsigned long long* acc, long long j, u64 c1, u64 c2) {
+  u64* a = acc + 4 * j;
+  if (c1) atomicAdd(a + 1, c1);
+  if (c2) atomicAdd(a + 2, c2);
+}
+__device__ __forceinline__ void sub_parts(unsigned long long* acc, long long j, u64 c1, u64 c2) {
+  u64* a = acc + 4 * j;
+  if (c1) atomicAdd(a + 1, (u64)(0ull - c1));
+  if (c2) atomicAdd(a + 2, (u64)(0ull - c2));
+}
+
 // Estimator input of bin j: P_j = S_j Q_j 2^-96, or x[j].
 __device__ __forceinline__ double spec_value(const SpecIn& in, long long j) {
   if (in.acc) {
@@ -141,14 +153,8 @@ void launch_power_out(const unsigned long long* acc, const double* S, long long 
 // therefore have kAccReplicas private copies (words 1 and 2 of every bin), a source
 // picking one by its index; a fold adds them into the spectrum after the pass.  Integer
 // sums, so the result does not depend on the split.
-__device__ __forceinline__ void deposit_rep(AccReplicas rep, long long j, int r, double q,
-                                            unsigned* err) {
-  if ((u64)__double_as_longlong(q) >= 0x47E0000000000000ull) {
-    atomicOr(err, ERR_RANGE);
-    return;
-  }
-  u64 c0, c1, c2;
-  q_parts(q, &c0, &c1, &c2);
+__device__ __forceinline__ void add_parts_rep(AccReplicas rep, long long j, int r, u64 c1,
+                                              u64 c2) {
   u64* a = rep.w + 2 * ((size_t)r * rep.nbins + j);
   if (c1) atomicAdd(a + 0, c1);
   if (c2) atomicAdd(a + 1, c2);
@@ -203,22 +209,28 @@ __device__ __forceinline__ double sweep_deposit(const Sweep& sw, const Grid& g, 
 // FP64 path of the catalog pass for one source: the sweep, its pieces deposited; returns
 // the sum of its contributions.  Kept out of line so that none of it is speculated into the
 // common path.
-__device__ __noinline__ double prepass_slow(double a2, double fs, double fds, const Grid g,
+// A single-bin sweep is deposited as q_single(A, gq) exactly as the common path deposits it, so
+// that every single-bin source is removed the same way whichever path deposited it.
+__device__ __noinline__ double prepass_slow(double A, double fs, double fds, const Grid g,
                                             const Tables tb, unsigned long long* acc,
                                             unsigned* err) {
   Sweep sw = make_sweep(fs, fds, g.T, g.T2);
   if (sw.ka == sw.kb) {
     long long j = sw.ka - g.k_lo;
     if (j >= 0 && j < g.nb) {
-      double q = __dmul_rn(a2, tb.gq[j]);
-      deposit_q(acc, j, q, err);
-      return q;
+      u64 c1, c2, qb;
+      if (!q_single(A, tb.gq[j], &c1, &c2, &qb)) {
+        atomicOr(err, ERR_RANGE);
+        return 0.0;
+      }
+      add_parts(acc, j, c1, c2);
+      return __longlong_as_double((long long)qb);
     }
     return 0.0;
   }
   long long k0, k1;
   sweep_bins(sw, g, &k0, &k1);
-  return sweep_deposit(sw, g, tb, a2, k0, k1, 0, 1, acc, err);
+  return sweep_deposit(sw, g, tb, __dmul_rn(A, A), k0, k1, 0, 1, acc, err);
 }
 
 // Bins the FP64 path of a source would walk (0 for a single-bin sweep).
@@ -232,28 +244,30 @@ __device__ __noinline__ long long slow_span(double fs, double fds, const Grid g)
 
 // The FP64 path of one long sweep, by a whole warp: the lanes share its bins; the sum of the
 // contributions comes back in every lane.
-__device__ __noinline__ double prepass_slow_warp(double a2, double fs, double fds, const Grid g,
+__device__ __noinline__ double prepass_slow_warp(double A, double fs, double fds, const Grid g,
                                                  const Tables tb, unsigned long long* acc,
                                                  unsigned* err) {
   const int lane = threadIdx.x & 31;
   Sweep sw = make_sweep(fs, fds, g.T, g.T2);
   long long k0, k1;
   sweep_bins(sw, g, &k0, &k1);
-  double r = sweep_deposit(sw, g, tb, a2, k0, k1, lane, 32, acc, err);
+  double r = sweep_deposit(sw, g, tb, __dmul_rn(A, A), k0, k1, lane, 32, acc, err);
   for (int o = 16; o > 0; o >>= 1) r = __dadd_rn(r, __shfl_xor_sync(0xFFFFFFFFu, r, o));
   return r;
 }
 
 // Record of a kept candidate (rare; out of line).
-__device__ __noinline__ void emit_candidate(Cands cd, long long c, long long s, double a2,
+__device__ __noinline__ void emit_candidate(Cands cd, long long c, long long s, double A,
                                             double fs, double fds, const Grid g) {
   Sweep sw = make_sweep(fs, fds, g.T, g.T2);
+  const double a2 = __dmul_rn(A, A);
   cd.src[c] = s;
   cd.pk[c] = make_int4((int)(sw.ka - g.k_lo), (int)(sw.kb - sw.ka + 1),
                        __float_as_int(dbl_to_f32_scaled(a2, 160)),
                        __float_as_int((float)(sw.lo - (double)sw.ka)));
   cd.len[c] = (float)(sw.hi - sw.lo);
   cd.a2[c] = a2;
+  cd.amp[c] = A;
   cd.lo[c] = sw.lo;
   cd.hi[c] = sw.hi;
   cd.res[c] = 0;
@@ -262,7 +276,7 @@ __device__ __noinline__ void emit_candidate(Cands cd, long long c, long long s, 
 // The decision for one source once r (its rho_0^2 / 4 in units of 2^-96) is known: count
 // it among the paper's candidates, and keep it when it can still be resolved.
 __device__ __forceinline__ void prepass_decide(double r, u64 tk_bits, u64 tl_bits, bool valid,
-                                               long long s, double a2, double fs, double fds,
+                                               long long s, double A, double fs, double fds,
                                                const Grid& g, Cands& cd, RunState* rs,
                                                unsigned long long& nkappa) {
   const int lane = threadIdx.x & 31;
@@ -280,7 +294,7 @@ __device__ __forceinline__ void prepass_decide(double r, u64 tk_bits, u64 tl_bit
     b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
     if (live) {
       long long c = (long long)b0 + __popc(m & ((1u << lane) - 1u));
-      emit_candidate(cd, c, s, a2, fs, fds, g);
+      emit_candidate(cd, c, s, A, fs, fds, g);
     }
   }
 }
@@ -341,7 +355,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 // slow source delays no other warp.
 constexpr int kPreConsumers = 8;
 constexpr int kPrepassThreads = (kPreConsumers + 1) * 32;
-constexpr int kPreTile = 1024;                                // sources per staged tile
+constexpr int kPreTile = 512;                                 // sources per staged tile
 constexpr int kPreStages = 4;                                 // tiles in flight per CTA
 constexpr int kPreWarpSrc = kPreTile / kPreConsumers;         // sources per consumer warp
 constexpr int kPrePer = kPreWarpSrc / 32;                     // sources per lane per tile
@@ -419,10 +433,9 @@ __device__ __forceinline__ void prepass_drain_warp(const CatalogRef* __restrict_
   const int lane = threadIdx.x & 31;
   const bool valid = lane < cnt;
   long long s = valid ? q[lane] : 0;
-  double a2 = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
+  double a = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
   bool wide = false;
   if (valid) {
-    double a;
     if (cat->staged == kCatGenerated) {
       const double3 gsrc = gen_source_at(cat, s);
       a = gsrc.x;
@@ -433,21 +446,20 @@ __device__ __forceinline__ void prepass_drain_warp(const CatalogRef* __restrict_
       fs = f[s];
       fds = fdot[s];
     }
-    a2 = __dmul_rn(a, a);
     wide = slow_span(fs, fds, g) > kSlowLaneBins;
-    if (!wide) r = prepass_slow(a2, fs, fds, g, tb, acc, &rs->err);
+    if (!wide) r = prepass_slow(a, fs, fds, g, tb, acc, &rs->err);
   }
-  prepass_decide(r, tk_bits, tl_bits, valid && !wide, s, a2, fs, fds, g, cd, rs, nkappa);
+  prepass_decide(r, tk_bits, tl_bits, valid && !wide, s, a, fs, fds, g, cd, rs, nkappa);
   unsigned pending = __ballot_sync(0xFFFFFFFFu, wide);
   while (pending) {
     const int src = __ffs(pending) - 1;
     pending &= pending - 1;
     const long long sw_s = __shfl_sync(0xFFFFFFFFu, s, src);
-    const double sw_a2 = __shfl_sync(0xFFFFFFFFu, a2, src);
+    const double sw_a = __shfl_sync(0xFFFFFFFFu, a, src);
     const double sw_f = __shfl_sync(0xFFFFFFFFu, fs, src);
     const double sw_fd = __shfl_sync(0xFFFFFFFFu, fds, src);
-    const double rw = prepass_slow_warp(sw_a2, sw_f, sw_fd, g, tb, acc, &rs->err);
-    prepass_decide(rw, tk_bits, tl_bits, lane == 0, sw_s, sw_a2, sw_f, sw_fd, g, cd, rs,
+    const double rw = prepass_slow_warp(sw_a, sw_f, sw_fd, g, tb, acc, &rs->err);
+    prepass_decide(rw, tk_bits, tl_bits, lane == 0, sw_s, sw_a, sw_f, sw_fd, g, cd, rs,
                    nkappa);
   }
 }
@@ -480,7 +492,7 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity,
   return false;
 }
 
-__global__ void __launch_bounds__(kPrepassThreads, 2) k_prepass(
+__global__ void __launch_bounds__(kPrepassThreads, 3) k_prepass(
     const CatalogRef* __restrict__ cat, Grid g, Tables tb, double thr_kappa, double thr_live,
     unsigned long long* __restrict__ acc, AccReplicas rep, Cands cd, RunState* rs,
     int test_flags) {
@@ -613,27 +625,30 @@ __global__ void __launch_bounds__(kPrepassThreads, 2) k_prepass(
     for (int k = 0; k < kPrePer; ++k) {
       const long long s = t * kPreTile + base + 32 * k;
       bool valid = false, slow = false;
-      double a2 = 0.0, r = 0.0;
-      const double fs = fv[k], fds = dv[k];
+      double r = 0.0;
+      const double a = av[k], fs = fv[k], fds = dv[k];
       if (s < N) {
-        a2 = __dmul_rn(av[k], av[k]);
+        // finite inputs, and A^2 finite (|A| < 2^512): else the source is refused below
+        const bool fin = finite3(a, fs, fds) &&
+                         (((u64)__double_as_longlong(a) >> 52) & 0x7FF) < 1535;
         long long k0 = 0;
-        bool single = single_bin(fs, fds, g, &k0);
-        if (single && !finite3(a2, fs, fds)) {
-          single = false;  // a non-finite amplitude or frequency derivative: refused below
-        }
+        const bool single = fin && single_bin(fs, fds, g, &k0);
         if (single) {
           valid = true;
           const long long j = k0 - g.k_lo;
           if (j >= 0 && j < g.nb) {
-            const double q = __dmul_rn(a2, tb.gq[j]);
-            if (j < rep.nbins)
-              deposit_rep(rep, j, (int)(s & (kAccReplicas - 1)), q, &rs->err);
-            else
-              deposit_q(acc, j, q, &rs->err);
-            r = q;
+            u64 c1, c2, qb;
+            if (q_single(a, tb.gq[j], &c1, &c2, &qb)) {
+              if (j < rep.nbins)
+                add_parts_rep(rep, j, (int)(s & (kAccReplicas - 1)), c1, c2);
+              else
+                add_parts(acc, j, c1, c2);
+              r = __longlong_as_double((long long)qb);
+            } else {
+              atomicOr(&rs->err, ERR_RANGE);
+            }
           }
-        } else if (finite3(a2, fs, fds)) {
+        } else if (fin) {
           slow = true;
         } else {
           atomicOr(&rs->err, ERR_INPUT);  // the source is skipped; the run reports it
@@ -643,7 +658,7 @@ __global__ void __launch_bounds__(kPrepassThreads, 2) k_prepass(
       const unsigned sm = __ballot_sync(0xFFFFFFFFu, slow);
       if (slow) myq[qn + __popc(sm & ((1u << lane) - 1u))] = s;
       qn += __popc(sm);
-      prepass_decide(r, tk_bits, tl_bits, valid, s, a2, fs, fds, g, cd, rs, nkappa);
+      prepass_decide(r, tk_bits, tl_bits, valid, s, a, fs, fds, g, cd, rs, nkappa);
       if (qn >= 32) {
         __syncwarp();
         prepass_drain_warp(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, myq, 32,
@@ -666,7 +681,7 @@ void launch_prepass(const CatalogRef* cat, long long cap, const Grid& g, const T
                     double thr_kappa, double thr_live, unsigned long long* acc, AccReplicas rep,
                     Cands cd, RunState* rs, int nsm, int test_flags, cudaStream_t st) {
   long long tiles = (cap + kPreTile - 1) / kPreTile;
-  long long lim = (long long)nsm * 2;  // resident CTAs (launch bounds, shared memory)
+  long long lim = (long long)nsm * 3;  // resident CTAs (launch bounds, shared memory)
   int bl = (int)(tiles < lim ? (tiles < 1 ? 1 : tiles) : lim);
   k_prepass<<<bl, kPrepassThreads, kPrepassSmem, st>>>(cat, g, tb, thr_kappa, thr_live, acc,
                                                        rep, cd, rs, test_flags);
@@ -1753,7 +1768,8 @@ __device__ __forceinline__ void remove_part(const Cands& cd, long long c, const 
   if (sw.ka == sw.kb) {
     long long j = sw.ka - g.k_lo;
     if (off == 0 && j >= 0 && j < g.nb) {
-      remove_q(acc, j, __dmul_rn(a2, tb.gq[j]));
+      u64 c1, c2, qb;
+      if (q_single(cd.amp[c], tb.gq[j], &c1, &c2, &qb)) sub_parts(acc, j, c1, c2);
       d.mark_next(j / Kc);
     }
     return;

@@ -17,6 +17,7 @@ struct Cands {
                       //   z = bits of A^2 * 2^160 (FP32), w = bits of lo - ka (FP32)
   float* len;         // hi - lo (FP32 screen of sweeps over more than one bin)
   double* a2;         // A^2 (exact path)
+  double* amp;        // A (removal of a single-bin source: the same units it deposited)
   double* lo;         // sweep endpoints in bin units (exact path)
   double* hi;
   unsigned char* res; // 1 once resolved

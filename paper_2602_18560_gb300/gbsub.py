@@ -109,7 +109,7 @@ EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_load_gen
            "sub_get_catalog", "sub_run", "sub_get_stats",
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
            "sub_get_tables", "sub_get_timing", "sub_get_work", "sub_coarse_grain", "sub_profile",
-           "sub_device_bytes", "sub_snr_check",
+           "sub_device_bytes", "sub_snr_check", "sub_get_profile_iterations",
            "sub_destroy",
            "sub_last_error", "sub_running_mean_noalloc", "sub_get_power", "sub_batch_create",
            "sub_batch_run", "sub_batch_last_ms", "sub_batch_last_error", "sub_batch_destroy",
@@ -159,6 +159,7 @@ def lib(build_if_missing: bool = True):
             "sub_profile": (i32, [P, P, P, ctypes.POINTER(sub_stats)]),
             "sub_device_bytes": (i64, [P]),
             "sub_snr_check": (i32, [P, P, P, P, P, i64, ctypes.POINTER(i64)]),
+            "sub_get_profile_iterations": (i32, [P, P, i32]),
             "sub_destroy": (None, [P]),
             "sub_last_error": (ctypes.c_char_p, [P]),
             "sub_running_mean_noalloc": (i32, [P, P, i64, i32, P]),
@@ -399,6 +400,14 @@ def sub_profile(ctx):
     return {k: (ms[i], n[i]) for i, k in enumerate(KERNELS)}, st
 
 
+def sub_get_profile_iterations(ctx, cap=4096):
+    """Per iteration of the last sub_profile: {kernel: ms}."""
+    buf = (ctypes.c_float * (cap * len(KERNELS)))()
+    m = _check(ctx, lib().sub_get_profile_iterations(ctx, buf, cap))
+    return [{k: buf[i * len(KERNELS) + j] for j, k in enumerate(KERNELS)}
+            for i in range(min(m, cap))]
+
+
 def sub_device_bytes(ctx) -> int:
     return lib().sub_device_bytes(ctx)
 
@@ -490,6 +499,9 @@ class Subtraction:
 
     def profile(self):
         return sub_profile(self.ctx)
+
+    def profile_iterations(self):
+        return sub_get_profile_iterations(self.ctx)
 
     @property
     def grid(self):
