@@ -853,7 +853,7 @@ __device__ __forceinline__ void cmp_keep(K& k, int& x, K ko, int xo, bool keep_m
 // unchanged elements that precede it, found by a binary search of the old order.  This is
 // the (key, position) order the full sort produces, so the two paths write the same arrays.
 // Returns false, having written nothing, when more than kResortMax positions changed.
-constexpr int kResortMax = 128;
+constexpr int kResortMax = kChangeMax;
 
 template <typename K>
 __device__ __forceinline__ bool key_pos_less(K ka, int pa, K kb, int pb) {
@@ -862,11 +862,13 @@ __device__ __forceinline__ bool key_pos_less(K ka, int pa, K kb, int pb) {
 
 template <int E, typename K>
 __device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __restrict__ skey_c,
-                                   uint16_t* __restrict__ srank_c, unsigned char* raw) {
+                                   uint16_t* __restrict__ srank_c, unsigned char* raw,
+                                   const ChangeLog& log, int b) {
   K* old_k = (K*)raw;                                // [kpad] old keys, in old sorted order
   K* ch_k = old_k + kpad;                            // [kResortMax] changed: new keys
   K* cs_k = ch_k + kResortMax;                       // [kResortMax] the same, sorted
-  uint16_t* old_p = (uint16_t*)(cs_k + kResortMax);  // [kpad] position of each old index
+  K* ch_o = cs_k + kResortMax;                       // [kResortMax] changed: old keys
+  uint16_t* old_p = (uint16_t*)(ch_o + kResortMax);  // [kpad] position of each old index
   uint16_t* csum = old_p + kpad;                     // [kpad + 2] changed before an old index
   uint16_t* ch_p = csum + kpad + 2;                  // [kResortMax] changed: positions
   uint16_t* cs_p = ch_p + kResortMax;                // [kResortMax] the same, sorted
@@ -913,6 +915,7 @@ __device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __r
       const int slot = atomicAdd(&n_changed, 1);
       if (slot < kResortMax) {
         ch_k[slot] = knew[a];
+        ch_o[slot] = old_k[r[a]];
         ch_p[slot] = (uint16_t)p;
       }
     }
@@ -921,6 +924,16 @@ __device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __r
   const int C = n_changed;
   __syncthreads();  // every thread has read the count before the caller reuses shared memory
   if (C > kResortMax) return false;
+  // the changes, for the median tiles that read this chunk
+  if (log.cnt) {
+    for (int t = tid; t < C; t += T) {
+      const size_t at = (size_t)b * kChangeMax + t;
+      log.pos[at] = ch_p[t];
+      log.old_key[at] = (unsigned long long)ch_o[t];
+      log.new_key[at] = (unsigned long long)ch_k[t];
+    }
+    if (tid == 0) log.cnt[b] = C;
+  }
   if (C == 0) return true;
   // 3. csum[i] = changed elements among old indices < i (exclusive scan in old order)
   int f[E], run = 0;
@@ -1009,7 +1022,8 @@ __device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __r
 template <int E, typename K>
 __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
                                                      K* __restrict__ skey,
-                                                     uint16_t* __restrict__ srank, Dirty d) {
+                                                     uint16_t* __restrict__ srank, Dirty d,
+                                                     ChangeLog log) {
   extern __shared__ __align__(16) unsigned char sort_raw[];
   K* sm_keys = (K*)sort_raw;
   uint16_t* sm_idx = (uint16_t*)(sm_keys + pl.kpad);
@@ -1035,10 +1049,12 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
       k[a] = kv;
       x[a] = i;
     }
-    if (resort && resort_few_changes<E, K>(k, len, kpad, skey + base, srank + base, sort_raw)) {
+    if (resort &&
+        resort_few_changes<E, K>(k, len, kpad, skey + base, srank + base, sort_raw, log, b)) {
       __syncthreads();  // before the next chunk overwrites shared memory
       continue;
     }
+    if (log.cnt && threadIdx.x == 0) log.cnt[b] = -1;  // sorted from scratch: no change list
     bool first_smem = true;
     for (int kk = 2; kk <= kpad; kk <<= 1) {
       int jj = kk >> 1;
@@ -1140,11 +1156,12 @@ static int persistent_grid(const SmoothPlan& pl, int items, int resident) {
 
 // Launch one k_chunk_sort instantiation with the key buffer cast to its key type.
 template <typename K>
-static void launch_sort_as(void (*kern)(SpecIn, long long, SmoothPlan, K*, uint16_t*, Dirty),
+static void launch_sort_as(void (*kern)(SpecIn, long long, SmoothPlan, K*, uint16_t*, Dirty,
+                                        ChangeLog),
                            int bl, int th, size_t smem, cudaStream_t st, SpecIn in, long long n,
                            const SmoothPlan& pl, unsigned long long* skey, uint16_t* srank,
-                           Dirty d) {
-  kern<<<bl, th, smem, st>>>(in, n, pl, (K*)skey, srank, d);
+                           Dirty d, ChangeLog log) {
+  kern<<<bl, th, smem, st>>>(in, n, pl, (K*)skey, srank, d, log);
 }
 
 static int sort_per_thread(const SmoothPlan& pl) {
@@ -1156,7 +1173,7 @@ static size_t sort_smem(const SmoothPlan& pl) {
   const size_t kb = pl.fp32_keys ? 4 : 8;
   const size_t full = (size_t)pl.kpad * (kb + sizeof(uint16_t));
   const size_t few = (size_t)pl.kpad * (kb + 2 + 1) + (size_t)(pl.kpad + 2) * 2 +
-                     (size_t)kResortMax * 2 * (kb + 2);
+                     (size_t)kResortMax * 2 * (kb + 2) + (size_t)kResortMax * kb;
   return full > few ? full : few;
 }
 template <typename K, typename F>
@@ -1176,12 +1193,12 @@ static void with_sort_kernel(const SmoothPlan& pl, F fn) {
 }
 
 void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
-                       uint16_t* srank, Dirty d, cudaStream_t st) {
+                       uint16_t* srank, Dirty d, ChangeLog log, cudaStream_t st) {
   const size_t smem = sort_smem(pl);
   const int th = sort_threads(pl);
   const int bl = persistent_grid(pl, pl.nch, pl.res_sort);
   with_sort_kernel(pl, [&](auto kern) {
-    launch_sort_as(kern, bl, th, smem, st, in, n, pl, skey, srank, d);
+    launch_sort_as(kern, bl, th, smem, st, in, n, pl, skey, srank, d, log);
   });
 }
 
@@ -1212,15 +1229,82 @@ __device__ __forceinline__ int wm_rank1(const u64* rkl, int i) {
   return (int)(e >> 32) + __popc((uint32_t)e & ((1u << (i & 31)) - 1u));
 }
 
+// Median of output j from the selected elements: the upper median at tile-local position pa
+// and, for an even count, the lower one at pb; keys read through the chunks' sorted arrays.
+template <typename K>
+__device__ __forceinline__ double median_value(const K* __restrict__ skey,
+                                               const uint16_t* __restrict__ srank,
+                                               long long span, int Kc, int cnt, int pa, int pb,
+                                               double inv_scale) {
+  const K khi = skey[span + (pa >= Kc ? Kc : 0) + srank[span + pa]];
+  double med;
+  if (cnt & 1) {
+    med = key_value<K>(khi, inv_scale);
+  } else {
+    const K klo = skey[span + (pb >= Kc ? Kc : 0) + srank[span + pb]];
+    med = __dmul_rn(__dadd_rn(key_value<K>(klo, inv_scale), key_value<K>(khi, inv_scale)), 0.5);
+  }
+  return __dmul_rn(kMedianBias, med);
+}
+
+// Tiles whose two chunks changed in at most this many positions in all take the incremental
+// path below.
+constexpr int kIncMax = 64;
+
+// Incremental selection for output j of a tile whose chunks changed in a few positions since
+// the previous estimate.  The element e the output selected last time (its anchor) had
+// exactly k elements of the window before it in the (key, position) order.  Keys only
+// changed at the listed positions, so now d = (listed window positions that come before e
+// now) - (those that came before e then) more elements precede e; the element with k before
+// it is then the d-th window element below e in the new merged order (above it for d < 0).
+// Returns the tile-local position of that element, or -1 when e itself changed or the walk
+// leaves the span (the caller then selects the whole tile again).
+template <typename K>
+__device__ __forceinline__ int median_move(const K* __restrict__ skey,
+                                           const uint16_t* __restrict__ srank, long long span,
+                                           int Kc, int M, int ws, int we, int pe,
+                                           const uint16_t* __restrict__ v_of_pos,
+                                           const uint16_t* __restrict__ pos_of, int nchg,
+                                           const uint16_t* cpos, const u64* cold,
+                                           const u64* cnew) {
+  if (pe < ws || pe > we) return -1;
+  const K ke = skey[span + (pe >= Kc ? Kc : 0) + srank[span + pe]];
+  int d = 0;
+  for (int c = 0; c < nchg; ++c) {
+    const int pc = cpos[c];
+    if (pc == pe) return -1;
+    if (pc < ws || pc > we) continue;
+    d += (key_pos_less<K>((K)cnew[c], pc, ke, pe) ? 1 : 0) -
+         (key_pos_less<K>((K)cold[c], pc, ke, pe) ? 1 : 0);
+  }
+  int r = v_of_pos[pe];
+  int guard = M;
+  while (d > 0 && guard-- > 0) {
+    if (--r < 0) return -1;
+    const int p = pos_of[r];
+    if (p >= ws && p <= we) --d;
+  }
+  while (d < 0 && guard-- > 0) {
+    if (++r >= M) return -1;
+    const int p = pos_of[r];
+    if (p >= ws && p <= we) ++d;
+  }
+  return d == 0 ? pos_of[r] : -1;
+}
+
 // One tile; returns the largest relative change of S_n among its outputs (conv_rtol).
+// inc: the tile's chunks changed in at most kIncMax positions since their previous sort
+// (chg0 listed in log for chunk u-1, chg1 for chunk u), and every output's previous selection
+// is in log.anchor.
 template <typename K>
 __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
                                               const uint16_t* __restrict__ srank, long long n,
                                               const SmoothPlan& pl, const SgOut& o, long long u,
-                                              unsigned char* sm_raw, int* zeros) {
+                                              unsigned char* sm_raw, int* zeros, bool inc,
+                                              int chg0, int chg1, const ChangeLog& log) {
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Kc = pl.Kc, M = 2 * Kc, LV = wm_levels(M);
-  const int nwm = M >> 5, ws = nwm + 1;  // words per level (one zero word of padding)
+  const int nwm = M >> 5, ws_ = nwm + 1;  // words per level (one zero word of padding)
   const int h = pl.W / 2;
   long long j_lo = (u - 1) * Kc + h, j_hi = u * Kc + h;
   if (j_lo < 0) j_lo = 0;
@@ -1234,17 +1318,42 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   double relmax = 0.0;
   K* sk = (K*)sm_raw;                                        // [M] sorted keys (step 1)
   uint16_t* seq1 = (uint16_t*)sm_raw;                        // [M] (steps 2-3, over sk)
-  uint16_t* src = seq1 + M;                                  // [M] rank -> element
-  uint16_t* seq0 = (uint16_t*)(sm_raw + sizeof(K) * (size_t)M);  // [M]
-  // [LV][ws]: per bitset word, its 32 bits (low half) and the ones before it (high half),
+  uint16_t* src = seq1 + M;                                  // [M] rank -> position
+  uint16_t* seq0 = (uint16_t*)(sm_raw + sizeof(K) * (size_t)M);  // [M] position -> rank
+  // [LV][ws_]: per bitset word, its 32 bits (low half) and the ones before it (high half),
   // so that a rank is one 64-bit load
   u64* rk = (u64*)(seq0 + M);
   uint16_t* mr = (uint16_t*)rk;  // [M] merged index of (chunk, sorted index) (step 1, over rk)
+  const size_t rk_bytes = (size_t)LV * ws_ * 8 > (size_t)2 * M ? (size_t)LV * ws_ * 8 : (size_t)2 * M;
+  u64* cold = (u64*)((unsigned char*)rk + rk_bytes);         // [2 kChangeMax] changes
+  u64* cnew = cold + 2 * kChangeMax;
+  uint16_t* cpos = (uint16_t*)(cnew + 2 * kChangeMax);
   __shared__ int warp_ones[32];
+  __shared__ int nchg;
 
   // 1. merged ranks.  Chunk u-1 precedes chunk u on equal keys (its positions are lower).
   for (int i = tid; i < len0; i += T) sk[i] = skey[span + i];
   for (int i = tid; i < len1; i += T) sk[Kc + i] = skey[span + Kc + i];
+  if (inc) {
+    // the changes of both chunks, at tile-local positions
+    if (tid == 0) nchg = 0;
+    __syncthreads();
+    for (int X = 0; X < 2; ++X) {
+      const long long cb = u - 1 + X;
+      const int c = X ? chg1 : chg0;
+      if (c <= 0) continue;
+      const int base = X ? nchg : 0;
+      for (int t = tid; t < c; t += T) {
+        const size_t at = (size_t)cb * kChangeMax + t;
+        cpos[base + t] = (uint16_t)(X * Kc + log.pos[at]);
+        cold[base + t] = log.old_key[at];
+        cnew[base + t] = log.new_key[at];
+      }
+      __syncthreads();
+      if (tid == 0) nchg += c;
+      __syncthreads();
+    }
+  }
   __syncthreads();
   {
     // merge path: thread t emits the merged indices [d0, d1) of the two sorted chunks,
@@ -1278,13 +1387,48 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
     if (q < (X ? len1 : len0)) {
       const int si = srank[span + p];
       v = mr[X * Kc + si];
-      src[v] = (uint16_t)((X << 15) | si);
+      src[v] = (uint16_t)p;
     } else {
       v = len0 + len1 + (X ? (Kc - len0) + (q - len1) : (q - len0));
+      src[v] = (uint16_t)p;  // outside the band: never inside a window
     }
     seq0[p] = (uint16_t)v;
   }
   __syncthreads();
+  const int nout = (int)(j_hi - j_lo);
+  int* anc_hi = log.anchor;
+  int* anc_lo = log.anchor ? log.anchor + n : nullptr;
+
+  if (inc) {
+    // 2'. every output moved from its previous selection
+    bool ok = true;
+    const int C = nchg;
+    for (int t = tid; t < nout && ok; t += T) {
+      const long long j = j_lo + t;
+      const long long s = j - h > 0 ? j - h : 0;
+      const long long e = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
+      const int cnt = (int)(e - s + 1);
+      const int ws = (int)(s - span), we = (int)(e - span);
+      const int pa = median_move<K>(skey, srank, span, Kc, M, ws, we, anc_hi[j] - (int)span,
+                                    seq0, src, C, cpos, cold, cnew);
+      int pb = pa;
+      if (!(cnt & 1))
+        pb = median_move<K>(skey, srank, span, Kc, M, ws, we, anc_lo[j] - (int)span, seq0, src,
+                            C, cpos, cold, cnew);
+      if (pa < 0 || pb < 0) {
+        ok = false;
+        break;
+      }
+      anc_hi[j] = (int)(span + pa);
+      anc_lo[j] = (int)(span + pb);
+      const double v = median_value<K>(skey, srank, span, Kc, cnt, pa, pb, inv_scale);
+      const double rel = sg_store(o, j, v);
+      relmax = rel > relmax ? rel : relmax;
+    }
+    if (!__syncthreads_or(!ok)) return relmax;
+    // an anchor changed (or could not be moved): select the whole tile again
+    relmax = 0.0;
+  }
 
   // 2. wavelet matrix.  Warp w owns the words [w wpw, (w + 1) wpw) of every level (M is a
   // multiple of 64: whole words).  A level takes two barriers: one after the warps have
@@ -1296,7 +1440,7 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   uint16_t* nxt = seq1;
   for (int l = 0; l < LV; ++l) {
     const int sh = LV - 1 - l;
-    u64* rkl = rk + (size_t)l * ws;
+    u64* rkl = rk + (size_t)l * ws_;
     int mine = 0;
     for (int k = w0; k < w1; ++k)
       mine += __popc(__ballot_sync(0xFFFFFFFFu, (cur[k * 32 + lane] >> sh) & 1));
@@ -1306,9 +1450,9 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
     const int c = lane < nwarp ? warp_ones[lane] : 0;
     int incl = c;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl += t;
+    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+      const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o2);
+      if (lane >= o2) incl += t;
     }
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     int run = __shfl_sync(0xFFFFFFFFu, incl - c, warp);
@@ -1336,7 +1480,6 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   }
 
   // 3. selections
-  const int nout = (int)(j_hi - j_lo);
   for (int t = tid; t < nout; t += T) {
     const long long j = j_lo + t;
     const long long s = j - h > 0 ? j - h : 0;
@@ -1346,7 +1489,7 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
     int la = (int)(s - span), ra = (int)(e + 1 - span), ka = cnt >> 1, va = 0;
     int lb = la, rb = ra, kb = ka > 0 ? ka - 1 : 0, vb = 0;
     for (int l = 0; l < LV; ++l) {
-      const u64* rkl = rk + (size_t)l * ws;
+      const u64* rkl = rk + (size_t)l * ws_;
       const int Z = zeros[l];
       const int oal = wm_rank1(rkl, la);
       const int oar = wm_rank1(rkl, ra);
@@ -1378,19 +1521,14 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
         vb |= bit;
       }
     }
-    const int ea = src[va];
-    const K khi = skey[span + (ea >> 15) * Kc + (ea & 0x7FFF)];
-    double med;
-    if (cnt & 1) {
-      med = key_value<K>(khi, inv_scale);
-    } else {
-      const int eb = src[vb];
-      const K klo = skey[span + (eb >> 15) * Kc + (eb & 0x7FFF)];
-      med = __dmul_rn(__dadd_rn(key_value<K>(klo, inv_scale), key_value<K>(khi, inv_scale)),
-                      0.5);
+    const int pa = src[va];
+    const int pb = (cnt & 1) ? pa : src[vb];
+    if (anc_hi) {
+      anc_hi[j] = (int)(span + pa);
+      anc_lo[j] = (int)(span + pb);
     }
-    double v = __dmul_rn(kMedianBias, med);
-    double rel = sg_store(o, j, v);
+    const double v = median_value<K>(skey, srank, span, Kc, cnt, pa, pb, inv_scale);
+    const double rel = sg_store(o, j, v);
     relmax = rel > relmax ? rel : relmax;
   }
   return relmax;
@@ -1399,17 +1537,33 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
 template <typename K>
 __global__ void __launch_bounds__(512, 2) k_median_wm(
     const K* __restrict__ skey, const uint16_t* __restrict__ srank,
-    long long n, SmoothPlan pl, SgOut o, Dirty d) {
+    long long n, SmoothPlan pl, SgOut o, Dirty d, ChangeLog log) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int zeros[16];
   double relmax = 0.0;
   const int nitem = d.count(kListTile, pl.nch + 1);
+  // after the first iteration of a tracked run, each dirty chunk's re-sort listed its changes
+  const bool tracked = d.base != nullptr && d.rs->iter > 0 && log.cnt != nullptr;
   int u_next = d.item(kListTile, blockIdx.x);  // loaded beside the count (grid <= list length)
   for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
     // a tile whose windows changed
     const int u = u_next;
     if (it + (int)gridDim.x < nitem) u_next = d.item(kListTile, it + gridDim.x);
-    double r = median_tile<K>(skey, srank, n, pl, o, u, sm_raw, zeros);
+    bool inc = false;
+    int chg[2] = {0, 0};
+    if (tracked) {
+      inc = true;
+      for (int X = 0; X < 2; ++X) {
+        const long long cb = u - 1 + X;
+        if (cb < 0 || cb >= pl.nch) continue;
+        if (!d.any(cb, 0)) continue;  // not re-sorted this time: unchanged
+        const int c = log.cnt[cb];
+        if (c < 0) inc = false;
+        chg[X] = c < 0 ? 0 : c;
+      }
+      if (chg[0] + chg[1] > kIncMax) inc = false;
+    }
+    double r = median_tile<K>(skey, srank, n, pl, o, u, sm_raw, zeros, inc, chg[0], chg[1], log);
     relmax = r > relmax ? r : relmax;
     __syncthreads();  // before the next tile overwrites shared memory
   }
@@ -1429,18 +1583,20 @@ size_t median_smem_bytes(int Kc, int key_bytes) {
   while ((1 << LV) < M) ++LV;
   size_t ws = (size_t)M / 32 + 1;
   size_t rk = (size_t)LV * ws * 8, mr = (size_t)2 * M;  // the merged indices sit over rk
-  return (size_t)key_bytes * M + (size_t)2 * M + (rk > mr ? rk : mr);
+  const size_t changes = (size_t)2 * kChangeMax * (8 + 8 + 2);
+  return (size_t)key_bytes * M + (size_t)2 * M + (rk > mr ? rk : mr) + changes;
 }
 
 void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
-                           const SmoothPlan& pl, SgOut o, Dirty d, cudaStream_t st) {
+                           const SmoothPlan& pl, SgOut o, Dirty d, ChangeLog log,
+                           cudaStream_t st) {
   int th = median_threads(pl);
   size_t smem = median_smem_bytes(pl.Kc, pl.fp32_keys ? 4 : 8);
   int bl = persistent_grid(pl, pl.nch + 1, pl.res_median);
   if (pl.fp32_keys)
-    k_median_wm<uint32_t><<<bl, th, smem, st>>>((const uint32_t*)skey, srank, n, pl, o, d);
+    k_median_wm<uint32_t><<<bl, th, smem, st>>>((const uint32_t*)skey, srank, n, pl, o, d, log);
   else
-    k_median_wm<u64><<<bl, th, smem, st>>>(skey, srank, n, pl, o, d);
+    k_median_wm<u64><<<bl, th, smem, st>>>(skey, srank, n, pl, o, d, log);
 }
 
 // ============================================================================ window mean

@@ -130,6 +130,20 @@ struct Dirty {
   }
 };
 
+// What the latest re-sort of each chunk changed: the positions whose key changed, with their
+// old and new keys (the bits of the sort keys, widened to 64 bits), at most kChangeMax per
+// chunk, or cnt = -1 when the chunk was sorted from scratch.  With them, and the element each
+// output selected last time (anchor), a median tile whose chunks changed in a few positions
+// moves every output's median from the previous one instead of selecting it again.
+constexpr int kChangeMax = 128;
+struct ChangeLog {
+  int* cnt;                     // [nch]
+  uint16_t* pos;                // [nch][kChangeMax], position within the chunk
+  unsigned long long* old_key;  // [nch][kChangeMax]
+  unsigned long long* new_key;  // [nch][kChangeMax]
+  int* anchor;                  // [2][n]: bin of the upper, then of the lower median element
+};
+
 // Output epilogue of the kernel that writes S_gal.
 struct SgOut {
   double* out;           // S_gal (or the median of median-then-mean)
@@ -208,12 +222,13 @@ void launch_max_bits(const double* x, long long n, unsigned long long* max_bits,
 
 // Sort every chunk of the input whose values changed (sorted keys, position -> rank).
 void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
-                       uint16_t* srank, Dirty d, cudaStream_t st);
+                       uint16_t* srank, Dirty d, ChangeLog log, cudaStream_t st);
 
 // out = C * running median from the sorted chunks, recomputed in the tiles whose windows
 // changed.
 void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
-                           const SmoothPlan& pl, SgOut o, Dirty d, cudaStream_t st);
+                           const SmoothPlan& pl, SgOut o, Dirty d, ChangeLog log,
+                           cudaStream_t st);
 size_t median_smem_bytes(int Kc, int key_bytes);
 
 // Exact 128-bit prefix sums of the input inside each chunk at a per-chunk scale sig[b];
