@@ -1229,46 +1229,60 @@ __device__ __forceinline__ int wm_rank1(const u64* rkl, int i) {
   return (int)(e >> 32) + __popc((uint32_t)e & ((1u << (i & 31)) - 1u));
 }
 
-// Median of output j from the selected elements: the upper median at tile-local position pa
-// and, for an even count, the lower one at pb; keys read through the chunks' sorted arrays.
+// Keys of the tile's positions (tile-local p: chunk u-1 below Kc, chunk u above): from the
+// sorted keys and sorted indices held in shared memory, or through the global arrays.
 template <typename K>
-__device__ __forceinline__ double median_value(const K* __restrict__ skey,
-                                               const uint16_t* __restrict__ srank,
-                                               long long span, int Kc, int cnt, int pa, int pb,
+struct TileKeys {
+  const K* sk;          // [2 Kc] sorted keys of both chunks (shared), or null
+  const uint16_t* srl;  // [2 Kc] sorted index of each position (shared)
+  const K* skey;
+  const uint16_t* srank;
+  long long span;
+  int Kc;
+  __device__ __forceinline__ K at(int p) const {
+    const int base = p >= Kc ? Kc : 0;
+    if (sk) return sk[base + srl[p]];
+    return skey[span + base + srank[span + p]];
+  }
+};
+
+// C times the median of a window from its selected elements: the upper median at tile-local
+// position pa and, for an even count, the lower one at pb.
+template <typename K>
+__device__ __forceinline__ double median_value(const TileKeys<K>& tk, int cnt, int pa, int pb,
                                                double inv_scale) {
-  const K khi = skey[span + (pa >= Kc ? Kc : 0) + srank[span + pa]];
+  const K khi = tk.at(pa);
   double med;
   if (cnt & 1) {
     med = key_value<K>(khi, inv_scale);
   } else {
-    const K klo = skey[span + (pb >= Kc ? Kc : 0) + srank[span + pb]];
+    const K klo = tk.at(pb);
     med = __dmul_rn(__dadd_rn(key_value<K>(klo, inv_scale), key_value<K>(khi, inv_scale)), 0.5);
   }
   return __dmul_rn(kMedianBias, med);
 }
 
 // Tiles whose two chunks changed in at most this many positions in all take the incremental
-// path below.
-constexpr int kIncMax = 64;
+// path below (chunks of at most kIncMaxKc bins, whose tiles keep their keys in shared memory).
+constexpr int kIncMax = 32;
+constexpr int kIncMaxKc = 2048;
 
-// Incremental selection for output j of a tile whose chunks changed in a few positions since
-// the previous estimate.  The element e the output selected last time (its anchor) had
-// exactly k elements of the window before it in the (key, position) order.  Keys only
-// changed at the listed positions, so now d = (listed window positions that come before e
-// now) - (those that came before e then) more elements precede e; the element with k before
-// it is then the d-th window element below e in the new merged order (above it for d < 0).
-// Returns the tile-local position of that element, or -1 when e itself changed or the walk
-// leaves the span (the caller then selects the whole tile again).
+// Incremental selection for one window of a tile whose chunks changed in a few positions since
+// the previous estimate.  The element e the window selected last time (its anchor) had
+// exactly k window elements before it in the (key, position) order.  Keys only changed at the
+// listed positions, so now d = (listed window positions that come before e now) - (those that
+// came before e then) more elements precede e; the element with k before it is then the d-th
+// window element below e in the new merged order (above it for d < 0).  Returns the tile-local
+// position of that element, or -1 when e itself changed or the walk leaves the span (the
+// caller then selects the whole tile again).
 template <typename K>
-__device__ __forceinline__ int median_move(const K* __restrict__ skey,
-                                           const uint16_t* __restrict__ srank, long long span,
-                                           int Kc, int M, int ws, int we, int pe,
+__device__ __forceinline__ int median_move(const TileKeys<K>& tk, int M, int ws, int we, int pe,
                                            const uint16_t* __restrict__ v_of_pos,
                                            const uint16_t* __restrict__ pos_of, int nchg,
                                            const uint16_t* cpos, const u64* cold,
                                            const u64* cnew) {
   if (pe < ws || pe > we) return -1;
-  const K ke = skey[span + (pe >= Kc ? Kc : 0) + srank[span + pe]];
+  const K ke = tk.at(pe);
   int d = 0;
   for (int c = 0; c < nchg; ++c) {
     const int pc = cpos[c];
@@ -1316,15 +1330,35 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   if (u >= 1) len0 = (n - span) < Kc ? (int)(n - span) : Kc;
   if (u < pl.nch) len1 = (n - span - Kc) < Kc ? (int)(n - span - Kc) : Kc;
   double relmax = 0.0;
-  K* sk = (K*)sm_raw;                                        // [M] sorted keys (step 1)
-  uint16_t* seq1 = (uint16_t*)sm_raw;                        // [M] (steps 2-3, over sk)
-  uint16_t* src = seq1 + M;                                  // [M] rank -> position
-  uint16_t* seq0 = (uint16_t*)(sm_raw + sizeof(K) * (size_t)M);  // [M] position -> rank
+  // Shared memory.  Chunks of at most kIncMaxKc bins: the sorted keys and the sorted index of
+  // every position stay for the selections; wider chunks put the wavelet's scratch over the
+  // keys and read keys through global memory (and never take the incremental path).
+  const bool keep = Kc <= kIncMaxKc;
+  K* sk = (K*)sm_raw;  // [M] sorted keys of chunks u-1 and u
+  uint16_t *srl = nullptr, *seq0, *src, *seq1;
+  if (keep) {
+    srl = (uint16_t*)(sk + M);  // [M] sorted index of each position
+    seq0 = srl + M;             // [M] position -> merged rank
+    src = seq0 + M;             // [M] merged rank -> position
+    seq1 = src + M;             // [M] wavelet scratch
+  } else {
+    seq1 = (uint16_t*)sm_raw;   // over the keys once they are merged
+    src = seq1 + M;
+    seq0 = (uint16_t*)(sm_raw + sizeof(K) * (size_t)M);
+  }
   // [LV][ws_]: per bitset word, its 32 bits (low half) and the ones before it (high half),
   // so that a rank is one 64-bit load
-  u64* rk = (u64*)(seq0 + M);
+  u64* rk = (u64*)((keep ? seq1 : seq0) + M);
   uint16_t* mr = (uint16_t*)rk;  // [M] merged index of (chunk, sorted index) (step 1, over rk)
-  const size_t rk_bytes = (size_t)LV * ws_ * 8 > (size_t)2 * M ? (size_t)LV * ws_ * 8 : (size_t)2 * M;
+  TileKeys<K> tk;
+  tk.sk = keep ? sk : nullptr;
+  tk.srl = srl;
+  tk.skey = skey;
+  tk.srank = srank;
+  tk.span = span;
+  tk.Kc = Kc;
+  const size_t rk_bytes =
+      (size_t)LV * ws_ * 8 > (size_t)2 * M ? (size_t)LV * ws_ * 8 : (size_t)2 * M;
   u64* cold = (u64*)((unsigned char*)rk + rk_bytes);         // [2 kChangeMax] changes
   u64* cnew = cold + 2 * kChangeMax;
   uint16_t* cpos = (uint16_t*)(cnew + 2 * kChangeMax);
@@ -1334,6 +1368,10 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   // 1. merged ranks.  Chunk u-1 precedes chunk u on equal keys (its positions are lower).
   for (int i = tid; i < len0; i += T) sk[i] = skey[span + i];
   for (int i = tid; i < len1; i += T) sk[Kc + i] = skey[span + Kc + i];
+  if (keep) {
+    for (int i = tid; i < len0; i += T) srl[i] = srank[span + i];
+    for (int i = tid; i < len1; i += T) srl[Kc + i] = srank[span + Kc + i];
+  }
   if (inc) {
     // the changes of both chunks, at tile-local positions
     if (tid == 0) nchg = 0;
@@ -1385,7 +1423,7 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
     const int X = p >= Kc, q = p - X * Kc;
     int v;
     if (q < (X ? len1 : len0)) {
-      const int si = srank[span + p];
+      const int si = keep ? srl[p] : srank[span + p];
       v = mr[X * Kc + si];
       src[v] = (uint16_t)p;
     } else {
@@ -1409,19 +1447,19 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
       const long long e = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
       const int cnt = (int)(e - s + 1);
       const int ws = (int)(s - span), we = (int)(e - span);
-      const int pa = median_move<K>(skey, srank, span, Kc, M, ws, we, anc_hi[j] - (int)span,
-                                    seq0, src, C, cpos, cold, cnew);
+      const int pa = median_move<K>(tk, M, ws, we, anc_hi[j] - (int)span, seq0, src, C, cpos,
+                                    cold, cnew);
       int pb = pa;
       if (!(cnt & 1))
-        pb = median_move<K>(skey, srank, span, Kc, M, ws, we, anc_lo[j] - (int)span, seq0, src,
-                            C, cpos, cold, cnew);
+        pb = median_move<K>(tk, M, ws, we, anc_lo[j] - (int)span, seq0, src, C, cpos, cold,
+                            cnew);
       if (pa < 0 || pb < 0) {
         ok = false;
         break;
       }
       anc_hi[j] = (int)(span + pa);
       anc_lo[j] = (int)(span + pb);
-      const double v = median_value<K>(skey, srank, span, Kc, cnt, pa, pb, inv_scale);
+      const double v = median_value<K>(tk, cnt, pa, pb, inv_scale);
       const double rel = sg_store(o, j, v);
       relmax = rel > relmax ? rel : relmax;
     }
@@ -1527,7 +1565,7 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
       anc_hi[j] = (int)(span + pa);
       anc_lo[j] = (int)(span + pb);
     }
-    const double v = median_value<K>(skey, srank, span, Kc, cnt, pa, pb, inv_scale);
+    const double v = median_value<K>(tk, cnt, pa, pb, inv_scale);
     const double rel = sg_store(o, j, v);
     relmax = rel > relmax ? rel : relmax;
   }
@@ -1561,7 +1599,7 @@ __global__ void __launch_bounds__(512, 2) k_median_wm(
         if (c < 0) inc = false;
         chg[X] = c < 0 ? 0 : c;
       }
-      if (chg[0] + chg[1] > kIncMax) inc = false;
+      if (chg[0] + chg[1] > kIncMax || pl.Kc > kIncMaxKc) inc = false;
     }
     double r = median_tile<K>(skey, srank, n, pl, o, u, sm_raw, zeros, inc, chg[0], chg[1], log);
     relmax = r > relmax ? r : relmax;
@@ -1583,8 +1621,11 @@ size_t median_smem_bytes(int Kc, int key_bytes) {
   while ((1 << LV) < M) ++LV;
   size_t ws = (size_t)M / 32 + 1;
   size_t rk = (size_t)LV * ws * 8, mr = (size_t)2 * M;  // the merged indices sit over rk
+  if (Kc > kIncMaxKc)  // keys, one index array, the wavelet levels
+    return (size_t)key_bytes * M + (size_t)2 * M + (rk > mr ? rk : mr);
+  // keys, four index arrays, the wavelet levels, the change lists of both chunks
   const size_t changes = (size_t)2 * kChangeMax * (8 + 8 + 2);
-  return (size_t)key_bytes * M + (size_t)2 * M + (rk > mr ? rk : mr) + changes;
+  return (size_t)key_bytes * M + (size_t)8 * M + (rk > mr ? rk : mr) + changes;
 }
 
 void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
