@@ -940,6 +940,7 @@ extern "C" int sub_get_work(sub_ctx* c, int64_t* work, int32_t n) {
   CU(cudaMemcpyAsync(c->h_rs, c->rs, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream), c);
   CU(cudaStreamSynchronize(c->stream), c);
   for (int i = 0; i < n && i < 4; ++i) work[i] = (int64_t)c->h_rs->work[i];
+  for (int i = 4; i < n && i < 6; ++i) work[i] = (int64_t)c->h_rs->median_inc[i - 4];
   return SUB_OK;
 }
 

@@ -1268,13 +1268,16 @@ constexpr int kIncMax = 32;
 constexpr int kIncMaxKc = 2048;
 
 // Incremental selection for one window of a tile whose chunks changed in a few positions since
-// the previous estimate.  The element e the window selected last time (its anchor) had
-// exactly k window elements before it in the (key, position) order.  Keys only changed at the
-// listed positions, so now d = (listed window positions that come before e now) - (those that
-// came before e then) more elements precede e; the element with k before it is then the d-th
-// window element below e in the new merged order (above it for d < 0).  Returns the tile-local
-// position of that element, or -1 when e itself changed or the walk leaves the span (the
-// caller then selects the whole tile again).
+// the previous estimate.  The element e at position pe that the window selected last time (its
+// anchor) had exactly k window elements before it in the (key, position) order.  Take the
+// reference point V = (e's key before the changes, pe).  Keys changed only at the listed
+// positions, so now k + D window elements come before V, with D = (listed window elements
+// other than e that come before V now) - (those that came before V then), plus one if e's own
+// new key puts it before V.  The window element with exactly k before it is then the D-th
+// window element below V in the new merged order, or for D <= 0 the (1 - D)-th at or above V
+// (V itself when e is unchanged and D = 0).  Returns its tile-local position, or -1 if the
+// anchor is not in the window or a walk leaves the span (the caller then selects the whole
+// tile again; neither happens for a consistent state).
 template <typename K>
 __device__ __forceinline__ int median_move(const TileKeys<K>& tk, int M, int ws, int we, int pe,
                                            const uint16_t* __restrict__ v_of_pos,
@@ -1282,28 +1285,54 @@ __device__ __forceinline__ int median_move(const TileKeys<K>& tk, int M, int ws,
                                            const uint16_t* cpos, const u64* cold,
                                            const u64* cnew) {
   if (pe < ws || pe > we) return -1;
-  const K ke = tk.at(pe);
-  int d = 0;
+  const K kn = tk.at(pe);  // e's key now
+  int ie = -1;
+  for (int c = 0; c < nchg; ++c)
+    if (cpos[c] == pe) ie = c;
+  const K kv = ie >= 0 ? (K)cold[ie] : kn;  // V's key
+  int D = 0;
   for (int c = 0; c < nchg; ++c) {
     const int pc = cpos[c];
-    if (pc == pe) return -1;
-    if (pc < ws || pc > we) continue;
-    d += (key_pos_less<K>((K)cnew[c], pc, ke, pe) ? 1 : 0) -
-         (key_pos_less<K>((K)cold[c], pc, ke, pe) ? 1 : 0);
+    if (pc == pe || pc < ws || pc > we) continue;
+    D += (key_pos_less<K>((K)cnew[c], pc, kv, pe) ? 1 : 0) -
+         (key_pos_less<K>((K)cold[c], pc, kv, pe) ? 1 : 0);
   }
-  int r = v_of_pos[pe];
-  int guard = M;
-  while (d > 0 && guard-- > 0) {
-    if (--r < 0) return -1;
+  int r;       // merged rank of V: the elements at lower ranks come before it
+  int need;    // window elements to step over (D > 0: below V; else: at or above V)
+  if (ie < 0) {
+    r = v_of_pos[pe];  // e itself sits at V
+    if (D == 0) return pe;
+    need = D > 0 ? D : -D;
+    if (D < 0) ++r;    // above V, e excluded
+  } else {
+    if (key_pos_less<K>(kn, pe, kv, pe)) ++D;
+    int lo = 0, hi = M;  // first merged rank whose element comes after V
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      const int pm = pos_of[mid];
+      if (key_pos_less<K>(tk.at(pm), pm, kv, pe))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    r = lo;
+    need = D > 0 ? D : 1 - D;
+  }
+  if (D > 0) {
+    int got = 0;
+    while (got < need) {
+      if (--r < 0) return -1;
+      const int p = pos_of[r];
+      if (p >= ws && p <= we) ++got;
+    }
+    return pos_of[r];
+  }
+  int got = 0;
+  for (;; ++r) {
+    if (r >= M) return -1;
     const int p = pos_of[r];
-    if (p >= ws && p <= we) --d;
+    if (p >= ws && p <= we && ++got == need) return p;
   }
-  while (d < 0 && guard-- > 0) {
-    if (++r >= M) return -1;
-    const int p = pos_of[r];
-    if (p >= ws && p <= we) ++d;
-  }
-  return d == 0 ? pos_of[r] : -1;
 }
 
 // One tile; returns the largest relative change of S_n among its outputs (conv_rtol).
@@ -1463,8 +1492,13 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
       const double rel = sg_store(o, j, v);
       relmax = rel > relmax ? rel : relmax;
     }
-    if (!__syncthreads_or(!ok)) return relmax;
-    // an anchor changed (or could not be moved): select the whole tile again
+    const bool redo = __syncthreads_or(!ok);
+    if (tid == 0 && o.rs) {
+      atomicAdd(&o.rs->median_inc[0], 1ull);
+      if (redo) atomicAdd(&o.rs->median_inc[1], 1ull);
+    }
+    if (!redo) return relmax;
+    // an anchor could not be moved (an inconsistent state): select the whole tile again
     relmax = 0.0;
   }
 

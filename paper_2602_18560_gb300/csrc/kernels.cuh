@@ -38,6 +38,7 @@ struct RunState {
   unsigned long long relchg_bits;   // max relative change of S_n (conv_rtol)
   unsigned long long next_tile;  // catalog tiles handed out so far (catalog pass)
   unsigned long long work[4];    // work-list items the loop kernels were handed (by list)
+  unsigned long long median_inc[2];  // median tiles moved incrementally, and of them redone
   unsigned long long nnear;      // FP64 decisions with |rho^2 / rho_th^2 - 1| < 2e-9
   unsigned long long nuncertain; // FP32 decisions (mixed precision) inside the screen's bound
   unsigned err;
