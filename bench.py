@@ -707,9 +707,6 @@ def main():
                   "n_uncertain_fp32": st.n_uncertain, "n_resolved": st.n_resolved,
                   "resolved_per_iteration": [int(x) for x in sub.history()],
                   "iteration_ms_host_driven": [round(x, 4) for x in per_iter],
-                  "median_tiles": {"all": work["tiles"],
-                                   "moved_incrementally": work["median_incremental"],
-                                   "redone": work["median_redone"]},
                   "late_iteration_ms_median": (float(np.median(per_iter[2:]))
                                                if len(per_iter) > 2 else None),
                   "prepass_ms": pre_ms, "loop_ms": loop_ms},

@@ -243,9 +243,7 @@ int sub_coarse_grain(sub_ctx* ctx, const double* x, int32_t add_instr, int32_t n
  * one chunk of such a chunk, work[2] within two, work[3] median tiles (Kc outputs each).
  * Which kernel takes which list depends on the estimator: median-then-mean sorts 0,
  * selects medians on 3, sums prefixes on 1 and window means on 2; median sorts 0 and
- * selects on 3; mean sums prefixes on 0 and window means on 1.  work[4]: median tiles whose
- * outputs were moved from their previous selections (few changed positions), work[5]: of
- * those, tiles that had to be selected again in full.  Writes min(n, 6) entries.
+ * selects on 3; mean sums prefixes on 0 and window means on 1.  Writes min(n, 4) entries.
  * Synchronises. */
 int sub_get_work(sub_ctx* ctx, int64_t* work, int32_t n);
 

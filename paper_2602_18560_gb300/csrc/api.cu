@@ -238,11 +238,6 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   if (p->estimator != SUB_MEAN) {
     rc = dalloc(c, (void**)&c->skey, (size_t)ncell * 8);
     if (!rc) rc = dalloc(c, (void**)&c->srank, (size_t)ncell * 2);
-    if (!rc) rc = dalloc(c, (void**)&c->chlog.cnt, (size_t)pl.nch * 4);
-    if (!rc) rc = dalloc(c, (void**)&c->chlog.pos, (size_t)pl.nch * kChangeMax * 2);
-    if (!rc) rc = dalloc(c, (void**)&c->chlog.old_key, (size_t)pl.nch * kChangeMax * 8);
-    if (!rc) rc = dalloc(c, (void**)&c->chlog.new_key, (size_t)pl.nch * kChangeMax * 8);
-    if (!rc) rc = dalloc(c, (void**)&c->chlog.anchor, (size_t)n * 8);
     if (!rc && p->estimator == SUB_MEDIAN_MEAN) rc = dalloc(c, (void**)&c->M, (size_t)n * 8);
     if (rc) return fail(rc);
   }
@@ -529,8 +524,8 @@ static void enqueue_estimate(sub_ctx* c, cudaStream_t st, SpecIn in, int rtol_on
       break;
     }
     case SUB_MEDIAN: {
-      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(in, n, pl, c->skey, c->srank, d, c->chlog, st); }
-      { KTimer t(c, st, SUB_K_MEDIAN); launch_running_median(c->skey, c->srank, n, pl, o, d, c->chlog, st); }
+      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(in, n, pl, c->skey, c->srank, d, st); }
+      { KTimer t(c, st, SUB_K_MEDIAN); launch_running_median(c->skey, c->srank, n, pl, o, d, st); }
       break;
     }
     default: {
@@ -542,8 +537,8 @@ static void enqueue_estimate(sub_ctx* c, cudaStream_t st, SpecIn in, int rtol_on
       mi.acc = nullptr;
       mi.S = nullptr;
       mi.x = c->M;
-      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(in, n, pl, c->skey, c->srank, d, c->chlog, st); }
-      { KTimer t(c, st, SUB_K_MEDIAN); launch_running_median(c->skey, c->srank, n, pl, om, d, c->chlog, st); }
+      { KTimer t(c, st, SUB_K_SORT); launch_chunk_sort(in, n, pl, c->skey, c->srank, d, st); }
+      { KTimer t(c, st, SUB_K_MEDIAN); launch_running_median(c->skey, c->srank, n, pl, om, d, st); }
       { KTimer t(c, st, SUB_K_PREFIX); launch_chunk_prefix(mi, n, pl, c->pre_lo, c->pre_hi, c->sig, c->uflow, nullptr, d, 1, st); }
       { KTimer t(c, st, SUB_K_MEAN); launch_window_mean(c->M, n, pl, c->pre_lo, c->pre_hi, c->sig, c->uflow, o, d, 2, st); }
       break;
@@ -940,7 +935,6 @@ extern "C" int sub_get_work(sub_ctx* c, int64_t* work, int32_t n) {
   CU(cudaMemcpyAsync(c->h_rs, c->rs, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream), c);
   CU(cudaStreamSynchronize(c->stream), c);
   for (int i = 0; i < n && i < 4; ++i) work[i] = (int64_t)c->h_rs->work[i];
-  for (int i = 4; i < n && i < 6; ++i) work[i] = (int64_t)c->h_rs->median_inc[i - 4];
   return SUB_OK;
 }
 

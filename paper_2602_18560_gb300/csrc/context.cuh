@@ -51,7 +51,6 @@ struct sub_ctx {
   int* list_counts = nullptr;      // [kNumLists]
   unsigned long long* skey = nullptr;
   uint16_t* srank = nullptr;
-  gbsub::ChangeLog chlog = {};  // the sorts' change lists and the medians' anchors
   unsigned long long *pre_lo = nullptr, *pre_hi = nullptr;
   unsigned* uflow = nullptr;
   // catalog and per-source buffers

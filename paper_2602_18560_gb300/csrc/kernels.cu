@@ -853,7 +853,7 @@ __device__ __forceinline__ void cmp_keep(K& k, int& x, K ko, int xo, bool keep_m
 // unchanged elements that precede it, found by a binary search of the old order.  This is
 // the (key, position) order the full sort produces, so the two paths write the same arrays.
 // Returns false, having written nothing, when more than kResortMax positions changed.
-constexpr int kResortMax = kChangeMax;
+constexpr int kResortMax = 128;
 
 template <typename K>
 __device__ __forceinline__ bool key_pos_less(K ka, int pa, K kb, int pb) {
@@ -862,13 +862,11 @@ __device__ __forceinline__ bool key_pos_less(K ka, int pa, K kb, int pb) {
 
 template <int E, typename K>
 __device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __restrict__ skey_c,
-                                   uint16_t* __restrict__ srank_c, unsigned char* raw,
-                                   const ChangeLog& log, int b) {
+                                   uint16_t* __restrict__ srank_c, unsigned char* raw) {
   K* old_k = (K*)raw;                                // [kpad] old keys, in old sorted order
   K* ch_k = old_k + kpad;                            // [kResortMax] changed: new keys
   K* cs_k = ch_k + kResortMax;                       // [kResortMax] the same, sorted
-  K* ch_o = cs_k + kResortMax;                       // [kResortMax] changed: old keys
-  uint16_t* old_p = (uint16_t*)(ch_o + kResortMax);  // [kpad] position of each old index
+  uint16_t* old_p = (uint16_t*)(cs_k + kResortMax);  // [kpad] position of each old index
   uint16_t* csum = old_p + kpad;                     // [kpad + 2] changed before an old index
   uint16_t* ch_p = csum + kpad + 2;                  // [kResortMax] changed: positions
   uint16_t* cs_p = ch_p + kResortMax;                // [kResortMax] the same, sorted
@@ -915,7 +913,6 @@ __device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __r
       const int slot = atomicAdd(&n_changed, 1);
       if (slot < kResortMax) {
         ch_k[slot] = knew[a];
-        ch_o[slot] = old_k[r[a]];
         ch_p[slot] = (uint16_t)p;
       }
     }
@@ -924,16 +921,6 @@ __device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __r
   const int C = n_changed;
   __syncthreads();  // every thread has read the count before the caller reuses shared memory
   if (C > kResortMax) return false;
-  // the changes, for the median tiles that read this chunk
-  if (log.cnt) {
-    for (int t = tid; t < C; t += T) {
-      const size_t at = (size_t)b * kChangeMax + t;
-      log.pos[at] = ch_p[t];
-      log.old_key[at] = (unsigned long long)ch_o[t];
-      log.new_key[at] = (unsigned long long)ch_k[t];
-    }
-    if (tid == 0) log.cnt[b] = C;
-  }
   if (C == 0) return true;
   // 3. csum[i] = changed elements among old indices < i (exclusive scan in old order)
   int f[E], run = 0;
@@ -1022,8 +1009,7 @@ __device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __r
 template <int E, typename K>
 __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, SmoothPlan pl,
                                                      K* __restrict__ skey,
-                                                     uint16_t* __restrict__ srank, Dirty d,
-                                                     ChangeLog log) {
+                                                     uint16_t* __restrict__ srank, Dirty d) {
   extern __shared__ __align__(16) unsigned char sort_raw[];
   K* sm_keys = (K*)sort_raw;
   uint16_t* sm_idx = (uint16_t*)(sm_keys + pl.kpad);
@@ -1049,12 +1035,10 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
       k[a] = kv;
       x[a] = i;
     }
-    if (resort &&
-        resort_few_changes<E, K>(k, len, kpad, skey + base, srank + base, sort_raw, log, b)) {
+    if (resort && resort_few_changes<E, K>(k, len, kpad, skey + base, srank + base, sort_raw)) {
       __syncthreads();  // before the next chunk overwrites shared memory
       continue;
     }
-    if (log.cnt && threadIdx.x == 0) log.cnt[b] = -1;  // sorted from scratch: no change list
     bool first_smem = true;
     for (int kk = 2; kk <= kpad; kk <<= 1) {
       int jj = kk >> 1;
@@ -1156,12 +1140,11 @@ static int persistent_grid(const SmoothPlan& pl, int items, int resident) {
 
 // Launch one k_chunk_sort instantiation with the key buffer cast to its key type.
 template <typename K>
-static void launch_sort_as(void (*kern)(SpecIn, long long, SmoothPlan, K*, uint16_t*, Dirty,
-                                        ChangeLog),
+static void launch_sort_as(void (*kern)(SpecIn, long long, SmoothPlan, K*, uint16_t*, Dirty),
                            int bl, int th, size_t smem, cudaStream_t st, SpecIn in, long long n,
                            const SmoothPlan& pl, unsigned long long* skey, uint16_t* srank,
-                           Dirty d, ChangeLog log) {
-  kern<<<bl, th, smem, st>>>(in, n, pl, (K*)skey, srank, d, log);
+                           Dirty d) {
+  kern<<<bl, th, smem, st>>>(in, n, pl, (K*)skey, srank, d);
 }
 
 static int sort_per_thread(const SmoothPlan& pl) {
@@ -1173,7 +1156,7 @@ static size_t sort_smem(const SmoothPlan& pl) {
   const size_t kb = pl.fp32_keys ? 4 : 8;
   const size_t full = (size_t)pl.kpad * (kb + sizeof(uint16_t));
   const size_t few = (size_t)pl.kpad * (kb + 2 + 1) + (size_t)(pl.kpad + 2) * 2 +
-                     (size_t)kResortMax * 2 * (kb + 2) + (size_t)kResortMax * kb;
+                     (size_t)kResortMax * 2 * (kb + 2);
   return full > few ? full : few;
 }
 template <typename K, typename F>
@@ -1193,12 +1176,12 @@ static void with_sort_kernel(const SmoothPlan& pl, F fn) {
 }
 
 void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
-                       uint16_t* srank, Dirty d, ChangeLog log, cudaStream_t st) {
+                       uint16_t* srank, Dirty d, cudaStream_t st) {
   const size_t smem = sort_smem(pl);
   const int th = sort_threads(pl);
   const int bl = persistent_grid(pl, pl.nch, pl.res_sort);
   with_sort_kernel(pl, [&](auto kern) {
-    launch_sort_as(kern, bl, th, smem, st, in, n, pl, skey, srank, d, log);
+    launch_sort_as(kern, bl, th, smem, st, in, n, pl, skey, srank, d);
   });
 }
 
@@ -1229,125 +1212,15 @@ __device__ __forceinline__ int wm_rank1(const u64* rkl, int i) {
   return (int)(e >> 32) + __popc((uint32_t)e & ((1u << (i & 31)) - 1u));
 }
 
-// Keys of the tile's positions (tile-local p: chunk u-1 below Kc, chunk u above): from the
-// sorted keys and sorted indices held in shared memory, or through the global arrays.
-template <typename K>
-struct TileKeys {
-  const K* sk;          // [2 Kc] sorted keys of both chunks (shared), or null
-  const uint16_t* srl;  // [2 Kc] sorted index of each position (shared)
-  const K* skey;
-  const uint16_t* srank;
-  long long span;
-  int Kc;
-  __device__ __forceinline__ K at(int p) const {
-    const int base = p >= Kc ? Kc : 0;
-    if (sk) return sk[base + srl[p]];
-    return skey[span + base + srank[span + p]];
-  }
-};
-
-// C times the median of a window from its selected elements: the upper median at tile-local
-// position pa and, for an even count, the lower one at pb.
-template <typename K>
-__device__ __forceinline__ double median_value(const TileKeys<K>& tk, int cnt, int pa, int pb,
-                                               double inv_scale) {
-  const K khi = tk.at(pa);
-  double med;
-  if (cnt & 1) {
-    med = key_value<K>(khi, inv_scale);
-  } else {
-    const K klo = tk.at(pb);
-    med = __dmul_rn(__dadd_rn(key_value<K>(klo, inv_scale), key_value<K>(khi, inv_scale)), 0.5);
-  }
-  return __dmul_rn(kMedianBias, med);
-}
-
-// Tiles whose two chunks changed in at most this many positions in all take the incremental
-// path below (chunks of at most kIncMaxKc bins, whose tiles keep their keys in shared memory).
-constexpr int kIncMax = 32;
-constexpr int kIncMaxKc = 2048;
-
-// Incremental selection for one window of a tile whose chunks changed in a few positions since
-// the previous estimate.  The element e at position pe that the window selected last time (its
-// anchor) had exactly k window elements before it in the (key, position) order.  Take the
-// reference point V = (e's key before the changes, pe).  Keys changed only at the listed
-// positions, so now k + D window elements come before V, with D = (listed window elements
-// other than e that come before V now) - (those that came before V then), plus one if e's own
-// new key puts it before V.  The window element with exactly k before it is then the D-th
-// window element below V in the new merged order, or for D <= 0 the (1 - D)-th at or above V
-// (V itself when e is unchanged and D = 0).  Returns its tile-local position, or -1 if the
-// anchor is not in the window or a walk leaves the span (the caller then selects the whole
-// tile again; neither happens for a consistent state).
-template <typename K>
-__device__ __forceinline__ int median_move(const TileKeys<K>& tk, int M, int ws, int we, int pe,
-                                           const uint16_t* __restrict__ v_of_pos,
-                                           const uint16_t* __restrict__ pos_of, int nchg,
-                                           const uint16_t* cpos, const u64* cold,
-                                           const u64* cnew) {
-  if (pe < ws || pe > we) return -1;
-  const K kn = tk.at(pe);  // e's key now
-  int ie = -1;
-  for (int c = 0; c < nchg; ++c)
-    if (cpos[c] == pe) ie = c;
-  const K kv = ie >= 0 ? (K)cold[ie] : kn;  // V's key
-  int D = 0;
-  for (int c = 0; c < nchg; ++c) {
-    const int pc = cpos[c];
-    if (pc == pe || pc < ws || pc > we) continue;
-    D += (key_pos_less<K>((K)cnew[c], pc, kv, pe) ? 1 : 0) -
-         (key_pos_less<K>((K)cold[c], pc, kv, pe) ? 1 : 0);
-  }
-  int r;       // merged rank of V: the elements at lower ranks come before it
-  int need;    // window elements to step over (D > 0: below V; else: at or above V)
-  if (ie < 0) {
-    r = v_of_pos[pe];  // e itself sits at V
-    if (D == 0) return pe;
-    need = D > 0 ? D : -D;
-    if (D < 0) ++r;    // above V, e excluded
-  } else {
-    if (key_pos_less<K>(kn, pe, kv, pe)) ++D;
-    int lo = 0, hi = M;  // first merged rank whose element comes after V
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      const int pm = pos_of[mid];
-      if (key_pos_less<K>(tk.at(pm), pm, kv, pe))
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    r = lo;
-    need = D > 0 ? D : 1 - D;
-  }
-  if (D > 0) {
-    int got = 0;
-    while (got < need) {
-      if (--r < 0) return -1;
-      const int p = pos_of[r];
-      if (p >= ws && p <= we) ++got;
-    }
-    return pos_of[r];
-  }
-  int got = 0;
-  for (;; ++r) {
-    if (r >= M) return -1;
-    const int p = pos_of[r];
-    if (p >= ws && p <= we && ++got == need) return p;
-  }
-}
-
 // One tile; returns the largest relative change of S_n among its outputs (conv_rtol).
-// inc: the tile's chunks changed in at most kIncMax positions since their previous sort
-// (chg0 listed in log for chunk u-1, chg1 for chunk u), and every output's previous selection
-// is in log.anchor.
 template <typename K>
 __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
                                               const uint16_t* __restrict__ srank, long long n,
                                               const SmoothPlan& pl, const SgOut& o, long long u,
-                                              unsigned char* sm_raw, int* zeros, bool inc,
-                                              int chg0, int chg1, const ChangeLog& log) {
+                                              unsigned char* sm_raw, int* zeros) {
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Kc = pl.Kc, M = 2 * Kc, LV = wm_levels(M);
-  const int nwm = M >> 5, ws_ = nwm + 1;  // words per level (one zero word of padding)
+  const int nwm = M >> 5, ws = nwm + 1;  // words per level (one zero word of padding)
   const int h = pl.W / 2;
   long long j_lo = (u - 1) * Kc + h, j_hi = u * Kc + h;
   if (j_lo < 0) j_lo = 0;
@@ -1359,68 +1232,19 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   if (u >= 1) len0 = (n - span) < Kc ? (int)(n - span) : Kc;
   if (u < pl.nch) len1 = (n - span - Kc) < Kc ? (int)(n - span - Kc) : Kc;
   double relmax = 0.0;
-  // Shared memory.  Chunks of at most kIncMaxKc bins: the sorted keys and the sorted index of
-  // every position stay for the selections; wider chunks put the wavelet's scratch over the
-  // keys and read keys through global memory (and never take the incremental path).
-  const bool keep = Kc <= kIncMaxKc;
-  K* sk = (K*)sm_raw;  // [M] sorted keys of chunks u-1 and u
-  uint16_t *srl = nullptr, *seq0, *src, *seq1;
-  if (keep) {
-    srl = (uint16_t*)(sk + M);  // [M] sorted index of each position
-    seq0 = srl + M;             // [M] position -> merged rank
-    src = seq0 + M;             // [M] merged rank -> position
-    seq1 = src + M;             // [M] wavelet scratch
-  } else {
-    seq1 = (uint16_t*)sm_raw;   // over the keys once they are merged
-    src = seq1 + M;
-    seq0 = (uint16_t*)(sm_raw + sizeof(K) * (size_t)M);
-  }
-  // [LV][ws_]: per bitset word, its 32 bits (low half) and the ones before it (high half),
+  K* sk = (K*)sm_raw;                                        // [M] sorted keys (step 1)
+  uint16_t* seq1 = (uint16_t*)sm_raw;                        // [M] (steps 2-3, over sk)
+  uint16_t* src = seq1 + M;                                  // [M] rank -> element
+  uint16_t* seq0 = (uint16_t*)(sm_raw + sizeof(K) * (size_t)M);  // [M]
+  // [LV][ws]: per bitset word, its 32 bits (low half) and the ones before it (high half),
   // so that a rank is one 64-bit load
-  u64* rk = (u64*)((keep ? seq1 : seq0) + M);
+  u64* rk = (u64*)(seq0 + M);
   uint16_t* mr = (uint16_t*)rk;  // [M] merged index of (chunk, sorted index) (step 1, over rk)
-  TileKeys<K> tk;
-  tk.sk = keep ? sk : nullptr;
-  tk.srl = srl;
-  tk.skey = skey;
-  tk.srank = srank;
-  tk.span = span;
-  tk.Kc = Kc;
-  const size_t rk_bytes =
-      (size_t)LV * ws_ * 8 > (size_t)2 * M ? (size_t)LV * ws_ * 8 : (size_t)2 * M;
-  u64* cold = (u64*)((unsigned char*)rk + rk_bytes);         // [2 kChangeMax] changes
-  u64* cnew = cold + 2 * kChangeMax;
-  uint16_t* cpos = (uint16_t*)(cnew + 2 * kChangeMax);
   __shared__ int warp_ones[32];
-  __shared__ int nchg;
 
   // 1. merged ranks.  Chunk u-1 precedes chunk u on equal keys (its positions are lower).
   for (int i = tid; i < len0; i += T) sk[i] = skey[span + i];
   for (int i = tid; i < len1; i += T) sk[Kc + i] = skey[span + Kc + i];
-  if (keep) {
-    for (int i = tid; i < len0; i += T) srl[i] = srank[span + i];
-    for (int i = tid; i < len1; i += T) srl[Kc + i] = srank[span + Kc + i];
-  }
-  if (inc) {
-    // the changes of both chunks, at tile-local positions
-    if (tid == 0) nchg = 0;
-    __syncthreads();
-    for (int X = 0; X < 2; ++X) {
-      const long long cb = u - 1 + X;
-      const int c = X ? chg1 : chg0;
-      if (c <= 0) continue;
-      const int base = X ? nchg : 0;
-      for (int t = tid; t < c; t += T) {
-        const size_t at = (size_t)cb * kChangeMax + t;
-        cpos[base + t] = (uint16_t)(X * Kc + log.pos[at]);
-        cold[base + t] = log.old_key[at];
-        cnew[base + t] = log.new_key[at];
-      }
-      __syncthreads();
-      if (tid == 0) nchg += c;
-      __syncthreads();
-    }
-  }
   __syncthreads();
   {
     // merge path: thread t emits the merged indices [d0, d1) of the two sorted chunks,
@@ -1452,55 +1276,15 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
     const int X = p >= Kc, q = p - X * Kc;
     int v;
     if (q < (X ? len1 : len0)) {
-      const int si = keep ? srl[p] : srank[span + p];
+      const int si = srank[span + p];
       v = mr[X * Kc + si];
-      src[v] = (uint16_t)p;
+      src[v] = (uint16_t)((X << 15) | si);
     } else {
       v = len0 + len1 + (X ? (Kc - len0) + (q - len1) : (q - len0));
-      src[v] = (uint16_t)p;  // outside the band: never inside a window
     }
     seq0[p] = (uint16_t)v;
   }
   __syncthreads();
-  const int nout = (int)(j_hi - j_lo);
-  int* anc_hi = log.anchor;
-  int* anc_lo = log.anchor ? log.anchor + n : nullptr;
-
-  if (inc) {
-    // 2'. every output moved from its previous selection
-    bool ok = true;
-    const int C = nchg;
-    for (int t = tid; t < nout && ok; t += T) {
-      const long long j = j_lo + t;
-      const long long s = j - h > 0 ? j - h : 0;
-      const long long e = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
-      const int cnt = (int)(e - s + 1);
-      const int ws = (int)(s - span), we = (int)(e - span);
-      const int pa = median_move<K>(tk, M, ws, we, anc_hi[j] - (int)span, seq0, src, C, cpos,
-                                    cold, cnew);
-      int pb = pa;
-      if (!(cnt & 1))
-        pb = median_move<K>(tk, M, ws, we, anc_lo[j] - (int)span, seq0, src, C, cpos, cold,
-                            cnew);
-      if (pa < 0 || pb < 0) {
-        ok = false;
-        break;
-      }
-      anc_hi[j] = (int)(span + pa);
-      anc_lo[j] = (int)(span + pb);
-      const double v = median_value<K>(tk, cnt, pa, pb, inv_scale);
-      const double rel = sg_store(o, j, v);
-      relmax = rel > relmax ? rel : relmax;
-    }
-    const bool redo = __syncthreads_or(!ok);
-    if (tid == 0 && o.rs) {
-      atomicAdd(&o.rs->median_inc[0], 1ull);
-      if (redo) atomicAdd(&o.rs->median_inc[1], 1ull);
-    }
-    if (!redo) return relmax;
-    // an anchor could not be moved (an inconsistent state): select the whole tile again
-    relmax = 0.0;
-  }
 
   // 2. wavelet matrix.  Warp w owns the words [w wpw, (w + 1) wpw) of every level (M is a
   // multiple of 64: whole words).  A level takes two barriers: one after the warps have
@@ -1512,7 +1296,7 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   uint16_t* nxt = seq1;
   for (int l = 0; l < LV; ++l) {
     const int sh = LV - 1 - l;
-    u64* rkl = rk + (size_t)l * ws_;
+    u64* rkl = rk + (size_t)l * ws;
     int mine = 0;
     for (int k = w0; k < w1; ++k)
       mine += __popc(__ballot_sync(0xFFFFFFFFu, (cur[k * 32 + lane] >> sh) & 1));
@@ -1522,9 +1306,9 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
     const int c = lane < nwarp ? warp_ones[lane] : 0;
     int incl = c;
 #pragma unroll
-    for (int o2 = 1; o2 < 32; o2 <<= 1) {
-      const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o2);
-      if (lane >= o2) incl += t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += t;
     }
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     int run = __shfl_sync(0xFFFFFFFFu, incl - c, warp);
@@ -1552,6 +1336,7 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   }
 
   // 3. selections
+  const int nout = (int)(j_hi - j_lo);
   for (int t = tid; t < nout; t += T) {
     const long long j = j_lo + t;
     const long long s = j - h > 0 ? j - h : 0;
@@ -1561,7 +1346,7 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
     int la = (int)(s - span), ra = (int)(e + 1 - span), ka = cnt >> 1, va = 0;
     int lb = la, rb = ra, kb = ka > 0 ? ka - 1 : 0, vb = 0;
     for (int l = 0; l < LV; ++l) {
-      const u64* rkl = rk + (size_t)l * ws_;
+      const u64* rkl = rk + (size_t)l * ws;
       const int Z = zeros[l];
       const int oal = wm_rank1(rkl, la);
       const int oar = wm_rank1(rkl, ra);
@@ -1593,14 +1378,19 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
         vb |= bit;
       }
     }
-    const int pa = src[va];
-    const int pb = (cnt & 1) ? pa : src[vb];
-    if (anc_hi) {
-      anc_hi[j] = (int)(span + pa);
-      anc_lo[j] = (int)(span + pb);
+    const int ea = src[va];
+    const K khi = skey[span + (ea >> 15) * Kc + (ea & 0x7FFF)];
+    double med;
+    if (cnt & 1) {
+      med = key_value<K>(khi, inv_scale);
+    } else {
+      const int eb = src[vb];
+      const K klo = skey[span + (eb >> 15) * Kc + (eb & 0x7FFF)];
+      med = __dmul_rn(__dadd_rn(key_value<K>(klo, inv_scale), key_value<K>(khi, inv_scale)),
+                      0.5);
     }
-    const double v = median_value<K>(tk, cnt, pa, pb, inv_scale);
-    const double rel = sg_store(o, j, v);
+    double v = __dmul_rn(kMedianBias, med);
+    double rel = sg_store(o, j, v);
     relmax = rel > relmax ? rel : relmax;
   }
   return relmax;
@@ -1609,33 +1399,17 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
 template <typename K>
 __global__ void __launch_bounds__(512, 2) k_median_wm(
     const K* __restrict__ skey, const uint16_t* __restrict__ srank,
-    long long n, SmoothPlan pl, SgOut o, Dirty d, ChangeLog log) {
+    long long n, SmoothPlan pl, SgOut o, Dirty d) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int zeros[16];
   double relmax = 0.0;
   const int nitem = d.count(kListTile, pl.nch + 1);
-  // after the first iteration of a tracked run, each dirty chunk's re-sort listed its changes
-  const bool tracked = d.base != nullptr && d.rs->iter > 0 && log.cnt != nullptr;
   int u_next = d.item(kListTile, blockIdx.x);  // loaded beside the count (grid <= list length)
   for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
     // a tile whose windows changed
     const int u = u_next;
     if (it + (int)gridDim.x < nitem) u_next = d.item(kListTile, it + gridDim.x);
-    bool inc = false;
-    int chg[2] = {0, 0};
-    if (tracked) {
-      inc = true;
-      for (int X = 0; X < 2; ++X) {
-        const long long cb = u - 1 + X;
-        if (cb < 0 || cb >= pl.nch) continue;
-        if (!d.any(cb, 0)) continue;  // not re-sorted this time: unchanged
-        const int c = log.cnt[cb];
-        if (c < 0) inc = false;
-        chg[X] = c < 0 ? 0 : c;
-      }
-      if (chg[0] + chg[1] > kIncMax || pl.Kc > kIncMaxKc) inc = false;
-    }
-    double r = median_tile<K>(skey, srank, n, pl, o, u, sm_raw, zeros, inc, chg[0], chg[1], log);
+    double r = median_tile<K>(skey, srank, n, pl, o, u, sm_raw, zeros);
     relmax = r > relmax ? r : relmax;
     __syncthreads();  // before the next tile overwrites shared memory
   }
@@ -1655,23 +1429,18 @@ size_t median_smem_bytes(int Kc, int key_bytes) {
   while ((1 << LV) < M) ++LV;
   size_t ws = (size_t)M / 32 + 1;
   size_t rk = (size_t)LV * ws * 8, mr = (size_t)2 * M;  // the merged indices sit over rk
-  if (Kc > kIncMaxKc)  // keys, one index array, the wavelet levels
-    return (size_t)key_bytes * M + (size_t)2 * M + (rk > mr ? rk : mr);
-  // keys, four index arrays, the wavelet levels, the change lists of both chunks
-  const size_t changes = (size_t)2 * kChangeMax * (8 + 8 + 2);
-  return (size_t)key_bytes * M + (size_t)8 * M + (rk > mr ? rk : mr) + changes;
+  return (size_t)key_bytes * M + (size_t)2 * M + (rk > mr ? rk : mr);
 }
 
 void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
-                           const SmoothPlan& pl, SgOut o, Dirty d, ChangeLog log,
-                           cudaStream_t st) {
+                           const SmoothPlan& pl, SgOut o, Dirty d, cudaStream_t st) {
   int th = median_threads(pl);
   size_t smem = median_smem_bytes(pl.Kc, pl.fp32_keys ? 4 : 8);
   int bl = persistent_grid(pl, pl.nch + 1, pl.res_median);
   if (pl.fp32_keys)
-    k_median_wm<uint32_t><<<bl, th, smem, st>>>((const uint32_t*)skey, srank, n, pl, o, d, log);
+    k_median_wm<uint32_t><<<bl, th, smem, st>>>((const uint32_t*)skey, srank, n, pl, o, d);
   else
-    k_median_wm<u64><<<bl, th, smem, st>>>(skey, srank, n, pl, o, d, log);
+    k_median_wm<u64><<<bl, th, smem, st>>>(skey, srank, n, pl, o, d);
 }
 
 // ============================================================================ window mean

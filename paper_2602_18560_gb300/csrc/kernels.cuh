@@ -38,7 +38,6 @@ struct RunState {
   unsigned long long relchg_bits;   // max relative change of S_n (conv_rtol)
   unsigned long long next_tile;  // catalog tiles handed out so far (catalog pass)
   unsigned long long work[4];    // work-list items the loop kernels were handed (by list)
-  unsigned long long median_inc[2];  // median tiles moved incrementally, and of them redone
   unsigned long long nnear;      // FP64 decisions with |rho^2 / rho_th^2 - 1| < 2e-9
   unsigned long long nuncertain; // FP32 decisions (mixed precision) inside the screen's bound
   unsigned err;
@@ -131,20 +130,6 @@ struct Dirty {
   }
 };
 
-// What the latest re-sort of each chunk changed: the positions whose key changed, with their
-// old and new keys (the bits of the sort keys, widened to 64 bits), at most kChangeMax per
-// chunk, or cnt = -1 when the chunk was sorted from scratch.  With them, and the element each
-// output selected last time (anchor), a median tile whose chunks changed in a few positions
-// moves every output's median from the previous one instead of selecting it again.
-constexpr int kChangeMax = 128;
-struct ChangeLog {
-  int* cnt;                     // [nch]
-  uint16_t* pos;                // [nch][kChangeMax], position within the chunk
-  unsigned long long* old_key;  // [nch][kChangeMax]
-  unsigned long long* new_key;  // [nch][kChangeMax]
-  int* anchor;                  // [2][n]: bin of the upper, then of the lower median element
-};
-
 // Output epilogue of the kernel that writes S_gal.
 struct SgOut {
   double* out;           // S_gal (or the median of median-then-mean)
@@ -223,13 +208,12 @@ void launch_max_bits(const double* x, long long n, unsigned long long* max_bits,
 
 // Sort every chunk of the input whose values changed (sorted keys, position -> rank).
 void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned long long* skey,
-                       uint16_t* srank, Dirty d, ChangeLog log, cudaStream_t st);
+                       uint16_t* srank, Dirty d, cudaStream_t st);
 
 // out = C * running median from the sorted chunks, recomputed in the tiles whose windows
 // changed.
 void launch_running_median(const unsigned long long* skey, const uint16_t* srank, long long n,
-                           const SmoothPlan& pl, SgOut o, Dirty d, ChangeLog log,
-                           cudaStream_t st);
+                           const SmoothPlan& pl, SgOut o, Dirty d, cudaStream_t st);
 size_t median_smem_bytes(int Kc, int key_bytes);
 
 // Exact 128-bit prefix sums of the input inside each chunk at a per-chunk scale sig[b];

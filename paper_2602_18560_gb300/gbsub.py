@@ -379,10 +379,9 @@ def sub_coarse_grain(ctx, x=None, nbins=100, add_instr=False):
 def sub_get_work(ctx):
     """Work-list items the loop kernels of the last run were handed, by list: chunks whose
     values changed, chunks within one and within two of them, median tiles."""
-    w = (ctypes.c_int64 * 6)()
-    _check(ctx, lib().sub_get_work(ctx, w, 6))
-    return {"changed": w[0], "within1": w[1], "within2": w[2], "tiles": w[3],
-            "median_incremental": w[4], "median_redone": w[5]}
+    w = (ctypes.c_int64 * 4)()
+    _check(ctx, lib().sub_get_work(ctx, w, 4))
+    return {"changed": w[0], "within1": w[1], "within2": w[2], "tiles": w[3]}
 
 
 def sub_get_timing(ctx):
