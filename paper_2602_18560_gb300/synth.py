@@ -250,6 +250,31 @@ def single_constants(pop: Population):
                 d=_F(d), c=_F(c), pref=_F(pref), log1e3=_F(plog32(_F(1e-3))))
 
 
+def _gamma32(d, c, lo, hi, k0, k1):
+    """Gamma(d + 1/3, 1) in single precision (Marsaglia-Tsang with constants d, c), a
+    polar-method normal per counter-based attempt; d itself when every attempt is refused."""
+    X = np.full(lo.shape, d, dtype=np.float32)
+    todo = np.arange(lo.size)
+    for t in range(_MAX_GAMMA_TRIES):
+        if todo.size == 0:
+            break
+        y0, y1, y2, y3 = philox4x32_10(lo[todo], hi[todo], _STREAM_GAMMA + t, 0, k0, k1)
+        p = _F(2.0) * u32f(y0) - _F(1.0)
+        q = _F(2.0) * u32f(y1) - _F(1.0)
+        s2 = p * p + q * q
+        inside = (s2 < _F(1.0)) & (s2 > _F(0.0))
+        s2 = np.where(inside, s2, _F(0.5)).astype(np.float32)
+        z = p * np.sqrt(_F(-2.0) * plog32(s2) / s2)
+        v = _F(1.0) + c * z
+        ok = inside & (v > _F(0.0))
+        v = np.where(ok, v * v * v, _F(1.0)).astype(np.float32)
+        ua = u32f(y2)
+        acc = ok & (plog32(ua) < _F(0.5) * z * z + d - d * v + d * plog32(v))
+        X[todo[acc]] = (d * v)[acc]
+        todo = todo[~acc]
+    return X
+
+
 def catalog_single(n: int, seed: int, pop: Population | None = None, start: int = 0,
                    chunk: int = 1 << 22):
     """Sources start .. start+n-1 of the single-precision recipe with this seed, as FP64
@@ -277,30 +302,252 @@ def catalog_single(n: int, seed: int, pop: Population | None = None, start: int 
             lf = k["lmin"] + u * k["span"]
         fs = pexp32(lf)
         mc = (_F(0.2) + _F(0.6) * u32f(x2)) * gm
-        # Gamma(shape, 1): Marsaglia-Tsang, a polar-method normal per attempt
-        X = np.full(idx.shape, k["d"], dtype=np.float32)
-        todo = np.arange(idx.size)
-        for t in range(_MAX_GAMMA_TRIES):
-            if todo.size == 0:
-                break
-            y0, y1, y2, y3 = philox4x32_10(lo[todo], hi[todo], _STREAM_GAMMA + t, 0, k0, k1)
-            p = _F(2.0) * u32f(y0) - _F(1.0)
-            q = _F(2.0) * u32f(y1) - _F(1.0)
-            s2 = p * p + q * q
-            inside = (s2 < _F(1.0)) & (s2 > _F(0.0))
-            s2 = np.where(inside, s2, _F(0.5)).astype(np.float32)
-            z = p * np.sqrt(_F(-2.0) * plog32(s2) / s2)
-            v = _F(1.0) + k["c"] * z
-            ok = inside & (v > _F(0.0))
-            v = np.where(ok, v * v * v, _F(1.0)).astype(np.float32)
-            ua = u32f(y2)
-            acc = ok & (plog32(ua) < _F(0.5) * z * z + k["d"] - k["d"] * v + k["d"] * plog32(v))
-            X[todo[acc]] = (k["d"] * v)[acc]
-            todo = todo[~acc]
+        X = _gamma32(k["d"], k["c"], lo, hi, k0, k1)
         f[s:e] = fs
         fdot[s:e] = k["pref"] * pexp32(_F(5.0 / 3.0) * plog32(mc) + _F(11.0 / 3.0) * lf)
         A[s:e] = (_F(1e-23) * X) * pexp32(_F(2.0 / 3.0) * (lf - k["log1e3"]))
     return A, f, fdot
+
+
+# ------------------------------------------------------------------ the paper's population model
+# Sec. II.B "Population model" and Table I: f from a power law p(f) ~ f^alpha_pl on
+# [0.1, 10] mHz; the rescaled log frequency derivative xi = log10(fdot) - mu_g ~ Gamma with
+# concentration alpha_g and rate beta_g; the rescaled log amplitude
+# log10(f^(-2/3) A) - mu ~ log-normal of width sigma; f and xi tied by a Gaussian copula of
+# correlation rho (App. A).  The copula is sampled by conditioning, which gives the joint
+# distribution of App. A's four steps: xi from its marginal, z2 = Phi^-1(F_Gamma(xi)), then
+# z1 = rho z2 + sqrt(1 - rho^2) n with an independent normal n, and f = F_f^-1(Phi(z1)) (the
+# tail probability Phi(-z1) enters the inverse CDF, so the sparse high-frequency end keeps
+# its precision).  Single precision with basic operations only, as the device generator;
+# special functions from published methods: the inverse normal CDF by Wichura's AS241 in
+# its single-precision form PPND7 (Applied Statistics 37, 1988), erfc by the Chebyshev fit of Numerical Recipes (Press et al., 2nd ed., Sec. 6.2), the
+# regularized incomplete gamma function by its series and its continued fraction (modified
+# Lentz), log Gamma by the Lanczos form with g = 5 (Sec. 6.1 there).
+
+# Table I prior ranges of the population parameters (and N_b).
+PAPER_PRIOR = {"alpha_pl": (-4.0, -2.0), "alpha_g": (1.0, 3.0), "beta_g": (1.0, 3.0),
+               "mu_g": (-22.0, -20.0), "mu": (-23.0, -21.0), "sigma": (0.1, 0.3),
+               "rho": (0.0, 1.0), "n_b": (5e6, 3e7)}
+
+_STREAM_PAPER = 32  # the copula's and the amplitude's uniforms
+_LN10_32 = _F(2.302585092994046)
+# AS241 (Wichura 1988, Applied Statistics 37, 477), the single-precision version PPND7
+_PP_A = [_F(x) for x in (59.109374720, 159.29113202, 50.434271938, 3.3871327179)]
+_PP_B = [_F(x) for x in (67.187563600, 78.757757664, 17.895169469)]
+_PP_C = [_F(x) for x in (0.17023821103, 1.3067284816, 2.7568153900, 1.4234372777)]
+_PP_D = [_F(x) for x in (0.12021132975, 0.73700164250)]
+_PP_E = [_F(x) for x in (0.017337203997, 0.42868294337, 3.0812263860, 6.6579051150)]
+_PP_F = [_F(x) for x in (0.012258202635, 0.24197894225)]
+_ERFC_C = [_F(x) for x in (0.17087277, -0.82215223, 1.48851587, -1.13520398, 0.27886807,
+                           -0.18628806, 0.09678418, 0.37409196, 1.00002368, -1.26551223)]
+_LANCZOS = [_F(x) for x in (76.18009172947146, -86.50532032941677, 24.01409824083091,
+                            -1.231739572450155, 0.1208650973866179e-2, -0.5395239384953e-5)]
+_GAMMA_ITERS = 64
+_EPS32 = _F(5.9604644775390625e-08)     # 2^-24
+_FPMIN32 = _F(1e-30)
+
+
+def _horner32(x, coefs, one_last=False):
+    acc = np.full(x.shape, coefs[0], dtype=np.float32)
+    for c in coefs[1:]:
+        acc = acc * x + c
+    if one_last:
+        acc = acc * x + _F(1.0)
+    return acc
+
+
+def norm_ppf_lower32(t):
+    """Phi^-1(t) for 0 < t <= 1/2 (AS241 PPND7), single precision."""
+    t = np.asarray(t, dtype=np.float32)
+    q = t - _F(0.5)
+    central = np.abs(q) <= _F(0.425)
+    r = _F(0.180625) - q * q
+    x_c = q * _horner32(r, _PP_A) / _horner32(r, _PP_B, True)
+    rt = np.sqrt(_F(0.0) - plog32(np.where(central, _F(0.5), t)))
+    near = rt <= _F(5.0)
+    r1 = rt - _F(1.6)
+    r2 = rt - _F(5.0)
+    v = np.where(near, _horner32(r1, _PP_C) / _horner32(r1, _PP_D, True),
+                 _horner32(r2, _PP_E) / _horner32(r2, _PP_F, True))
+    return np.where(central, x_c, _F(0.0) - v).astype(np.float32)
+
+
+def norm_ppf32(u):
+    """Phi^-1(u) for 0 < u < 1: the lower half directly, the upper one by symmetry (1 - u is
+    exact in single precision for u >= 1/2)."""
+    u = np.asarray(u, dtype=np.float32)
+    low = u <= _F(0.5)
+    return np.where(low, norm_ppf_lower32(np.where(low, u, _F(0.5))),
+                    -norm_ppf_lower32(np.where(low, _F(0.5), _F(1.0) - u))).astype(np.float32)
+
+
+def erfc32(x):
+    """erfc(x) for x >= 0 (fractional error below 1.2e-7), single precision."""
+    x = np.asarray(x, dtype=np.float32)
+    t = _F(1.0) / (_F(1.0) + _F(0.5) * x)
+    acc = np.full(x.shape, _ERFC_C[0], dtype=np.float32)
+    for c in _ERFC_C[1:]:
+        acc = acc * t + c
+    arg = np.maximum(_F(0.0) - x * x + acc, _F(-87.0))
+    return t * pexp32(arg)
+
+
+def norm_sf32(z):
+    """Phi(-z) = 1 - Phi(z), the upper tail probability, single precision."""
+    z = np.asarray(z, dtype=np.float32)
+    pos = z >= _F(0.0)
+    e = _F(0.5) * erfc32(np.abs(z) * _F(0.7071067811865476))
+    return np.where(pos, e, _F(1.0) - e).astype(np.float32)
+
+
+def lgamma32(a):
+    """log Gamma(a) for a > 0 (Lanczos, g = 5, six terms), single precision."""
+    x = _F(a)
+    y = x
+    tmp = x + _F(5.5)
+    tmp = tmp - (x + _F(0.5)) * plog32(tmp)
+    ser = _F(1.000000000190015)
+    for c in _LANCZOS:
+        y = y + _F(1.0)
+        ser = ser + c / y
+    return _F(-tmp + plog32(_F(2.5066282746310005) * ser / x))
+
+
+def gamma_pq32(a, x, gln):
+    """(P, Q) = regularized lower and upper incomplete gamma functions of shape a at x >= 0,
+    single precision: the series for x < a + 1 (then Q = 1 - P), the continued fraction
+    for Q otherwise (then P = 1 - Q); at most 64 terms.  gln = lgamma32(a)."""
+    a = _F(a)
+    x = np.asarray(x, dtype=np.float32)
+    xs = np.maximum(x, _F(1e-30))
+    pref_arg = np.maximum((_F(0.0) - x + a * plog32(xs)) - _F(gln), _F(-87.0))
+    pref = pexp32(pref_arg)
+    use_ser = x < a + _F(1.0)
+    # series: sum_n x^n / (a (a+1) ... (a+n))
+    ap = np.full(x.shape, a, dtype=np.float32)
+    ssum = np.full(x.shape, _F(1.0) / a, dtype=np.float32)
+    dl = ssum.copy()
+    act = use_ser.copy()
+    for _ in range(_GAMMA_ITERS):
+        if not act.any():
+            break
+        ap_n = ap + _F(1.0)
+        dl_n = dl * x / ap_n
+        s_n = ssum + dl_n
+        ap = np.where(act, ap_n, ap)
+        dl = np.where(act, dl_n, dl)
+        ssum = np.where(act, s_n, ssum)
+        act = act & ~(np.abs(dl_n) < np.abs(s_n) * _EPS32)
+    P_ser = ssum * pref
+    # continued fraction for Q (modified Lentz)
+    b = x + _F(1.0) - a
+    c = np.full(x.shape, _F(1.0) / _FPMIN32, dtype=np.float32)
+    d = _F(1.0) / np.where(use_ser, _F(1.0), b)
+    h = d.copy()
+    act = ~use_ser
+    for i in range(1, _GAMMA_ITERS + 1):
+        if not act.any():
+            break
+        an = _F(-i) * (_F(i) - a)
+        b_n = b + _F(2.0)
+        d_n = an * d + b_n
+        d_n = np.where(np.abs(d_n) < _FPMIN32, _FPMIN32, d_n)
+        c_n = b_n + an / c
+        c_n = np.where(np.abs(c_n) < _FPMIN32, _FPMIN32, c_n)
+        d_n = _F(1.0) / d_n
+        de = d_n * c_n
+        h_n = h * de
+        b = np.where(act, b_n, b)
+        d = np.where(act, d_n, d)
+        c = np.where(act, c_n, c)
+        h = np.where(act, h_n, h)
+        act = act & ~(np.abs(de - _F(1.0)) < _EPS32)
+    Q_cf = pref * h
+    P = np.where(use_ser, P_ser, _F(1.0) - Q_cf).astype(np.float32)
+    Q = np.where(use_ser, _F(1.0) - P_ser, Q_cf).astype(np.float32)
+    return P, Q
+
+
+@dataclass
+class PaperPopulation:
+    """Population parameters Lambda of the paper (Table I), N_b aside."""
+    alpha_pl: float = -2.9    # p(f) ~ f^alpha_pl
+    alpha_g: float = 1.96     # Gamma concentration of xi = log10 fdot - mu_g
+    beta_g: float = 1.8       # Gamma rate
+    mu_g: float = -21.0
+    mu: float = -22.0         # log10(f^(-2/3) A) - mu ~ log-normal(sigma)
+    sigma: float = 0.18
+    rho: float = 0.99         # copula correlation of f and xi
+
+
+def paper_constants(pop: PaperPopulation):
+    """Per-population constants of the paper recipe (float32, as the device computes them)."""
+    k = single_constants(Population(gamma=-pop.alpha_pl, shape=pop.alpha_g))
+    rho = _F(pop.rho)
+    k.update(beta=_F(pop.beta_g), alpha=_F(pop.alpha_g), gln=lgamma32(pop.alpha_g),
+             mu_g=_F(pop.mu_g), mu=_F(pop.mu), sigma=_F(pop.sigma), rho=rho,
+             rho_c=np.sqrt(_F(1.0) - rho * rho))
+    return k
+
+
+def catalog_paper(n: int, seed: int, pop: PaperPopulation | None = None, start: int = 0,
+                  chunk: int = 1 << 21, with_latent: bool = False):
+    """Sources start .. start+n-1 of the paper's population model with this seed, in single
+    precision, as FP64 (A, f, fdot): the catalog the device generator produces.  With
+    with_latent, also (xi, log-normal amplitude factor, z1, z2) for tests."""
+    pop = pop or PaperPopulation()
+    if pop.alpha_g < 1.0:
+        raise ValueError("alpha_g must be >= 1")
+    k = paper_constants(pop)
+    kp = single_constants(Population(gamma=-pop.alpha_pl))
+    k0, k1 = seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF
+    A, f, fdot = np.empty(n), np.empty(n), np.empty(n)
+    lat = [np.empty(n, dtype=np.float32) for _ in range(4)] if with_latent else None
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        idx = np.arange(start + s, start + e, dtype=np.int64)
+        lo = (idx & 0xFFFFFFFF).astype(np.uint64)
+        hi = (idx >> 32).astype(np.uint64)
+        # xi = G / beta, G ~ Gamma(alpha_g, 1); its CDF value as a standard normal z2
+        G = _gamma32(k["d"], k["c"], lo, hi, k0, k1)
+        xi = G / k["beta"]
+        P, Q = gamma_pq32(k["alpha"], G, k["gln"])
+        low = P <= _F(0.5)
+        z2 = np.where(low, norm_ppf_lower32(np.where(low, P, _F(0.5))),
+                      -norm_ppf_lower32(np.where(low, _F(0.5), Q))).astype(np.float32)
+        x0, x1, x2, x3 = philox4x32_10(lo, hi, _STREAM_PAPER, 0, k0, k1)
+        z1 = k["rho"] * z2 + k["rho_c"] * norm_ppf32(u32f(x0))
+        # f from the tail probability of z1 (small: the sparse high-frequency end)
+        ut = norm_sf32(z1)
+        if kp["power"]:
+            lf = kp["lf0"] + kp["inv_e"] * plog32(kp["rho"] + ut * kp["omr"])
+        else:
+            lf = kp["lmin"] + (_F(1.0) - ut) * kp["span"]
+        fs = pexp32(lf)
+        fd = pexp32(_LN10_32 * (k["mu_g"] + xi))
+        am = pexp32(k["sigma"] * norm_ppf32(u32f(x1)))
+        a = pexp32(_F(2.0 / 3.0) * lf + _LN10_32 * (k["mu"] + am))
+        A[s:e], f[s:e], fdot[s:e] = a, fs, fd
+        if with_latent:
+            for arr, v in zip(lat, (xi, am, z1, z2)):
+                arr[s:e] = v
+    if with_latent:
+        return A, f, fdot, lat
+    return A, f, fdot
+
+
+def paper_population_draw(seed: int, index: int):
+    """Lambda and N_b from the Table I priors (independent uniforms), for draw `index`."""
+    x0, x1, x2, x3 = philox4x32_10(index & 0xFFFFFFFF, index >> 32, _STREAM_POP + 2, 0,
+                                   seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    y0, y1, y2, y3 = philox4x32_10(index & 0xFFFFFFFF, index >> 32, _STREAM_POP + 3, 0,
+                                   seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    us = [float(u32(w)) for w in (x0, x1, x2, x3, y0, y1, y2, y3)]
+    names = ("alpha_pl", "alpha_g", "beta_g", "mu_g", "mu", "sigma", "rho", "n_b")
+    v = {nm: PAPER_PRIOR[nm][0] + u * (PAPER_PRIOR[nm][1] - PAPER_PRIOR[nm][0])
+         for nm, u in zip(names, us)}
+    n_b = int(round(v.pop("n_b")))
+    return PaperPopulation(**v), n_b
 
 
 def population_draw(seed: int, index: int, gamma_range=(3.0, 4.5), shape_range=(1.5, 3.0)):
