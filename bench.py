@@ -652,6 +652,16 @@ def main():
     except Exception as exc:  # reported, not fatal
         screen = {"error": str(exc)}
 
+    # ---------------------------------------------------------------- the paper's simulator
+    # population parameters and N_b drawn from the Table I priors, the catalog drawn on the
+    # device from the paper's population model (Gaussian copula), subtracted, coarse-grained
+    prior = None
+    if ws == 1 and not args.no_batch:
+        try:
+            prior = prior_record(args, est)
+        except Exception as exc:  # reported, not fatal
+            prior = {"error": repr(exc)}
+
     # ---------------------------------------------------------------- batched and served records
     batch = serve = None
     if ws == 1 and not args.no_batch:
@@ -711,7 +721,7 @@ def main():
                                                if len(per_iter) > 2 else None),
                   "prepass_ms": pre_ms, "loop_ms": loop_ms},
         "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "fp32_screen": screen, "batch": batch, "serve": serve,
+        "fp32_screen": screen, "batch": batch, "serve": serve, "simulate_prior": prior,
         "coarse_grain": cg, "generated": gen,
         "gpu_launches": launches, "parity": parity,
     }
@@ -722,6 +732,44 @@ def main():
     if pg:
         pg.destroy_process_group()
 
+
+
+# ============================================================================ the paper's simulator
+
+PRIOR_SEED = 6
+
+
+def prior_record(args, est, draws=12, T_obs=4 * synth.YEAR):
+    """The paper's simulator end to end: Lambda and N_b from the Table I priors, the catalog of
+    the paper's population model drawn inside the catalog pass (nothing crosses the host
+    link), the subtraction, and the 100-bin coarse-grained foreground back on the host."""
+    import torch
+    from paper_2602_18560_gb300 import gbsub
+    draws_ = [synth.paper_population_draw(PRIOR_SEED, i) for i in range(draws)]
+    nmax = max(n for _, n in draws_)
+    s = gbsub.Subtraction(T_obs=T_obs, window=args.window, estimator=est)
+    s.load_population(nmax, 1, draws_[0][0], fused=True)
+    s.run()  # sizes the context and builds its graph
+    times, rows = [], []
+    for i, (pop, n) in enumerate(draws_):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.load_population(n, PRIOR_SEED * 1000003 + i, pop, fused=True)
+        st = s.run()
+        Sk, fk, ck = s.coarse_grain()
+        times.append(time.perf_counter() - t0)
+        rows.append({"n_b": n, "iterations": st.iterations, "n_resolved": st.n_resolved,
+                     "ms": times[-1] * 1e3})
+    s.close()
+    ntot = sum(n for _, n in draws_)
+    return {"workload": "%d draws of Lambda and N_b from the Table I priors (N_b in [5e6, 3e7], "
+                        "total %d sources), T_obs = 4 yr, catalogs of the paper's population "
+                        "model drawn on the device" % (draws, ntot),
+            "api": "sub_load_population(fused) + sub_run + sub_coarse_grain(100 bins) -> host",
+            "ms_per_simulation": 1e3 * sum(times) / len(times),
+            "simulations_per_s": len(times) / sum(times),
+            "sources_per_s": ntot / sum(times),
+            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 100 * 24, "draws": rows}
 
 
 # ============================================================================ batched catalogs

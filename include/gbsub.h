@@ -162,6 +162,31 @@ int sub_load_catalog(sub_ctx* ctx, const double* A, const double* f, const doubl
 int sub_load_generated(sub_ctx* ctx, int64_t n, uint64_t seed, double gamma, double shape,
                        int32_t fused);
 
+/* Population parameters of the paper's model (Sec. II.B "Population model", Table I; the
+ * number of binaries N_b is the n argument of the calls that take one). */
+typedef struct {
+  double alpha_pl;  /* power-law index: p(f) ~ f^alpha_pl on [0.1, 10] mHz; prior U(-4, -2)   */
+  double alpha_g;   /* Gamma concentration of xi = log10(fdot / Hz s^-1) - mu_g; U(1, 3)       */
+  double beta_g;    /* Gamma rate of xi; U(1, 3)                                              */
+  double mu_g;      /* offset of log10 fdot; U(-22, -20)                                      */
+  double mu;        /* log10((f/Hz)^(-2/3) A) - mu is log-normal; U(-23, -21)                  */
+  double sigma;     /* width of that log-normal; U(0.1, 0.3)                                  */
+  double rho;       /* Gaussian-copula correlation of f and fdot (App. A), 0 <= rho < 1; U(0, 1) */
+} sub_population;
+
+/* Generate a catalog of the paper's population model on the device instead of loading one:
+ * f, xi and the rescaled amplitude from their marginals (power law, Gamma, log-normal) with
+ * f and xi tied by the Gaussian copula of App. A (sampled by conditioning: xi from its
+ * marginal, its CDF value as a normal z2, then z1 = rho z2 + sqrt(1 - rho^2) n and f from the
+ * power law at Phi(z1)); fdot = 10^(mu_g + xi), A = f^(2/3) 10^(mu + rescaled amplitude).
+ * Source s is a pure function of (seed, s) in single-precision arithmetic of basic
+ * operations, as for sub_load_generated.
+ *   n, seed, fused : as sub_load_generated;  pop : the parameters above (copied)
+ * Errors: SUB_EINVAL (a parameter outside the ranges in sub_last_error), SUB_ENOMEM,
+ * SUB_EBUDGET, SUB_ECUDA. */
+int sub_load_population(sub_ctx* ctx, int64_t n, uint64_t seed, const sub_population* pop,
+                        int32_t fused);
+
 /* Sources start .. start+n-1 of the current catalog into A, f, fdot (n doubles each, at
  * `where`): copied from where the catalog lives, or generated again for a fused generated
  * catalog.  Synchronises.  Errors: SUB_EINVAL, SUB_ESTATE (no catalog), SUB_ECUDA. */
@@ -441,6 +466,13 @@ int sub_server_submit(sub_server* s, int64_t job_id, double T_obs, const double*
 int sub_server_submit_generated(sub_server* s, int64_t job_id, double T_obs, int64_t n,
                                 uint64_t seed, double gamma, double shape, double* S_gal,
                                 int64_t cap, uint8_t* mask);
+
+/* Queue a job whose catalog of n sources is drawn on the device from the paper's population
+ * model (sub_load_population, fused) with parameters pop (copied) and this seed.  S_gal and
+ * mask as for sub_server_submit.  Errors: SUB_EINVAL, SUB_ESTATE. */
+int sub_server_submit_population(sub_server* s, int64_t job_id, double T_obs, int64_t n,
+                                 uint64_t seed, const sub_population* pop, double* S_gal,
+                                 int64_t cap, uint8_t* mask);
 
 /* Move up to cap finished jobs into out, waiting up to timeout_ms for the first one
  * (0: no wait).  Returns how many were written. */

@@ -380,6 +380,42 @@ extern "C" int sub_load_generated(sub_ctx* c, int64_t n, uint64_t seed, double g
   return SUB_OK;
 }
 
+extern "C" int sub_load_population(sub_ctx* c, int64_t n, uint64_t seed, const sub_population* pop,
+                                   int32_t fused) {
+  if (!c) return SUB_EINVAL;
+  if (!pop || n < 0 || n > ((int64_t)1 << 40) || !(pop->alpha_pl >= -10.0 && pop->alpha_pl <= 8.0) ||
+      !(pop->alpha_g >= 1.0 && pop->alpha_g <= 1e3) || !(pop->beta_g > 0.0 && pop->beta_g <= 1e3) ||
+      !(pop->mu_g >= -40.0 && pop->mu_g <= 0.0) || !(pop->mu >= -40.0 && pop->mu <= 0.0) ||
+      !(pop->sigma > 0.0 && pop->sigma <= 10.0) || !(pop->rho >= 0.0 && pop->rho < 1.0)) {
+    set_err(c, "population catalog: need 0 <= n <= 2^40, -10 <= alpha_pl <= 8, 1 <= alpha_g <= "
+               "1e3, 0 < beta_g <= 1e3, -40 <= mu_g, mu <= 0, 0 < sigma <= 10, 0 <= rho < 1");
+    return SUB_EINVAL;
+  }
+  {
+    int rc = reserve_sources(c, n);
+    if (rc) return rc;
+  }
+  PaperPop pp;
+  pp.alpha_pl = pop->alpha_pl;
+  pp.alpha_g = pop->alpha_g;
+  pp.beta_g = pop->beta_g;
+  pp.mu_g = pop->mu_g;
+  pp.mu = pop->mu;
+  pp.sigma = pop->sigma;
+  pp.rho = pop->rho;
+  if (fused) {
+    launch_gen_setup_paper(c->dcat, n, seed, pp, nullptr, nullptr, nullptr, c->stream);
+  } else {
+    launch_gen_setup_paper(c->dcat, n, seed, pp, c->A, c->f, c->fdot, c->stream);
+    launch_generate(c->dcat, 0, n, c->A, c->f, c->fdot, c->stream);
+  }
+  CU(cudaGetLastError(), c);
+  c->N = n;
+  c->ran = false;
+  c->cat_kind = fused ? kCatGenerated : kCatDevice;
+  return SUB_OK;
+}
+
 extern "C" int sub_get_catalog(sub_ctx* c, double* A, double* f, double* fdot, int64_t start,
                                int64_t n, int where) {
   if (!c) return SUB_EINVAL;

@@ -696,8 +696,9 @@ void launch_set_catalog(CatalogRef* p, const CatalogRef& v, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- generated catalogs
-__global__ void k_gen_setup(CatalogRef* ref, long long n, unsigned long long seed, double gamma,
-                            double shape, const double* A, const double* f, const double* fdot) {
+// The recipe's constants for the power law f^-gamma and Gamma(shape, 1), computed on the device
+// (so that no host compiler contracts them into fused multiply-adds).
+__device__ GenParams gen_setup(unsigned long long seed, double gamma, double shape) {
   GenParams g;
   g.k0 = (unsigned)seed;
   g.k1 = (unsigned)(seed >> 32);
@@ -716,6 +717,13 @@ __global__ void k_gen_setup(CatalogRef* ref, long long n, unsigned long long see
   g.pref = __fmul_rn((float)19.2, gen_exp(__fmul_rn((float)(8.0 / 3.0),
                                                     gen_log((float)3.141592653589793))));
   g.log1e3 = gen_log((float)1e-3);
+  g.kind = 0;
+  g.beta = g.alpha = g.gln = g.mu_g = g.mu = g.sigma = g.rho_cop = g.rho_c = 0.0f;
+  return g;
+}
+
+__device__ void gen_publish(CatalogRef* ref, long long n, const GenParams& g, const double* A,
+                            const double* f, const double* fdot) {
   CatalogRef r;
   r.A = A;
   r.f = f;
@@ -727,10 +735,39 @@ __global__ void k_gen_setup(CatalogRef* ref, long long n, unsigned long long see
   *ref = r;
 }
 
+__global__ void k_gen_setup(CatalogRef* ref, long long n, unsigned long long seed, double gamma,
+                            double shape, const double* A, const double* f, const double* fdot) {
+  gen_publish(ref, n, gen_setup(seed, gamma, shape), A, f, fdot);
+}
+
+// The paper's population: the power law p(f) ~ f^alpha_pl (gamma = -alpha_pl), Gamma of shape
+// alpha_g, and the copula, amplitude and rate constants.
+__global__ void k_gen_setup_paper(CatalogRef* ref, long long n, unsigned long long seed,
+                                  PaperPop pp, const double* A, const double* f,
+                                  const double* fdot) {
+  GenParams g = gen_setup(seed, -pp.alpha_pl, pp.alpha_g);
+  g.kind = 1;
+  g.beta = __double2float_rn(pp.beta_g);
+  g.alpha = __double2float_rn(pp.alpha_g);
+  g.gln = gen_lgamma(g.alpha);
+  g.mu_g = __double2float_rn(pp.mu_g);
+  g.mu = __double2float_rn(pp.mu);
+  g.sigma = __double2float_rn(pp.sigma);
+  g.rho_cop = __double2float_rn(pp.rho);
+  g.rho_c = __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(g.rho_cop, g.rho_cop)));
+  gen_publish(ref, n, g, A, f, fdot);
+}
+
 void launch_gen_setup(CatalogRef* ref, long long n, unsigned long long seed, double gamma,
                       double shape, const double* A, const double* f, const double* fdot,
                       cudaStream_t st) {
   k_gen_setup<<<1, 1, 0, st>>>(ref, n, seed, gamma, shape, A, f, fdot);
+}
+
+void launch_gen_setup_paper(CatalogRef* ref, long long n, unsigned long long seed,
+                            const PaperPop& pp, const double* A, const double* f,
+                            const double* fdot, cudaStream_t st) {
+  k_gen_setup_paper<<<1, 1, 0, st>>>(ref, n, seed, pp, A, f, fdot);
 }
 
 __global__ void __launch_bounds__(256) k_generate(const CatalogRef* __restrict__ ref,

@@ -189,6 +189,10 @@ void launch_set_catalog(CatalogRef* p, const CatalogRef& v, cudaStream_t st);
 void launch_gen_setup(CatalogRef* ref, long long n, unsigned long long seed, double gamma,
                       double shape, const double* A, const double* f, const double* fdot,
                       cudaStream_t st);
+// The same for the paper's population model (Sec. II.B, Table I; App. A).
+void launch_gen_setup_paper(CatalogRef* ref, long long n, unsigned long long seed,
+                            const PaperPop& pp, const double* A, const double* f,
+                            const double* fdot, cudaStream_t st);
 // Sources start .. start+n-1 of the generated catalog described by ref->gen into A, f, fdot.
 void launch_generate(const CatalogRef* ref, long long start, long long n, double* A, double* f,
                      double* fdot, cudaStream_t st);

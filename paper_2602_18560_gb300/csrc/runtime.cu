@@ -222,8 +222,10 @@ struct Job {
   int64_t cap = 0;
   uint8_t* mask_out = nullptr;
   bool generated = false;  // the catalog is drawn on the device from (seed, gamma, shape)
+  bool paper = false;      // ... or from (seed, pop): the paper's population model
   uint64_t seed = 0;
   double gamma = 0.0, shape = 0.0;
+  sub_population pop = {};
   Clock::time_point t_submit, t_admit, t_done;
 };
 
@@ -382,8 +384,9 @@ static Slot* acquire_slot(sub_server* s, const Job& j, int* fail_status, bool id
 static int launch_job(sub_server* s, Slot* sl, Job& j) {
   sub_ctx* c = sl->ctx;
   const int64_t before = sub_device_bytes(c);
-  int rc = j.generated ? sub_load_generated(c, j.n, j.seed, j.gamma, j.shape, 1)
-                       : sub_load_catalog(c, j.A, j.f, j.fdot, j.n, SUB_HOST);
+  int rc = j.paper       ? sub_load_population(c, j.n, j.seed, &j.pop, 1)
+           : j.generated ? sub_load_generated(c, j.n, j.seed, j.gamma, j.shape, 1)
+                         : sub_load_catalog(c, j.A, j.f, j.fdot, j.n, SUB_HOST);
   s->pool_bytes += sub_device_bytes(c) - before;
   if (rc) return rc;
   rc = sub_run(c, nullptr);
@@ -612,6 +615,44 @@ extern "C" int sub_server_submit_generated(sub_server* s, int64_t job_id, double
   j.seed = seed;
   j.gamma = gamma;
   j.shape = shape;
+  j.t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return SUB_ESTATE;
+    s->queue.push_back(j);
+  }
+  s->cv_work.notify_one();
+  return SUB_OK;
+}
+
+extern "C" int sub_server_submit_population(sub_server* s, int64_t job_id, double T_obs,
+                                            int64_t n, uint64_t seed, const sub_population* pop,
+                                            double* S_gal, int64_t cap, uint8_t* mask) {
+  if (!s) return SUB_EINVAL;
+  if (!pop || n < 0 || n > ((int64_t)1 << 40) || !(T_obs > 0.0) ||
+      !(pop->alpha_g >= 1.0 && pop->alpha_g <= 1e3) || !(pop->rho >= 0.0 && pop->rho < 1.0) ||
+      !(pop->beta_g > 0.0) || !(pop->sigma > 0.0) ||
+      !(pop->alpha_pl >= -10.0 && pop->alpha_pl <= 8.0)) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = "sub_server_submit_population: bad size, T_obs or population";
+    return SUB_EINVAL;
+  }
+  if (S_gal && cap < bins_of(T_obs, s->p.f_min, s->p.f_max)) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = "sub_server_submit_population: S_gal buffer smaller than the number of bins";
+    return SUB_EINVAL;
+  }
+  Job j;
+  j.id = job_id;
+  j.T_obs = T_obs;
+  j.n = n;
+  j.sg_out = S_gal;
+  j.cap = cap;
+  j.mask_out = mask;
+  j.generated = true;
+  j.paper = true;
+  j.seed = seed;
+  j.pop = *pop;
   j.t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);

@@ -76,6 +76,15 @@ class sub_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class sub_population(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("alpha_pl", "alpha_g", "beta_g", "mu_g", "mu", "sigma", "rho")]
+
+
+def _population_struct(pop):
+    return sub_population(*(float(getattr(pop, k)) for k, _ in sub_population._fields_))
+
+
 class sub_server_params(ctypes.Structure):
     _fields_ = [
         ("hbm_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
@@ -106,6 +115,7 @@ class sub_server_stats(ctypes.Structure):
 _lib = None
 _lock = threading.Lock()
 EXPORTS = ("sub_params_default", "sub_create", "sub_load_catalog", "sub_load_generated",
+           "sub_load_population", "sub_server_submit_population",
            "sub_get_catalog", "sub_run", "sub_get_stats",
            "sub_get_history", "sub_get_spectrum", "sub_get_resolved_mask", "sub_estimate",
            "sub_get_tables", "sub_get_timing", "sub_get_work", "sub_coarse_grain", "sub_profile",
@@ -155,6 +165,10 @@ def lib(build_if_missing: bool = True):
             "sub_load_generated": (i32, [P, i64, ctypes.c_uint64, ctypes.c_double,
                                          ctypes.c_double, i32]),
             "sub_get_catalog": (i32, [P, P, P, P, i64, i64, i32]),
+            "sub_load_population": (i32, [P, i64, ctypes.c_uint64, ctypes.POINTER(sub_population),
+                                          i32]),
+            "sub_server_submit_population": (i32, [P, i64, ctypes.c_double, i64, ctypes.c_uint64,
+                                                   ctypes.POINTER(sub_population), P, i64, P]),
             "sub_coarse_grain": (i32, [P, P, i32, i32, P, P, P, i32]),
             "sub_profile": (i32, [P, P, P, ctypes.POINTER(sub_stats)]),
             "sub_device_bytes": (i64, [P]),
@@ -261,6 +275,14 @@ def sub_load_generated(ctx, n, seed, gamma=11.0 / 3.0, shape=2.0, fused=True):
     catalog pass; otherwise they are generated once into device memory."""
     return _check(ctx, lib().sub_load_generated(ctx, int(n), int(seed) & (2**64 - 1),
                                                 float(gamma), float(shape), int(bool(fused))))
+
+
+def sub_load_population(ctx, n, seed, pop, fused=True):
+    """A catalog of the paper's population model (synth.PaperPopulation fields) drawn on the
+    device."""
+    ps = _population_struct(pop)
+    _check(ctx, lib().sub_load_population(ctx, int(n), int(seed) & (2**64 - 1),
+                                          ctypes.byref(ps), int(bool(fused))))
 
 
 def sub_get_catalog(ctx, start, n, device=False):
@@ -460,6 +482,12 @@ class Subtraction:
         self._mapped = None
         return self
 
+    def load_population(self, n, seed, pop, fused=True):
+        sub_load_population(self.ctx, n, seed, pop, fused)
+        self.n_sources = int(n)
+        self._mapped = None
+        return self
+
     def catalog(self, start=0, n=None, device=False):
         n = self.n_sources - start if n is None else n
         return sub_get_catalog(self.ctx, start, n, device)
@@ -648,6 +676,23 @@ class Server:
         rc = lib().sub_server_submit_generated(self.s, int(job_id), float(T_obs), int(n),
                                                int(seed) & (2**64 - 1), float(pop.gamma),
                                                float(pop.shape), ps, ncap, pm)
+        if rc != OK:
+            raise SubError(rc, lib().sub_server_last_error(self.s).decode())
+        self._keep[int(job_id)] = (S_gal_out, mask_out)
+
+    def submit_population(self, job_id, T_obs, n, seed, pop, S_gal_out=None, mask_out=None):
+        """Queue a job whose catalog is drawn on the device from the paper's population model
+        (synth.PaperPopulation); result buffers as submit_generated."""
+        ps, ws_, ncap = _ptr(S_gal_out, np.float64)
+        pm, wm, nm = _ptr(mask_out, np.uint8)
+        if (S_gal_out is not None and ws_ != HOST) or (mask_out is not None and wm != HOST):
+            raise ValueError("result buffers must be host memory")
+        if mask_out is not None and nm < n:
+            raise ValueError("mask buffer smaller than the catalog")
+        pst = _population_struct(pop)
+        rc = lib().sub_server_submit_population(self.s, int(job_id), float(T_obs), int(n),
+                                                int(seed) & (2**64 - 1), ctypes.byref(pst),
+                                                ps, ncap, pm)
         if rc != OK:
             raise SubError(rc, lib().sub_server_last_error(self.s).decode())
         self._keep[int(job_id)] = (S_gal_out, mask_out)
