@@ -247,8 +247,8 @@ extern "C" int sub_create(const sub_params* p, void* stream, sub_ctx** out) {
   launch_tables(c->grid, p->tdi2, c->S, c->R, c->gq, c->Gf, c->invSf, c->stream);
   e = cudaMemsetAsync(c->Sg, 0, (size_t)n * 8, c->stream);
   // The FP32 keys of the mixed-precision median are the powers times 2^e: the spectrum
-  // holds at most 2^31 S_instr per bin, so with e = 59 - ilogb(max S_instr) every power
-  // is below 2^91, and the smallest non-zero power (2^-64 S_instr) stays far above the
+  // holds less than 2^63 S_instr per bin, so with e = 59 - ilogb(max S_instr) every power
+  // is below 2^123, and the smallest non-zero power (2^-64 S_instr) stays far above the
   // FP32 normal range over any band whose S_instr spans less than 2^60.
   if (e == cudaSuccess) e = cudaMemsetAsync(&c->rs->max_p_bits, 0, 8, c->stream);
   if (e == cudaSuccess) launch_max_bits(c->S, n, &c->rs->max_p_bits, c->stream);
@@ -690,7 +690,7 @@ static int fill_stats(sub_ctx* c, sub_stats* st) {
     set_err(c, "the catalog holds non-finite values of A, f or fdot; those sources were skipped");
   } else if (r.err & ERR_RANGE) {
     status = SUB_ERANGE;
-    set_err(c, "a deposited power exceeded the fixed-point range (P/S_instr >= 2^31 in one bin)");
+    set_err(c, "a deposited power exceeded the fixed-point range (P/S_instr >= 2^63 in one bin)");
   } else if (!r.converged) {
     status = SUB_ENOTCONVERGED;
     set_err(c, "max_iter (%d) reached before convergence", c->p.max_iter);

@@ -15,11 +15,13 @@ constexpr double kL = 2.5e9;        // LISA arm, m (Sec. III.A)
 constexpr double kPi = 3.14159265358979323846;
 // Chi^2_2 bias of the running median, (1 - 2/(9*2))^-3 = (8/9)^-3 = 729/512 (App. D).
 constexpr double kMedianBias = 729.0 / 512.0;
-// Per-bin fixed point of the deposited power: q = (P_k / S_instr,k) * 2^96, i.e. the
-// unit is 2^-96 of the instrument noise in that bin.  A contribution must stay below
-// 2^127 units (P/S < 2^31 in one bin).
+// Scale of the deposited power in the catalog pass and the SNR thresholds: q = (P_k /
+// S_instr,k) 2^96, i.e. units of 2^-96 of the instrument noise in that bin (the spectrum
+// itself keeps q 2^-32, see q_parts).  A contribution must stay below 2^159 units (P/S below
+// 2^63 in one bin).
 constexpr double kQScale = 79228162514264337593543950336.0;                   // 2^96
-constexpr double kQLimit = 170141183460469231731687303715884105728.0;          // 2^127
+// bits of 2^159, the first value of q beyond the fixed-point range
+constexpr unsigned long long kQLimitBits = 0x49E0000000000000ull;
 constexpr int kMaxWindow = 8192;
 
 // Error bits raised on the device.
@@ -94,34 +96,37 @@ __device__ __forceinline__ double u128_to_dbl_scaled(U128 v, int sh) {
   return ldexp(__ull2double_rn(top), shift - sh);
 }
 
-// A bin of the spectrum is three 64-bit words: w0 sums bits 0-31 of every
-// contribution, w1 bits 32-63 and w2 bits 64-127 (a fourth word pads the bin to
-// 32 bytes).  w0 and w1 take fewer than 2^32 terms below 2^32, so no word overflows
-// and Q = w2 2^64 + w1 2^32 + w0 is exact whatever the order of the additions;
-// removing a contribution subtracts the same three parts.
-// Contributions are kept to whole multiples of 2^32 units (2^-64 S_instr,k): the
-// resolution stays far below any power that matters, and the lowest word is never
-// touched, so a deposit or a removal is two 64-bit atomics.
+// A bin of the spectrum is three 64-bit words holding Q = w2 2^64 + w1 2^32 + w0 in units of
+// 2^-64 S_instr of the bin (a fourth word pads the bin to 32 bytes).  Each contribution, an
+// integer number of units (q 2^-32 of its value q in units of 2^-96 S_instr, truncated), is
+// split in bits 0-31 (into w0), bits 32-63 (w1) and bits 64-127 (w2): w0 and w1 take fewer
+// than 2^32 terms below 2^32, so no word overflows while Q stays below 2^127 (P/S_instr below
+// 2^63), and Q is exact whatever the order of the additions; removing a contribution
+// subtracts the same three parts.  w2 takes a part only for a contribution of at least
+// S_instr, so most deposits are two 64-bit atomics.
 __device__ __forceinline__ void q_parts(double q, u64* c0, u64* c1, u64* c2) {
-  U128 v = dbl_to_u128_scaled(q, 0);
-  *c0 = 0ull;
+  U128 v = dbl_to_u128_scaled(q, -32);
+  *c0 = v.lo & 0xFFFFFFFFull;
   *c1 = v.lo >> 32;
   *c2 = v.hi;
 }
 
-// Fixed-point units of the deposit of a single-bin source, Q = A^2 gq (units of 2^-96 of the
-// bin's S_instr; gq = 2^96 (T/5) R / S_instr), from the integer mantissas: the top 64 bits
-// of A's mantissa squared, times gq's, the products truncated.  Q is within 2^-61 of the
-// exact A^2 gq (the FP64 product RN(RN(A A) gq) is within 2^-52) and takes no FP64
-// instruction, which on this GPU run at a small fraction of the integer rate.
-//   c1, c2 : the parts the spectrum words take (bits 32-63 and 64-127 of Q)
-//   qbits  : Q as the bits of a double (mantissa truncated), for comparisons with the bits
-//            of non-negative doubles
-// Returns false when Q >= 2^127 (beyond the fixed-point range).  A finite (its sign does not
-// matter), gq > 0 finite; A or gq zero or subnormal gives Q = 0.
-__device__ __forceinline__ bool q_single(double A, double gq, u64* c1, u64* c2, u64* qbits) {
+// The deposit of a single-bin source, q = A^2 gq (units of 2^-96 of the bin's S_instr;
+// gq = 2^96 (T/5) R / S_instr), from the integer mantissas: the top 64 bits of A's mantissa
+// squared, times gq's, the products truncated.  It is within 2^-61 of the exact A^2 gq (the
+// FP64 product RN(RN(A A) gq) is within 2^-52) and takes no FP64 instruction, which on this
+// GPU runs at a small fraction of the integer rate.
+//   c0, c1, c2 : the parts the spectrum words take (q_parts: bits 0-31, 32-63 and 64-127 of
+//                Q = q 2^-32)
+//   qbits      : q as the bits of a double (mantissa truncated), for comparisons with the
+//                bits of non-negative doubles
+// Returns false when q >= 2^159 (beyond the fixed-point range).  A finite (its sign does not
+// matter), gq > 0 finite; A or gq zero or subnormal gives q = 0.
+__device__ __forceinline__ bool q_single(double A, double gq, u64* c0, u64* c1, u64* c2,
+                                         u64* qbits) {
   const u64 ba = (u64)__double_as_longlong(A), bg = (u64)__double_as_longlong(gq);
   const int ea = (int)((ba >> 52) & 0x7FF), eg = (int)((bg >> 52) & 0x7FF);
+  *c0 = 0ull;
   *c1 = 0ull;
   *c2 = 0ull;
   *qbits = 0ull;
@@ -130,22 +135,26 @@ __device__ __forceinline__ bool q_single(double A, double gq, u64* c1, u64* c2, 
   const u64 g = ((bg & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;
   const u64 a2 = __umul64hi(a, a);  // in [2^62, 2^64)
   const u64 p = __umul64hi(a2, g);  // in [2^61, 2^64)
-  const int sh = 2 * ea + eg - 3130;  // Q = p 2^sh
+  const int sh = 2 * ea + eg - 3130;  // q = p 2^sh
   const int lz = __clzll((long long)p);
-  const int E = sh + 63 - lz;         // Q in [2^E, 2^(E+1))
-  if (E >= 127) return false;
+  const int E = sh + 63 - lz;         // q in [2^E, 2^(E+1))
+  if (E >= 159) return false;
   if (E >= -1022) *qbits = ((u64)(E + 1023) << 52) | ((p << (lz + 1)) >> 12);
-  const int t = sh - 32;              // Q / 2^32 = p 2^t
-  if (t >= 32) {
-    *c2 = p << (t - 32);
-  } else if (t >= 0) {
-    *c1 = (u64)((unsigned)p << t);
-    *c2 = p >> (32 - t);
+  const int t = sh - 32;              // Q = q 2^-32 = p 2^t, Q = hi 2^64 + lo
+  u64 lo = 0ull, hi = 0ull;
+  if (t >= 64) {
+    hi = p << (t - 64);
+  } else if (t > 0) {
+    lo = p << t;
+    hi = p >> (64 - t);
+  } else if (t == 0) {
+    lo = p;
   } else if (t > -64) {
-    const u64 y = p >> (-t);
-    *c1 = y & 0xFFFFFFFFull;
-    *c2 = y >> 32;
+    lo = p >> (-t);
   }
+  *c0 = lo & 0xFFFFFFFFull;
+  *c1 = lo >> 32;
+  *c2 = hi;
   return true;
 }
 

@@ -81,8 +81,8 @@ void launch_tables(const Grid& g, int tdi2, double* S, double* R, double* gq, fl
 
 __device__ __forceinline__ void deposit_q(unsigned long long* acc, long long j, double q,
                                           unsigned* err) {
-  // q >= 0: compare the bits with those of 2^127 (no FP64 instruction)
-  if ((u64)__double_as_longlong(q) >= 0x47E0000000000000ull) {
+  // q >= 0: compare the bits with those of 2^159 (no FP64 instruction)
+  if ((u64)__double_as_longlong(q) >= kQLimitBits) {
     atomicOr(err, ERR_RANGE);
     return;
   }
@@ -95,7 +95,7 @@ __device__ __forceinline__ void deposit_q(unsigned long long* acc, long long j, 
 }
 
 __device__ __forceinline__ void remove_q(unsigned long long* acc, long long j, double q) {
-  if ((u64)__double_as_longlong(q) >= 0x47E0000000000000ull) return;  // never deposited
+  if ((u64)__double_as_longlong(q) >= kQLimitBits) return;  // never deposited
   u64 c0, c1, c2;
   q_parts(q, &c0, &c1, &c2);
   u64* a = acc + 4 * j;
@@ -104,14 +104,18 @@ __device__ __forceinline__ void remove_q(unsigned long long* acc, long long j, d
   if (c2) atomicAdd(a + 2, (u64)(0ull - c2));
 }
 
-// The two parts of a single-bin deposit (q_single) added to, or taken from, bin j.
-__device__ __forceinline__ void add_parts(unsigned long long* acc, long long j, u64 c1, u64 c2) {
+// The parts of a single-bin deposit (q_single) added to, or taken from, bin j.
+__device__ __forceinline__ void add_parts(unsigned long long* acc, long long j, u64 c0, u64 c1,
+                                          u64 c2) {
   u64* a = acc + 4 * j;
+  if (c0) atomicAdd(a + 0, c0);
   if (c1) atomicAdd(a + 1, c1);
   if (c2) atomicAdd(a + 2, c2);
 }
-__device__ __forceinline__ void sub_parts(unsigned long long* acc, long long j, u64 c1, u64 c2) {
+__device__ __forceinline__ void sub_parts(unsigned long long* acc, long long j, u64 c0, u64 c1,
+                                          u64 c2) {
   u64* a = acc + 4 * j;
+  if (c0) atomicAdd(a + 0, (u64)(0ull - c0));
   if (c1) atomicAdd(a + 1, (u64)(0ull - c1));
   if (c2) atomicAdd(a + 2, (u64)(0ull - c2));
 }
@@ -123,7 +127,7 @@ __device__ __forceinline__ double spec_value(const SpecIn& in, long long j) {
     ulonglong2 w01 = a[0];
     u64 w2 = in.acc[4 * j + 2];
     U128 Q = q_combine3(w01.x, w01.y, w2);
-    return __dmul_rn(in.S[j], u128_to_dbl_scaled(Q, 96));
+    return __dmul_rn(in.S[j], u128_to_dbl_scaled(Q, 64));
   }
   return in.x[j];
 }
@@ -150,14 +154,16 @@ void launch_power_out(const unsigned long long* acc, const double* S, long long 
 // The catalog is dominated by the low-frequency end of the band (the number of sources
 // falls steeply with f), so the 64-bit atomics of the deposits pile up on the cache lines
 // of the first bins: an L2 line takes one atomic at a time.  The first rep.nbins bins
-// therefore have kAccReplicas private copies (words 1 and 2 of every bin), a source
-// picking one by its index; a fold adds them into the spectrum after the pass.  Integer
-// sums, so the result does not depend on the split.
-__device__ __forceinline__ void add_parts_rep(AccReplicas rep, long long j, int r, u64 c1,
-                                              u64 c2) {
+// therefore have kAccReplicas private copies (words 0 and 1 of every bin), a source
+// picking one by its index; a fold adds them into the spectrum after the pass (word 2 takes
+// a part only from a source of at least S_instr in the bin, rare, and goes to the spectrum
+// directly).  Integer sums, so the result does not depend on the split.
+__device__ __forceinline__ void add_parts_rep(AccReplicas rep, unsigned long long* acc,
+                                              long long j, int r, u64 c0, u64 c1, u64 c2) {
   u64* a = rep.w + 2 * ((size_t)r * rep.nbins + j);
-  if (c1) atomicAdd(a + 0, c1);
-  if (c2) atomicAdd(a + 1, c2);
+  if (c0) atomicAdd(a + 0, c0);
+  if (c1) atomicAdd(a + 1, c1);
+  if (c2) atomicAdd(acc + 4 * j + 2, c2);
 }
 
 __global__ void k_fold_replicas(unsigned long long* __restrict__ acc, AccReplicas rep) {
@@ -170,8 +176,8 @@ __global__ void k_fold_replicas(unsigned long long* __restrict__ acc, AccReplica
     s1 += v.x;
     s2 += v.y;
   }
-  acc[4 * j + 1] += s1;
-  acc[4 * j + 2] += s2;
+  acc[4 * j + 0] += s1;
+  acc[4 * j + 1] += s2;
 }
 
 
@@ -218,12 +224,12 @@ __device__ __noinline__ double prepass_slow(double A, double fs, double fds, con
   if (sw.ka == sw.kb) {
     long long j = sw.ka - g.k_lo;
     if (j >= 0 && j < g.nb) {
-      u64 c1, c2, qb;
-      if (!q_single(A, tb.gq[j], &c1, &c2, &qb)) {
+      u64 c0, c1, c2, qb;
+      if (!q_single(A, tb.gq[j], &c0, &c1, &c2, &qb)) {
         atomicOr(err, ERR_RANGE);
         return 0.0;
       }
-      add_parts(acc, j, c1, c2);
+      add_parts(acc, j, c0, c1, c2);
       return __longlong_as_double((long long)qb);
     }
     return 0.0;
@@ -637,12 +643,12 @@ __global__ void __launch_bounds__(kPrepassThreads, 3) k_prepass(
           valid = true;
           const long long j = k0 - g.k_lo;
           if (j >= 0 && j < g.nb) {
-            u64 c1, c2, qb;
-            if (q_single(a, tb.gq[j], &c1, &c2, &qb)) {
+            u64 c0, c1, c2, qb;
+            if (q_single(a, tb.gq[j], &c0, &c1, &c2, &qb)) {
               if (j < rep.nbins)
-                add_parts_rep(rep, j, (int)(s & (kAccReplicas - 1)), c1, c2);
+                add_parts_rep(rep, acc, j, (int)(s & (kAccReplicas - 1)), c0, c1, c2);
               else
-                add_parts(acc, j, c1, c2);
+                add_parts(acc, j, c0, c1, c2);
               r = __longlong_as_double((long long)qb);
             } else {
               atomicOr(&rs->err, ERR_RANGE);
@@ -1805,8 +1811,8 @@ __device__ __forceinline__ void remove_part(const Cands& cd, long long c, const 
   if (sw.ka == sw.kb) {
     long long j = sw.ka - g.k_lo;
     if (off == 0 && j >= 0 && j < g.nb) {
-      u64 c1, c2, qb;
-      if (q_single(cd.amp[c], tb.gq[j], &c1, &c2, &qb)) sub_parts(acc, j, c1, c2);
+      u64 c0, c1, c2, qb;
+      if (q_single(cd.amp[c], tb.gq[j], &c0, &c1, &c2, &qb)) sub_parts(acc, j, c0, c1, c2);
       d.mark_next(j / Kc);
     }
     return;
