@@ -73,6 +73,12 @@ __device__ __forceinline__ float gen_u32f(unsigned x) {
   return __fmul_rn(__fadd_rn(__uint2float_rn(x), 0.5f), 2.3283064365386963e-10f);
 }
 
+// Uniform in [2^-24, 1 - 2^-24] from the top 23 bits of a word: never 0 or 1, so that a
+// normal deviate from it stays within 5.3 standard deviations (gen_u32f can round to 1).
+__device__ __forceinline__ float gen_u23f(unsigned x) {
+  return __fmul_rn(__fadd_rn(__uint2float_rn(x >> 9), 0.5f), 1.1920928955078125e-07f);
+}
+
 __device__ __forceinline__ float gen_log(float x) {
   const float tiny = (float)1.1754943508222875e-38;  // smallest normal
   if (!(x >= tiny)) x = tiny;
@@ -272,7 +278,7 @@ __device__ __forceinline__ void gen_source_paper(const GenParams& p, long long s
   const float z2 = P <= (float)0.5 ? gen_ppf_lower(P) : -gen_ppf_lower(Q);
   unsigned x[4] = {lo, hi, kStreamPaper, 0u};
   philox4x32_10(x, p.k0, p.k1);
-  const float z1 = __fadd_rn(__fmul_rn(p.rho_cop, z2), __fmul_rn(p.rho_c, gen_ppf(gen_u32f(x[0]))));
+  const float z1 = __fadd_rn(__fmul_rn(p.rho_cop, z2), __fmul_rn(p.rho_c, gen_ppf(gen_u23f(x[0]))));
   const float ut = gen_sf(z1);
   const float lf = p.power
                        ? __fadd_rn(p.lf0, __fmul_rn(p.inv_e, gen_log(__fadd_rn(p.rho, __fmul_rn(ut, p.omr)))))
@@ -280,7 +286,7 @@ __device__ __forceinline__ void gen_source_paper(const GenParams& p, long long s
   const float ln10 = (float)2.302585092994046;
   const float fs = gen_exp(lf);
   const float fd = gen_exp(__fmul_rn(ln10, __fadd_rn(p.mu_g, xi)));
-  const float am = gen_exp(__fmul_rn(p.sigma, gen_ppf(gen_u32f(x[1]))));
+  const float am = gen_exp(__fmul_rn(p.sigma, gen_ppf(gen_u23f(x[1]))));
   const float a = gen_exp(__fadd_rn(__fmul_rn((float)(2.0 / 3.0), lf),
                                     __fmul_rn(ln10, __fadd_rn(p.mu, am))));
   *A = (double)a;

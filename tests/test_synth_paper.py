@@ -122,3 +122,14 @@ def test_prior_draws_inside_table_I():
         for name, (lo, hi) in synth.PAPER_PRIOR.items():
             v = n_b if name == "n_b" else getattr(pop, name)
             assert lo <= v <= hi, (name, v)
+
+
+def test_normal_draws_stay_bounded():
+    # the uniforms behind the copula's and the amplitude's normals are never 0 or 1 (a 32-bit
+    # word's float can round to 1, whose normal deviate would be unbounded): every normal stays
+    # within 5.34 standard deviations, so no amplitude leaves the spectrum's range
+    words = np.array([0, 1, 511, 512, 2**31, 2**32 - 513, 2**32 - 1], dtype=np.uint32)
+    u = synth.u23f(words)
+    assert np.all((u > 0) & (u < 1))
+    z = synth.norm_ppf32(u)
+    assert np.all(np.isfinite(z)) and np.max(np.abs(z)) < 5.34
