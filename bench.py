@@ -765,8 +765,12 @@ def prior_record(args, est, draws=12, T_obs=4 * synth.YEAR):
     return {"workload": "%d draws of Lambda and N_b from the Table I priors (N_b in [5e6, 3e7], "
                         "total %d sources), T_obs = 4 yr, catalogs of the paper's population "
                         "model drawn on the device" % (draws, ntot),
+            "note": "the time of a draw grows with the bins its sources sweep: the Gamma prior of "
+                    "log10 fdot puts some sources at fdot > 1e-12 Hz/s, whose sweeps of 1e4 bins "
+                    "and more are deposited by the FP64 path",
             "api": "sub_load_population(fused) + sub_run + sub_coarse_grain(100 bins) -> host",
             "ms_per_simulation": 1e3 * sum(times) / len(times),
+            "ms_per_simulation_median": 1e3 * float(np.median(times)),
             "simulations_per_s": len(times) / sum(times),
             "sources_per_s": ntot / sum(times),
             "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 100 * 24, "draws": rows}
