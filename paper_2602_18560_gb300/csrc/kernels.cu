@@ -499,7 +499,7 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity,
 }
 
 __global__ void __launch_bounds__(kPrepassThreads, 3) k_prepass(
-    const CatalogRef* __restrict__ cat, Grid g, Tables tb, double thr_kappa, double thr_live,
+    const CatalogRef* cat, Grid g, Tables tb, double thr_kappa, double thr_live,
     unsigned long long* __restrict__ acc, AccReplicas rep, Cands cd, RunState* rs,
     int test_flags) {
   extern __shared__ __align__(128) double pre_tiles[];  // [stage][A | f | fdot][kPreTile]
@@ -507,20 +507,12 @@ __global__ void __launch_bounds__(kPrepassThreads, 3) k_prepass(
   __shared__ long long stage_tile[kPreStages];  // tile held by each stage
   __shared__ long long slow_q[kPreConsumers][kSlowWarpCap];
   __shared__ int abort_flag;
-  const double* __restrict__ A = cat->A;
-  const double* __restrict__ f = cat->f;
-  const double* __restrict__ fdot = cat->fdot;
-  const long long N = cat->n;
-  const bool use_tma = cat->staged == kCatDevice;
-  const bool generated = cat->staged == kCatGenerated;
+  // the catalog record (and a generated catalog's constants), read once per CTA: every
+  // thread of the grid loading it would queue on one L2 line
+  __shared__ CatalogRef scat;
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int warp = tid >> 5;
-  const long long ntiles = (N + kPreTile - 1) / kPreTile;
-  // full tiles of device memory come through TMA; the ragged one, and every tile of a catalog
-  // in host memory or generated, through plain loads (or the generator)
-  const long long nfull = use_tma ? N / kPreTile : 0;
   if (tid == 0) {
+    scat = *cat;
     for (int k = 0; k < kPreStages; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], kPreConsumers);
@@ -529,6 +521,19 @@ __global__ void __launch_bounds__(kPrepassThreads, 3) k_prepass(
     abort_flag = 0;
   }
   __syncthreads();
+  cat = &scat;
+  const double* __restrict__ A = scat.A;
+  const double* __restrict__ f = scat.f;
+  const double* __restrict__ fdot = scat.fdot;
+  const long long N = scat.n;
+  const bool use_tma = scat.staged == kCatDevice;
+  const bool generated = scat.staged == kCatGenerated;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const long long ntiles = (N + kPreTile - 1) / kPreTile;
+  // full tiles of device memory come through TMA; the ragged one, and every tile of a catalog
+  // in host memory or generated, through plain loads (or the generator)
+  const long long nfull = use_tma ? N / kPreTile : 0;
 
   if (warp == kPreConsumers) {
     // ------------------------------------------------ producer (one lane)
@@ -1058,11 +1063,12 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
   uint16_t* sm_idx = (uint16_t*)(sm_keys + pl.kpad);
   const int T = blockDim.x, tid = threadIdx.x;
   const int kpad = pl.kpad;  // = T * E
-  const int nitem = d.count(kListR0, pl.nch);
+  const ListHead head = list_head(d, kListR0, pl.nch);
+  const int nitem = head.count;
   // after the first iteration of a tracked run every chunk holds the sorted state of its
   // previous values
-  const bool resort = d.base != nullptr && d.rs->iter > 0;
-  int b_next = d.item(kListR0, blockIdx.x);  // loaded beside the count (grid <= list length)
+  const bool resort = d.base != nullptr && head.iter > 0;
+  int b_next = head.first;
   for (int item = blockIdx.x; item < nitem; item += gridDim.x) {
     const int b = b_next;  // a chunk whose input changed
     if (item + (int)gridDim.x < nitem) b_next = d.item(kListR0, item + gridDim.x);
@@ -1446,8 +1452,9 @@ __global__ void __launch_bounds__(512, 2) k_median_wm(
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int zeros[16];
   double relmax = 0.0;
-  const int nitem = d.count(kListTile, pl.nch + 1);
-  int u_next = d.item(kListTile, blockIdx.x);  // loaded beside the count (grid <= list length)
+  const ListHead head = list_head(d, kListTile, pl.nch + 1);
+  const int nitem = head.count;
+  int u_next = head.first;
   for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
     // a tile whose windows changed
     const int u = u_next;
@@ -1606,8 +1613,9 @@ __global__ void k_chunk_prefix(SpecIn in, long long n, SmoothPlan pl,
   __shared__ int any_uf;
   // chunks whose input changed (a chunk within in_radius of them is dirty)
   const int list = kListR0 + in_radius;
-  const int nitem = d.count(list, pl.nch);
-  int b_next = d.item(list, blockIdx.x);  // loaded beside the count (grid <= list length)
+  const ListHead head = list_head(d, list, pl.nch);
+  const int nitem = head.count;
+  int b_next = head.first;
   for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
     const int b = b_next;
     if (it + (int)gridDim.x < nitem) b_next = d.item(list, it + gridDim.x);
@@ -1656,8 +1664,9 @@ __global__ void k_window_mean(const double* __restrict__ x, long long n, SmoothP
   const int h = pl.W / 2;
   // output chunks with a dirty chunk within out_radius
   const int list = kListR0 + out_radius;
-  const int nitem = d.count(list, pl.nch);
-  int b_next = d.item(list, blockIdx.x);  // loaded beside the count (grid <= list length)
+  const ListHead head = list_head(d, list, pl.nch);
+  const int nitem = head.count;
+  int b_next = head.first;
   for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
     const long long b = b_next;
     if (it + (int)gridDim.x < nitem) b_next = d.item(list, it + gridDim.x);
@@ -1801,7 +1810,7 @@ __device__ __forceinline__ bool near_threshold(double r2, double th2) {
 // k0 + off + step, ... of its sweep.
 __device__ __forceinline__ void remove_part(const Cands& cd, long long c, const Grid& g,
                                             const Tables& tb, unsigned long long* acc,
-                                            const Dirty& d, int Kc, int off, int step) {
+                                            const DirtyIter& d, int Kc, int off, int step) {
   Sweep sw;
   sw.lo = cd.lo[c];
   sw.hi = cd.hi[c];
@@ -1841,8 +1850,18 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
     Cands cd, Grid g, Tables tb, const double* __restrict__ Sg, const float* __restrict__ inv_f,
     double th2, double rtol, int mode, unsigned char* __restrict__ resolved,
     unsigned long long* __restrict__ acc, RunState* rs, Dirty d, int Kc, int sg_radius) {
-  if (rs->final_pass || rtol_stop(rs, rtol)) return;
-  const long long nlive = (long long)rs->nlive;
+  // the loop state, read by one thread per CTA (every thread of the grid loading the same
+  // words would queue on one L2 line)
+  __shared__ long long snr_head[3];  // stop, iteration, live candidates
+  if (threadIdx.x == 0) {
+    snr_head[0] = (rs->final_pass || rtol_stop(rs, rtol)) ? 1 : 0;
+    snr_head[1] = rs->iter;
+    snr_head[2] = (long long)rs->nlive;
+  }
+  __syncthreads();
+  if (snr_head[0]) return;
+  const long long nlive = snr_head[2];
+  const DirtyIter di(d, (int)snr_head[1]);
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const float th2f = (float)th2;
@@ -1865,7 +1884,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
       if (kl > g.nb - 1) kl = g.nb - 1;
       if (kl >= 0) {
         long long c1 = kl / Kc;
-        for (long long cc = c0; cc <= c1 && !todo; ++cc) todo = d.any(cc, sg_radius);
+        for (long long cc = c0; cc <= c1 && !todo; ++cc) todo = di.any(cc, sg_radius);
       }
       wide = todo && nbin > kSnrLaneBins;
     }
@@ -1884,7 +1903,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
         cd.res[c] = 1;
         resolved[cd.src[c]] = 1;
         ++local_new;
-        remove_part(cd, c, g, tb, acc, d, Kc, 0, 1);
+        remove_part(cd, c, g, tb, acc, di, Kc, 0, 1);
       }
     }
     unsigned pending = __ballot_sync(0xFFFFFFFFu, wide);
@@ -1917,7 +1936,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
           resolved[cd.src[cw]] = 1;
           ++local_new;
         }
-        remove_part(cd, cw, g, tb, acc, d, Kc, lane, 32);
+        remove_part(cd, cw, g, tb, acc, di, Kc, lane, 32);
       }
     }
   }

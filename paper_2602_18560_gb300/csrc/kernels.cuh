@@ -130,6 +130,51 @@ struct Dirty {
   }
 };
 
+// The dirty sets of one iteration, the iteration fixed: the set read (cur) and the set
+// written for the next one (nxt); both null when nothing is tracked.
+struct DirtyIter {
+  const unsigned char* cur;
+  unsigned char* nxt;
+  int nch;
+  __device__ __forceinline__ DirtyIter(const Dirty& d, int iter) : nch(d.nch) {
+    cur = d.base ? d.base + (size_t)(iter & 1) * d.nch : nullptr;
+    nxt = d.base ? d.base + (size_t)((iter + 1) & 1) * d.nch : nullptr;
+  }
+  // any chunk of [c - radius, c + radius] (clipped to the chunks that exist)
+  __device__ __forceinline__ bool any(long long c, int radius) const {
+    if (!cur) return true;
+    long long a = c - radius, b = c + radius;
+    if (a < 0) a = 0;
+    if (b > nch - 1) b = nch - 1;
+    bool r = false;
+    for (long long i = a; i <= b; ++i) r |= cur[i] != 0;  // independent loads
+    return r;
+  }
+  __device__ __forceinline__ void mark_next(long long c) const {
+    if (nxt) nxt[c] = 1;
+  }
+};
+
+// A work list's length, the CTA's first item and the iteration, read by one thread and
+// shared with the CTA: when every thread of hundreds of CTAs loads the same words, the
+// requests queue on one L2 line and a late iteration's few working CTAs wait behind them.
+struct ListHead {
+  int count, first, iter;
+};
+__device__ __forceinline__ ListHead list_head(const Dirty& d, int which, int all) {
+  __shared__ ListHead sh;
+  if (threadIdx.x == 0) {
+    ListHead h;
+    h.count = d.count(which, all);
+    h.first = d.item(which, blockIdx.x);  // the grid is never longer than the list
+    h.iter = d.base ? d.rs->iter : 0;
+    sh = h;
+  }
+  __syncthreads();
+  const ListHead r = sh;
+  return r;
+}
+
 // Output epilogue of the kernel that writes S_gal.
 struct SgOut {
   double* out;           // S_gal (or the median of median-then-mean)
