@@ -80,11 +80,19 @@ __device__ __forceinline__ U128 dbl_to_u128_scaled(double x, int sh) {
   return r;
 }
 
+// x 2^k for 1 <= x <= 2^64: k added to the exponent field (exact, no FP64 instruction)
+// when the result is a normal number (-1022 <= k <= 959); otherwise ldexp.
+__device__ __forceinline__ double scale_pow2(double x, int k) {
+  if (k >= -1022 && k <= 959)
+    return __longlong_as_double(__double_as_longlong(x) + ((long long)k << 52));
+  return ldexp(x, k);
+}
+
 // Round-to-nearest double of v * 2^-sh.
 __device__ __forceinline__ double u128_to_dbl_scaled(U128 v, int sh) {
   if (v.hi == 0ull) {
     if (v.lo == 0ull) return 0.0;
-    return ldexp(__ull2double_rn(v.lo), -sh);
+    return scale_pow2(__ull2double_rn(v.lo), -sh);
   }
   int lz = __clzll((i64)v.hi);      // 0..63
   int shift = 64 - lz;              // bits to drop so the top 64 bits remain
@@ -93,7 +101,7 @@ __device__ __forceinline__ double u128_to_dbl_scaled(U128 v, int sh) {
   u64 low_mask = (lz == 0) ? ~0ull : ((1ull << (64 - lz)) - 1ull);
   u64 sticky = ((v.lo & low_mask) != 0ull) ? 1ull : 0ull;
   top |= sticky;
-  return ldexp(__ull2double_rn(top), shift - sh);
+  return scale_pow2(__ull2double_rn(top), shift - sh);
 }
 
 // A bin of the spectrum is three 64-bit words holding Q = w2 2^64 + w1 2^32 + w0 in units of

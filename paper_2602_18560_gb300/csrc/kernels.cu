@@ -1253,6 +1253,9 @@ void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned lo
 // a tile's latency is a few thousand cycles even when a single chunk has changed.
 
 __device__ __forceinline__ int wm_levels(int M) { return 32 - __clz(M - 1); }
+// Words of a wavelet level per warp that the build keeps in registers (M = 2048 with 16 warps
+// takes 4).
+constexpr int kWmRegWords = 8;
 
 // Ones of a level's bitset before position i (the word holds its bits in the low half and
 // the ones of all earlier words in the high half).
@@ -1343,10 +1346,62 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   const int w0 = warp * wpw, w1 = min(w0 + wpw, nwm);
   uint16_t* cur = seq0;
   uint16_t* nxt = seq1;
+  // With at most kWmRegWords words per warp, a level loads the warp's elements once, all of
+  // them before the first ballot, and its ballots serve both the count and the partition.
+  const bool in_regs = w1 - w0 <= kWmRegWords;
   for (int l = 0; l < LV; ++l) {
     const int sh = LV - 1 - l;
     u64* rkl = rk + (size_t)l * ws;
     int mine = 0;
+    if (in_regs) {
+      uint32_t xv[kWmRegWords];
+      unsigned bal[kWmRegWords];
+#pragma unroll
+      for (int q = 0; q < kWmRegWords; ++q)
+        xv[q] = (w0 + q < w1) ? cur[(w0 + q) * 32 + lane] : 0u;
+#pragma unroll
+      for (int q = 0; q < kWmRegWords; ++q) {
+        bal[q] = 0u;
+        if (w0 + q < w1) {
+          bal[q] = __ballot_sync(0xFFFFFFFFu, (xv[q] >> sh) & 1u);
+          mine += __popc(bal[q]);
+        }
+      }
+      if (lane == 0) warp_ones[warp] = mine;
+      __syncthreads();
+      const int c = lane < nwarp ? warp_ones[lane] : 0;
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      int run = __shfl_sync(0xFFFFFFFFu, incl - c, warp);
+      const int Z = M - total;
+      const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+      for (int q = 0; q < kWmRegWords; ++q) {
+        const int k = w0 + q;
+        if (k < w1) {
+          if (lane == 0) rkl[k] = ((u64)run << 32) | bal[q];
+          if (l + 1 < LV) {
+            const int ob = run + __popc(bal[q] & below);
+            nxt[((xv[q] >> sh) & 1u) ? Z + ob : k * 32 + lane - ob] = (uint16_t)xv[q];
+          }
+          run += __popc(bal[q]);
+        }
+      }
+      if (tid == 0) {
+        rkl[nwm] = (u64)total << 32;
+        zeros[l] = Z;
+      }
+      __syncthreads();
+      uint16_t* t = cur;
+      cur = nxt;
+      nxt = t;
+      continue;
+    }
     for (int k = w0; k < w1; ++k)
       mine += __popc(__ballot_sync(0xFFFFFFFFu, (cur[k * 32 + lane] >> sh) & 1));
     if (lane == 0) warp_ones[warp] = mine;
@@ -1662,6 +1717,7 @@ __global__ void k_window_mean(const double* __restrict__ x, long long n, SmoothP
                               SgOut o, Dirty d, int out_radius) {
   double relmax = 0.0;
   const int h = pl.W / 2;
+  const double inv_w = 1.0 / (double)pl.W;
   // output chunks with a dirty chunk within out_radius
   const int list = kListR0 + out_radius;
   const ListHead head = list_head(d, list, pl.nch);
@@ -1670,11 +1726,15 @@ __global__ void k_window_mean(const double* __restrict__ x, long long n, SmoothP
   for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
     const long long b = b_next;
     if (it + (int)gridDim.x < nitem) b_next = d.item(list, it + gridDim.x);
-    const long long jend = (b + 1) * pl.Kc < n ? (b + 1) * pl.Kc : n;
-    for (long long j = b * pl.Kc + threadIdx.x; j < jend; j += blockDim.x) {
+    const long long b0 = b * pl.Kc;
+    const long long jend = b0 + pl.Kc < n ? b0 + pl.Kc : n;
+    for (long long j = b0 + threadIdx.x; j < jend; j += blockDim.x) {
       long long s = j - h > 0 ? j - h : 0;
       long long e = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
-      long long cs = s / pl.Kc, ce = e / pl.Kc;
+      // s and e lie within one chunk of chunk b (h < W <= Kc): no 64-bit division
+      const long long ds = s - b0, de = e - b0;
+      const long long cs = b + (ds < 0 ? -1 : (ds >= pl.Kc ? 1 : 0));
+      const long long ce = b + (de < 0 ? -1 : (de >= pl.Kc ? 1 : 0));
       long long cnt = e - s + 1;
       double sum;
       if (cs == ce) {
@@ -1685,7 +1745,7 @@ __global__ void k_window_mean(const double* __restrict__ x, long long n, SmoothP
         double s2 = part_sum(x, ce * pl.Kc, ce * pl.Kc, e, pre_lo, pre_hi, sig[ce], uflow[ce]);
         sum = __dadd_rn(s1, s2);
       }
-      double v = (cnt == pl.W) ? __dmul_rn(sum, 1.0 / (double)pl.W) : __ddiv_rn(sum, (double)cnt);
+      double v = (cnt == pl.W) ? __dmul_rn(sum, inv_w) : __ddiv_rn(sum, (double)cnt);
       double rel = sg_store(o, j, v);
       relmax = rel > relmax ? rel : relmax;
     }
