@@ -373,9 +373,8 @@ constexpr size_t kPrepassSmem = (size_t)kPreStages * kPreTile * 3 * sizeof(doubl
 // launch, long after every other warp is done).
 constexpr long long kSlowLaneBins = 4;
 
-// Source s of a generated catalog (kept out of line: the common path of the pass stays
-// small when the catalog is read from memory).
-__device__ __noinline__ double3 gen_source_at(const CatalogRef* __restrict__ cat, long long s) {
+// Source s of a generated catalog.
+__device__ __forceinline__ double3 gen_source_at(const CatalogRef* __restrict__ cat, long long s) {
   const GenParams g = cat->gen;
   double3 r;
   gen_source(g, s, &r.x, &r.y, &r.z);
@@ -428,6 +427,7 @@ __device__ __forceinline__ bool single_bin(double fs, double fds, const Grid& g,
 
 // The FP64 path of up to 32 queued sources q[0 .. cnt) of one warp (lane i takes entry i;
 // sweeps longer than kSlowLaneBins by the whole warp).
+template <bool kGen>
 __device__ __forceinline__ void prepass_drain_warp(const CatalogRef* __restrict__ cat,
                                                    const double* __restrict__ A,
                                                    const double* __restrict__ f,
@@ -442,7 +442,7 @@ __device__ __forceinline__ void prepass_drain_warp(const CatalogRef* __restrict_
   double a = 0.0, fs = 0.0, fds = 0.0, r = 0.0;
   bool wide = false;
   if (valid) {
-    if (cat->staged == kCatGenerated) {
+    if (kGen) {
       const double3 gsrc = gen_source_at(cat, s);
       a = gsrc.x;
       fs = gsrc.y;
@@ -467,6 +467,61 @@ __device__ __forceinline__ void prepass_drain_warp(const CatalogRef* __restrict_
     const double rw = prepass_slow_warp(sw_a, sw_f, sw_fd, g, tb, acc, &rs->err);
     prepass_decide(rw, tk_bits, tl_bits, lane == 0, sw_s, sw_a, sw_f, sw_fd, g, cd, rs,
                    nkappa);
+  }
+}
+
+// One source of the catalog pass (s < N; every lane of the warp calls it together): the
+// common case deposited here, a source the FP64 path must take appended to the warp's queue
+// q (qn entries, the same in every lane), which is drained 32 at a time.
+template <bool kGen>
+__device__ __forceinline__ void prepass_source(
+    long long s, long long N, double a, double fs, double fds, const CatalogRef* __restrict__ cat,
+    const double* __restrict__ A, const double* __restrict__ f, const double* __restrict__ fdot,
+    const Grid& g, const Tables& tb, u64 tk_bits, u64 tl_bits, unsigned long long* __restrict__ acc,
+    const AccReplicas& rep, Cands& cd, RunState* rs, long long* q, int& qn,
+    unsigned long long& nkappa) {
+  const int lane = threadIdx.x & 31;
+  bool valid = false, slow = false;
+  double r = 0.0;
+  if (s < N) {
+    // finite inputs, and A^2 finite (|A| < 2^512): else the source is refused below
+    const bool fin = finite3(a, fs, fds) && (((u64)__double_as_longlong(a) >> 52) & 0x7FF) < 1535;
+    long long k0 = 0;
+    const bool single = fin && single_bin(fs, fds, g, &k0);
+    if (single) {
+      valid = true;
+      const long long j = k0 - g.k_lo;
+      if (j >= 0 && j < g.nb) {
+        u64 c0, c1, c2, qb;
+        if (q_single(a, tb.gq[j], &c0, &c1, &c2, &qb)) {
+          if (j < rep.nbins)
+            add_parts_rep(rep, acc, j, (int)(s & (kAccReplicas - 1)), c0, c1, c2);
+          else
+            add_parts(acc, j, c0, c1, c2);
+          r = __longlong_as_double((long long)qb);
+        } else {
+          atomicOr(&rs->err, ERR_RANGE);
+        }
+      }
+    } else if (fin) {
+      slow = true;
+    } else {
+      atomicOr(&rs->err, ERR_INPUT);  // the source is skipped; the run reports it
+    }
+  }
+  // append the warp's slow sources to its queue
+  const unsigned sm = __ballot_sync(0xFFFFFFFFu, slow);
+  if (slow) q[qn + __popc(sm & ((1u << lane) - 1u))] = s;
+  qn += __popc(sm);
+  prepass_decide(r, tk_bits, tl_bits, valid, s, a, fs, fds, g, cd, rs, nkappa);
+  if (qn >= 32) {
+    __syncwarp();
+    prepass_drain_warp<kGen>(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, q, 32,
+                             nkappa);
+    __syncwarp();
+    if (lane < qn - 32) q[lane] = q[32 + lane];
+    qn -= 32;
+    __syncwarp();
   }
 }
 
@@ -527,12 +582,12 @@ __global__ void __launch_bounds__(kPrepassThreads, 3) k_prepass(
   const double* __restrict__ fdot = scat.fdot;
   const long long N = scat.n;
   const bool use_tma = scat.staged == kCatDevice;
-  const bool generated = scat.staged == kCatGenerated;
+  if (scat.staged == kCatGenerated) return;  // k_prepass_gen's catalog
   const int lane = tid & 31;
   const int warp = tid >> 5;
   const long long ntiles = (N + kPreTile - 1) / kPreTile;
   // full tiles of device memory come through TMA; the ragged one, and every tile of a catalog
-  // in host memory or generated, through plain loads (or the generator)
+  // in host memory, through plain loads
   const long long nfull = use_tma ? N / kPreTile : 0;
 
   if (warp == kPreConsumers) {
@@ -565,7 +620,7 @@ __global__ void __launch_bounds__(kPrepassThreads, 3) k_prepass(
         bulk_g2s(d + kPreTile, f + off, kPreTile * sizeof(double), &full[stage]);
         bulk_g2s(d + 2 * kPreTile, fdot + off, kPreTile * sizeof(double), &full[stage]);
       } else if (t >= nfull) {
-        mbar_arrive(&full[stage]);  // a ragged, mapped or generated tile, or the end
+        mbar_arrive(&full[stage]);  // a ragged or mapped tile, or the end
       }
       // (with the test hook a full tile gets no copy and no arrival: its waits run out)
       if (t >= ntiles) break;
@@ -617,73 +672,70 @@ __global__ void __launch_bounds__(kPrepassThreads, 3) k_prepass(
         fv[k] = sF[idx];
         dv[k] = sD[idx];
       } else if (s < N) {
-        if (generated) {
-          const double3 gsrc = gen_source_at(cat, s);
-          av[k] = gsrc.x;
-          fv[k] = gsrc.y;
-          dv[k] = gsrc.z;
-        } else {
-          av[k] = A[s];
-          fv[k] = f[s];
-          dv[k] = fdot[s];
-        }
+        av[k] = A[s];
+        fv[k] = f[s];
+        dv[k] = fdot[s];
       }
     }
     // the stage may be refilled once every warp has its values in registers
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[stage]);
 #pragma unroll
-    for (int k = 0; k < kPrePer; ++k) {
-      const long long s = t * kPreTile + base + 32 * k;
-      bool valid = false, slow = false;
-      double r = 0.0;
-      const double a = av[k], fs = fv[k], fds = dv[k];
-      if (s < N) {
-        // finite inputs, and A^2 finite (|A| < 2^512): else the source is refused below
-        const bool fin = finite3(a, fs, fds) &&
-                         (((u64)__double_as_longlong(a) >> 52) & 0x7FF) < 1535;
-        long long k0 = 0;
-        const bool single = fin && single_bin(fs, fds, g, &k0);
-        if (single) {
-          valid = true;
-          const long long j = k0 - g.k_lo;
-          if (j >= 0 && j < g.nb) {
-            u64 c0, c1, c2, qb;
-            if (q_single(a, tb.gq[j], &c0, &c1, &c2, &qb)) {
-              if (j < rep.nbins)
-                add_parts_rep(rep, acc, j, (int)(s & (kAccReplicas - 1)), c0, c1, c2);
-              else
-                add_parts(acc, j, c0, c1, c2);
-              r = __longlong_as_double((long long)qb);
-            } else {
-              atomicOr(&rs->err, ERR_RANGE);
-            }
-          }
-        } else if (fin) {
-          slow = true;
-        } else {
-          atomicOr(&rs->err, ERR_INPUT);  // the source is skipped; the run reports it
-        }
-      }
-      // append the warp's slow sources to its queue
-      const unsigned sm = __ballot_sync(0xFFFFFFFFu, slow);
-      if (slow) myq[qn + __popc(sm & ((1u << lane) - 1u))] = s;
-      qn += __popc(sm);
-      prepass_decide(r, tk_bits, tl_bits, valid, s, a, fs, fds, g, cd, rs, nkappa);
-      if (qn >= 32) {
-        __syncwarp();
-        prepass_drain_warp(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, myq, 32,
-                           nkappa);
-        __syncwarp();
-        if (lane < qn - 32) myq[lane] = myq[32 + lane];
-        qn -= 32;
-        __syncwarp();
-      }
+    for (int k = 0; k < kPrePer; ++k)
+      prepass_source<false>(t * kPreTile + base + 32 * k, N, av[k], fv[k], dv[k], cat, A, f,
+                            fdot, g, tb, tk_bits, tl_bits, acc, rep, cd, rs, myq, qn, nkappa);
+  }
+  __syncwarp();
+  if (qn > 0)
+    prepass_drain_warp<false>(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, myq, qn,
+                              nkappa);
+  for (int o = 16; o > 0; o >>= 1) nkappa += __shfl_xor_sync(0xFFFFFFFFu, nkappa, o);
+  if (lane == 0 && nkappa) atomicAdd(&rs->ncand, nkappa);
+}
+
+// The catalog pass over a generated catalog: every source computed from (seed, index) where
+// the pass over a stored catalog loads it, then the same per-source step.  Generation is
+// ~300 FP32 and integer instructions per source, so there is nothing to stage: each warp takes
+// runs of 32 kGenPer sources from the tile counter.  The other pass leaves a generated catalog
+// to this one, and this one leaves every other catalog to it.
+constexpr int kGenThreads = 256;
+constexpr int kGenPer = 8;  // sources per lane per run
+
+__global__ void __launch_bounds__(kGenThreads, 4) k_prepass_gen(
+    const CatalogRef* cat, Grid g, Tables tb, double thr_kappa, double thr_live,
+    unsigned long long* __restrict__ acc, AccReplicas rep, Cands cd, RunState* rs) {
+  __shared__ CatalogRef scat;
+  __shared__ long long slow_q[kGenThreads / 32][kSlowWarpCap];
+  if (threadIdx.x == 0) scat = *cat;
+  __syncthreads();
+  if (scat.staged != kCatGenerated) return;
+  cat = &scat;
+  const long long N = scat.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u64 tk_bits = (u64)__double_as_longlong(thr_kappa);
+  const u64 tl_bits = (u64)__double_as_longlong(thr_live);
+  unsigned long long nkappa = 0;
+  long long* myq = slow_q[warp];
+  int qn = 0;
+  constexpr long long kRun = 32LL * kGenPer;
+  for (;;) {
+    unsigned long long r0 = 0;
+    if (lane == 0) r0 = atomicAdd(&rs->next_tile, 1ull);
+    const long long base = (long long)__shfl_sync(0xFFFFFFFFu, r0, 0) * kRun;
+    if (base >= N) break;
+#pragma unroll 1
+    for (int k = 0; k < kGenPer; ++k) {
+      const long long s = base + 32 * k + lane;
+      double3 src = make_double3(0.0, 0.0, 0.0);
+      if (s < N) src = gen_source_at(cat, s);
+      prepass_source<true>(s, N, src.x, src.y, src.z, cat, nullptr, nullptr, nullptr, g, tb,
+                           tk_bits, tl_bits, acc, rep, cd, rs, myq, qn, nkappa);
     }
   }
   __syncwarp();
   if (qn > 0)
-    prepass_drain_warp(cat, A, f, fdot, g, tb, tk_bits, tl_bits, acc, cd, rs, myq, qn, nkappa);
+    prepass_drain_warp<true>(cat, nullptr, nullptr, nullptr, g, tb, tk_bits, tl_bits, acc, cd,
+                             rs, myq, qn, nkappa);
   for (int o = 16; o > 0; o >>= 1) nkappa += __shfl_xor_sync(0xFFFFFFFFu, nkappa, o);
   if (lane == 0 && nkappa) atomicAdd(&rs->ncand, nkappa);
 }
@@ -696,6 +748,12 @@ void launch_prepass(const CatalogRef* cat, long long cap, const Grid& g, const T
   int bl = (int)(tiles < lim ? (tiles < 1 ? 1 : tiles) : lim);
   k_prepass<<<bl, kPrepassThreads, kPrepassSmem, st>>>(cat, g, tb, thr_kappa, thr_live, acc,
                                                        rep, cd, rs, test_flags);
+  // the generated-catalog pass: resident CTAs, at most one per run of sources
+  const long long runs = (cap + 32LL * kGenPer - 1) / (32LL * kGenPer);
+  const long long glim = (long long)nsm * 4 * (kGenThreads / 32);
+  const long long gwarps = runs < glim ? (runs < 1 ? 1 : runs) : glim;
+  k_prepass_gen<<<(unsigned)((gwarps + kGenThreads / 32 - 1) / (kGenThreads / 32)), kGenThreads, 0,
+                  st>>>(cat, g, tb, thr_kappa, thr_live, acc, rep, cd, rs);
   if (rep.nbins > 0)
     k_fold_replicas<<<(unsigned)((rep.nbins + 255) / 256), 256, 0, st>>>(acc, rep);
 }
