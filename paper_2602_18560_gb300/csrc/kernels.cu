@@ -1311,9 +1311,120 @@ void launch_chunk_sort(SpecIn in, long long n, const SmoothPlan& pl, unsigned lo
 // a tile's latency is a few thousand cycles even when a single chunk has changed.
 
 __device__ __forceinline__ int wm_levels(int M) { return 32 - __clz(M - 1); }
-// Words of a wavelet level per warp that the build keeps in registers (M = 2048 with 16 warps
-// takes 4).
-constexpr int kWmRegWords = 8;
+// Ones of the warps before this one (run) and of all of them (total), from the per-warp
+// counts c (lane i holds warp i's, zero beyond the warps).
+__device__ __forceinline__ void wm_warp_offsets(int c, int warp, int* run, int* total) {
+  const int lane = threadIdx.x & 31;
+  *total = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)c);
+  *run = (int)__reduce_add_sync(0xFFFFFFFFu, lane < warp ? (unsigned)c : 0u);
+}
+
+__device__ __forceinline__ unsigned lds_u16(uint32_t addr) {
+  unsigned short v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts_u16(uint32_t addr, unsigned v) {
+  asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"((unsigned short)v) : "memory");
+}
+
+// Wavelet matrix of the permutation seq0 (M elements) when every warp owns exactly WPW words
+// of a level: each level loads the warp's elements once, all of them before the first ballot,
+// and the ballots serve both the count and the stable partition into the other buffer.
+// Level l stores its words in rk[l ws ..] (bits in the low half, ones of the earlier words
+// in the high half) and its number of zeros in zeros[l].  seq0 and seq1 are both
+// overwritten.
+template <int WPW>
+__device__ __forceinline__ void wm_build_fixed(uint16_t* seq0, uint16_t* seq1, u64* rk, int ws,
+                                               int* zeros, int* warp_ones, int M, int LV,
+                                               int nwm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int w0 = warp * WPW;
+  const unsigned below = (1u << lane) - 1u;
+  uint32_t cur = (uint32_t)__cvta_generic_to_shared(seq0);
+  uint32_t nxt = (uint32_t)__cvta_generic_to_shared(seq1);
+  for (int l = 0; l < LV; ++l) {
+    const int sh = LV - 1 - l;
+    u64* rkl = rk + (size_t)l * ws;
+    uint32_t xv[WPW];
+    unsigned bal[WPW];
+    int mine = 0;
+#pragma unroll
+    for (int q = 0; q < WPW; ++q) xv[q] = lds_u16(cur + 2u * (uint32_t)((w0 + q) * 32 + lane));
+#pragma unroll
+    for (int q = 0; q < WPW; ++q) {
+      bal[q] = __ballot_sync(0xFFFFFFFFu, (xv[q] >> sh) & 1u);
+      mine += __popc(bal[q]);
+    }
+    if (lane == 0) warp_ones[warp] = mine;
+    __syncthreads();
+    int run, total;
+    wm_warp_offsets(lane < nwarp ? warp_ones[lane] : 0, warp, &run, &total);
+    const int Z = M - total;
+#pragma unroll
+    for (int q = 0; q < WPW; ++q) {
+      const int k = w0 + q;
+      if (lane == 0) rkl[k] = ((u64)run << 32) | bal[q];
+      if (l + 1 < LV) {
+        const int ob = run + __popc(bal[q] & below);
+        const int dst = ((xv[q] >> sh) & 1u) ? Z + ob : k * 32 + lane - ob;
+        sts_u16(nxt + 2u * (uint32_t)dst, xv[q]);
+      }
+      run += __popc(bal[q]);
+    }
+    if (tid == 0) {
+      rkl[nwm] = (u64)total << 32;
+      zeros[l] = Z;
+    }
+    __syncthreads();
+    const uint32_t t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+}
+
+// The same for any number of words per warp (the last warps may own fewer, or none).
+__device__ __forceinline__ void wm_build_any(uint16_t* seq0, uint16_t* seq1, u64* rk, int ws,
+                                             int* zeros, int* warp_ones, int M, int LV,
+                                             int nwm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int wpw = (nwm + nwarp - 1) / nwarp;
+  const int w0 = warp * wpw, w1 = min(w0 + wpw, nwm);
+  uint16_t* cur = seq0;
+  uint16_t* nxt = seq1;
+  for (int l = 0; l < LV; ++l) {
+    const int sh = LV - 1 - l;
+    u64* rkl = rk + (size_t)l * ws;
+    int mine = 0;
+    for (int k = w0; k < w1; ++k)
+      mine += __popc(__ballot_sync(0xFFFFFFFFu, (cur[k * 32 + lane] >> sh) & 1));
+    if (lane == 0) warp_ones[warp] = mine;
+    __syncthreads();
+    int run, total;
+    wm_warp_offsets(lane < nwarp ? warp_ones[lane] : 0, warp, &run, &total);
+    const int Z = M - total;
+    for (int k = w0; k < w1; ++k) {
+      const int i = k * 32 + lane;
+      const int x = cur[i];
+      const int b = (x >> sh) & 1;
+      const unsigned bits = __ballot_sync(0xFFFFFFFFu, b);
+      if (lane == 0) rkl[k] = ((u64)run << 32) | bits;
+      if (l + 1 < LV) {
+        const int ob = run + __popc(bits & ((1u << lane) - 1u));
+        nxt[b ? Z + ob : i - ob] = (uint16_t)x;
+      }
+      run += __popc(bits);
+    }
+    if (tid == 0) {
+      rkl[nwm] = (u64)total << 32;
+      zeros[l] = Z;
+    }
+    __syncthreads();
+    uint16_t* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+}
 
 // Ones of a level's bitset before position i (the word holds its bits in the low half and
 // the ones of all earlier words in the high half).
@@ -1399,102 +1510,20 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   // 2. wavelet matrix.  Warp w owns the words [w wpw, (w + 1) wpw) of every level (M is a
   // multiple of 64: whole words).  A level takes two barriers: one after the warps have
   // counted their ones, one after the stable partition.
-  const int nwarp = T >> 5;
-  const int wpw = (nwm + nwarp - 1) / nwarp;
-  const int w0 = warp * wpw, w1 = min(w0 + wpw, nwm);
-  uint16_t* cur = seq0;
-  uint16_t* nxt = seq1;
-  // With at most kWmRegWords words per warp, a level loads the warp's elements once, all of
-  // them before the first ballot, and its ballots serve both the count and the partition.
-  const bool in_regs = w1 - w0 <= kWmRegWords;
-  for (int l = 0; l < LV; ++l) {
-    const int sh = LV - 1 - l;
-    u64* rkl = rk + (size_t)l * ws;
-    int mine = 0;
-    if (in_regs) {
-      uint32_t xv[kWmRegWords];
-      unsigned bal[kWmRegWords];
-#pragma unroll
-      for (int q = 0; q < kWmRegWords; ++q)
-        xv[q] = (w0 + q < w1) ? cur[(w0 + q) * 32 + lane] : 0u;
-#pragma unroll
-      for (int q = 0; q < kWmRegWords; ++q) {
-        bal[q] = 0u;
-        if (w0 + q < w1) {
-          bal[q] = __ballot_sync(0xFFFFFFFFu, (xv[q] >> sh) & 1u);
-          mine += __popc(bal[q]);
-        }
-      }
-      if (lane == 0) warp_ones[warp] = mine;
-      __syncthreads();
-      const int c = lane < nwarp ? warp_ones[lane] : 0;
-      int incl = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      int run = __shfl_sync(0xFFFFFFFFu, incl - c, warp);
-      const int Z = M - total;
-      const unsigned below = (1u << lane) - 1u;
-#pragma unroll
-      for (int q = 0; q < kWmRegWords; ++q) {
-        const int k = w0 + q;
-        if (k < w1) {
-          if (lane == 0) rkl[k] = ((u64)run << 32) | bal[q];
-          if (l + 1 < LV) {
-            const int ob = run + __popc(bal[q] & below);
-            nxt[((xv[q] >> sh) & 1u) ? Z + ob : k * 32 + lane - ob] = (uint16_t)xv[q];
-          }
-          run += __popc(bal[q]);
-        }
-      }
-      if (tid == 0) {
-        rkl[nwm] = (u64)total << 32;
-        zeros[l] = Z;
-      }
-      __syncthreads();
-      uint16_t* t = cur;
-      cur = nxt;
-      nxt = t;
-      continue;
-    }
-    for (int k = w0; k < w1; ++k)
-      mine += __popc(__ballot_sync(0xFFFFFFFFu, (cur[k * 32 + lane] >> sh) & 1));
-    if (lane == 0) warp_ones[warp] = mine;
-    __syncthreads();
-    // ones of the warps before this one, and of all
-    const int c = lane < nwarp ? warp_ones[lane] : 0;
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    int run = __shfl_sync(0xFFFFFFFFu, incl - c, warp);
-    const int Z = M - total;
-    for (int k = w0; k < w1; ++k) {
-      const int i = k * 32 + lane;
-      const int x = cur[i];
-      const int b = (x >> sh) & 1;
-      const unsigned bits = __ballot_sync(0xFFFFFFFFu, b);
-      if (lane == 0) rkl[k] = ((u64)run << 32) | bits;
-      if (l + 1 < LV) {
-        const int ob = run + __popc(bits & ((1u << lane) - 1u));
-        nxt[b ? Z + ob : i - ob] = (uint16_t)x;
-      }
-      run += __popc(bits);
-    }
-    if (tid == 0) {
-      rkl[nwm] = (u64)total << 32;
-      zeros[l] = Z;
-    }
-    __syncthreads();
-    uint16_t* t = cur;
-    cur = nxt;
-    nxt = t;
+  {
+    const int nwarp = T >> 5;
+    const int wpw = (nwm + nwarp - 1) / nwarp;
+    const bool full = wpw * nwarp == nwm;
+    if (full && wpw == 4)
+      wm_build_fixed<4>(seq0, seq1, rk, ws, zeros, warp_ones, M, LV, nwm);
+    else if (full && wpw == 2)
+      wm_build_fixed<2>(seq0, seq1, rk, ws, zeros, warp_ones, M, LV, nwm);
+    else if (full && wpw == 8)
+      wm_build_fixed<8>(seq0, seq1, rk, ws, zeros, warp_ones, M, LV, nwm);
+    else if (full && wpw == 1)
+      wm_build_fixed<1>(seq0, seq1, rk, ws, zeros, warp_ones, M, LV, nwm);
+    else
+      wm_build_any(seq0, seq1, rk, ws, zeros, warp_ones, M, LV, nwm);
   }
 
   // 3. selections
