@@ -1439,7 +1439,7 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
                                               const uint16_t* __restrict__ srank, long long n,
                                               const SmoothPlan& pl, const SgOut& o, long long u,
                                               unsigned char* sm_raw, int* zeros) {
-  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = blockDim.x, tid = threadIdx.x;
   const int Kc = pl.Kc, M = 2 * Kc, LV = wm_levels(M);
   const int nwm = M >> 5, ws = nwm + 1;  // words per level (one zero word of padding)
   const int h = pl.W / 2;
@@ -2022,8 +2022,12 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
     bool todo = false, wide = false;
     const long long c = grp + (long long)lane * ngroups;
     int4 pk = make_int4(0, 0, 0, 0);
-    if (c < nlive && !cd.res[c]) {
+    unsigned char done = 1;
+    if (c < nlive) {  // both loads at once
+      done = cd.res[c];
       pk = cd.pk[c];
+    }
+    if (!done) {
       const int ka = pk.x;
       const int nbin = pk.y;
       long long c0 = ka < 0 ? 0 : ka / Kc;
@@ -2222,6 +2226,21 @@ __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist
                           int nch, int* lists, int* counts) {
   // every thread reads the count before thread 0 advances it (after the barriers below)
   const int it0 = rs->iter;
+  // thread 0 loads the rest of the loop state now, so that its latency overlaps the lists
+  int final_pass = 0;
+  unsigned err = 0u;
+  unsigned long long nn = 0ull, nres = 0ull;
+  bool rstop = false;
+  unsigned long long work[kNumLists] = {};
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < kNumLists; ++i) work[i] = rs->work[i];
+    final_pass = rs->final_pass;
+    err = rs->err;
+    nn = rs->count_new;
+    nres = rs->nres;
+    rstop = rtol_stop(rs, rtol);
+  }
   if (dirty) {
     // clear the set this iteration read; the removals of this iteration marked the other
     // one, which the next iteration reads through its work lists
@@ -2232,15 +2251,13 @@ __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist
   __syncthreads();
   if (threadIdx.x != 0) return;
   unsigned go = 1u;
-  if (rs->final_pass || (rs->err & ERR_TIMEOUT)) {
+  if (final_pass || (err & ERR_TIMEOUT)) {
     go = 0u;  // the last pass is done, or the catalog pass gave up
   } else {
-    bool rstop = rtol_stop(rs, rtol);
     int it = it0 + 1;
     rs->iter = it;
-    unsigned long long nn = rs->count_new;
     if (new_hist && it <= max_iter) new_hist[it - 1] = (int)nn;
-    rs->nres += nn;
+    rs->nres = nres + nn;
     if (rstop || nn == 0ull) {
       rs->converged = 1;
       go = 0u;
@@ -2253,7 +2270,7 @@ __global__ void k_control(RunState* rs, int max_iter, double rtol, int* new_hist
   rs->relchg_bits = 0ull;
   if (!go) rs->stopped = 1;
   if (go && dirty)  // the lists just built go to the next iteration's kernels
-    for (int i = 0; i < kNumLists; ++i) rs->work[i] += (unsigned long long)counts[i];
+    for (int i = 0; i < kNumLists; ++i) rs->work[i] = work[i] + (unsigned long long)counts[i];
   if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, go);
 }
 
