@@ -967,7 +967,8 @@ __device__ __forceinline__ bool key_pos_less(K ka, int pa, K kb, int pb) {
 }
 
 template <int E, typename K>
-__device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __restrict__ skey_c,
+__device__ bool resort_few_changes(const K (&knew)[E], const K (&kold)[E], const int (&rold)[E],
+                                   int len, int kpad, K* __restrict__ skey_c,
                                    uint16_t* __restrict__ srank_c, unsigned char* raw) {
   K* old_k = (K*)raw;                                // [kpad] old keys, in old sorted order
   K* ch_k = old_k + kpad;                            // [kResortMax] changed: new keys
@@ -987,12 +988,14 @@ __device__ bool resort_few_changes(const K (&knew)[E], int len, int kpad, K* __r
     n_changed = 0;
     bad_state = 0;
   }
-  for (int i = tid; i < len; i += T) old_k[i] = skey_c[i];
+  // (the caller loaded this thread's old keys kold and sorted indices rold, of indices and
+  // positions tid E + a, beside the new values)
   int r[E];
 #pragma unroll
   for (int a = 0; a < E; ++a) {
     const int p = tid * E + a;
-    r[a] = p < len ? (int)srank_c[p] : 0;
+    if (p < len) old_k[p] = kold[a];
+    r[a] = p < len ? rold[a] : 0;
     if (r[a] >= len) {
       bad_state = 1;
       r[a] = 0;
@@ -1132,8 +1135,15 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
     if (item + (int)gridDim.x < nitem) b_next = d.item(kListR0, item + gridDim.x);
     const long long base = (long long)b * pl.Kc;
     const int len = (int)((n - base) < pl.Kc ? (n - base) : pl.Kc);
-    K k[E];
-    int x[E];
+    K k[E], kold[E];
+    int x[E], rold[E];
+    // the previous sorted state, loaded beside the new values
+#pragma unroll
+    for (int a = 0; a < E; ++a) {
+      const int i = tid * E + a;
+      kold[a] = (resort && i < len) ? skey[base + i] : (K)0;
+      rold[a] = (resort && i < len) ? (int)srank[base + i] : 0;
+    }
 #pragma unroll
     for (int a = 0; a < E; ++a) {
       const int i = tid * E + a;
@@ -1142,7 +1152,8 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
       k[a] = kv;
       x[a] = i;
     }
-    if (resort && resort_few_changes<E, K>(k, len, kpad, skey + base, srank + base, sort_raw)) {
+    if (resort &&
+        resort_few_changes<E, K>(k, kold, rold, len, kpad, skey + base, srank + base, sort_raw)) {
       __syncthreads();  // before the next chunk overwrites shared memory
       continue;
     }
