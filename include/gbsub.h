@@ -295,10 +295,12 @@ int sub_profile(sub_ctx* ctx, float ms[SUB_K_COUNT], int32_t launches[SUB_K_COUN
  * measuring the FP32 screen that SUB_FP64 decides on first:
  *   src[i]         : the candidate's index in the catalog
  *   rho2_screen[i] : rho^2 in FP32 as the screen evaluates it (through 1 / (1 + S_gal/S_instr)
- *                    of the last estimate, in FP32)
+ *                    of the last estimate, in FP32), summed bin by bin on one thread
  *   rho2_exact[i]  : rho^2 in FP64, summed in the oracle's order (the value SUB_FP64 decides
- *                    on when the screen cannot)
- *   nbins[i]       : bins of the band the screen summed (its error bound grows with them)
+ *                    on when the screen cannot; for a sweep of more than 4 bins the run sums
+ *                    it across a warp, which differs by rounding only)
+ *   nbins[i]       : bins of the band the screen summed (the error bound of this one-thread
+ *                    sum grows with them)
  * All four are host arrays of cap entries; *n_out (may be null) receives the count.  The
  * call allocates and frees a temporary device buffer of 24 bytes per candidate and
  * synchronises.  Errors: SUB_EINVAL (cap below the count, null output), SUB_ESTATE (no run

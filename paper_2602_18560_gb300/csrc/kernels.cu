@@ -1866,16 +1866,49 @@ void launch_window_mean(const double* x, long long n, const SmoothPlan& pl,
 // ============================================================================ SNR + resolve
 // rho^2 = 4 (T/5) A^2 sum_k w_k R_k / (S_k + S_gal,k) = sum_k rho0_k / (1 + S_gal,k / S_k).
 // The screen evaluates it in FP32 as sum_k a2f w_k Gf_k inv_f_k; its relative error is
-// below 2.2e-6 + 2e-7 per bin (FP32 roundings of the inputs, the ratio, the reciprocal,
-// the products and the sum of positive terms), so outside a margin of 1e-5 + 4e-7 per
-// bin around rho_th^2 the FP64 decision is known.  Inside it, and always when the
-// caller asks for the strict path, rho^2 is recomputed in FP64 exactly as the oracle
-// does.  In the mixed-precision mode the FP32 value decides alone.
+// below 2.2e-6 (FP32 roundings of the inputs, the ratio, the reciprocal and the products of
+// each term) + 2e-7 per rounding of the sum that a term passes through: per bin for a sum
+// on one lane, and for a sweep summed by a warp the longest lane's count plus the five
+// levels of the butterfly (a sum of positive terms loses at most one rounding per step of
+// its longest chain).  Outside twice that, 1e-5 + 4e-7 per step, around rho_th^2 the FP64
+// decision is known.  Inside it, and always when the caller asks for the strict path,
+// rho^2 is recomputed in FP64 with the oracle's terms: on one lane in the oracle's order
+// for a sweep of a few bins, by the warp for a longer one.  In the mixed-precision mode the
+// FP32 value decides alone.
 
 __device__ __forceinline__ bool rtol_stop(const RunState* rs, double rtol) {
   if (!(rtol > 0.0) || rs->iter < 1) return false;
   double r = __longlong_as_double((i64)rs->relchg_bits);
   return r <= rtol;
+}
+
+// rho^2 of a sweep of many bins in FP64 by a whole warp: the same terms as rho2_exact, lane i
+// summing the bins k0 + i, k0 + i + 32, ..., then a butterfly (a fixed order; every lane ends
+// with the same value).  Its rounding differs from the sequential sum's by a few parts in
+// 10^16; a decision that could differ lies within the near-threshold band.
+__device__ double rho2_exact_warp(const Grid& g, const Tables& tb, const double* __restrict__ Sg,
+                                  double a2, double lo, double hi) {
+  const int lane = threadIdx.x & 31;
+  Sweep sw;
+  sw.lo = lo;
+  sw.hi = hi;
+  sw.ka = (i64)floor(__dadd_rn(lo, 0.5));
+  sw.kb = (i64)floor(__dadd_rn(hi, 0.5));
+  const bool single = (sw.ka == sw.kb);
+  const long long k0 = sw.ka > g.k_lo ? sw.ka : g.k_lo;
+  const long long k1 = sw.kb < g.k_lo + g.nb - 1 ? sw.kb : g.k_lo + g.nb - 1;
+  double acc = 0.0;
+  for (long long k = k0 + lane; k <= k1; k += 32) {
+    const double w = single ? 1.0 : sweep_weight(sw, k);
+    if (w > 0.0) {
+      const long long j = k - g.k_lo;
+      const double sn = __dadd_rn(tb.S[j], Sg[j]);
+      const double psk = __dmul_rn(__dmul_rn(__dmul_rn(g.t5, tb.R[j]), a2), w);
+      acc = __dadd_rn(acc, __ddiv_rn(psk, sn));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, o));
+  return __dmul_rn(4.0, acc);
 }
 
 __device__ double rho2_exact(const Grid& g, const Tables& tb, const double* __restrict__ Sg,
@@ -2074,23 +2107,23 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
       pending &= pending - 1;
       int kcount;
       float r2 = screen_part(cd, cw, cd.pk[cw], g, tb, inv_f, lane, 32, kcount);
-      // butterfly sums: every lane ends with the same values
+      // butterfly sums: every lane ends with the same values.  The sum's longest sequential
+      // chain is the largest lane count, and the butterfly adds five roundings: the screen's
+      // bound takes that many terms, not every bin of the sweep
+      int kchain = kcount;
       for (int o = 16; o > 0; o >>= 1) {
         r2 = __fadd_rn(r2, __shfl_xor_sync(0xFFFFFFFFu, r2, o));
-        kcount += __shfl_xor_sync(0xFFFFFFFFu, kcount, o);
+        kchain = max(kchain, __shfl_xor_sync(0xFFFFFFFFu, kchain, o));
       }
-      int dec = screen_decide(r2, kcount, th2f, mode);
-      if (mode == 1 && lane == 0 && screen_uncertain(r2, kcount, th2f)) ++local_unc;
+      const int keff = kchain + 5;
+      int dec = screen_decide(r2, keff, th2f, mode);
+      if (mode == 1 && lane == 0 && screen_uncertain(r2, keff, th2f)) ++local_unc;
       if (dec < 0) {
-        // the oracle's order of summation, on one lane
-        int ex = 0;
-        if (lane == 0) {
-          ++local_exact;
-          const double v = rho2_exact(g, tb, Sg, cd.a2[cw], cd.lo[cw], cd.hi[cw]);
-          if (near_threshold(v, th2)) ++local_near;
-          ex = v > th2;
-        }
-        dec = __shfl_sync(0xFFFFFFFFu, ex, 0);
+        // FP64, the lanes sharing the bins
+        if (lane == 0) ++local_exact;
+        const double v = rho2_exact_warp(g, tb, Sg, cd.a2[cw], cd.lo[cw], cd.hi[cw]);
+        if (lane == 0 && near_threshold(v, th2)) ++local_near;
+        dec = v > th2 ? 1 : 0;
       }
       if (dec) {
         if (lane == 0) {
