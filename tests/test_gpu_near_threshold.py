@@ -2,8 +2,8 @@
 the C ABI, against the FP64 oracle.
 
 Sources are placed at rho = rho_th (1 + delta) for delta in +-{1e-10, 1e-8, 1e-6, 1e-5, 1e-4}
-on top of a dense faint background, with one-bin, three-bin, ten-bin (a whole warp walks
-it) and downward sweeps.  The sources sit 400 bins apart and the estimators are the median
+on top of a dense faint background, with one-bin, three-bin, ten-bin and forty-bin (a
+whole warp walks them, and recomputes them in FP64 across its lanes) and downward sweeps.  The sources sit 400 bins apart and the estimators are the median
 and the median then the mean over 101 bins: a resolvable source is among the brightest
 bins of every window it touches, so S_gal at its bins does not depend on its exact
 amplitude, and the amplitude that gives the wanted rho can be solved for against the
@@ -32,7 +32,8 @@ F_MAX = 3e-3
 W = 101
 DELTAS = [s * d for d in (1e-10, 1e-8, 1e-6, 1e-5, 1e-4) for s in (1.0, -1.0)]
 # (u0 - k, du) in bin units: the sweep [u0, u0 + du] of a source centred on bin k
-KINDS = {"single": (-0.3, 0.5), "three": (-0.3, 2.6), "ten": (-0.3, 9.4), "down": (0.2, -3.3)}
+KINDS = {"single": (-0.3, 0.5), "three": (-0.3, 2.6), "ten": (-0.3, 9.4),
+         "forty": (-0.3, 39.6), "down": (0.2, -3.3)}
 
 
 @pytest.fixture(scope="module", autouse=True)
