@@ -330,13 +330,11 @@ int sub_get_profile_iterations(sub_ctx* ctx, float* ms, int32_t cap);
  *   stream : cudaStream_t to run on (NULL: the legacy default stream).  The call
  *            returns after enqueueing.
  * Scratch lives in one static device array of about 21 MB that every GPU loading
- * the library holds until the process exits.  The first call on a device (with
- * that device current) looks up the array's device address; make that first call
- * before any stream capture.  The address is kept for the life of the process, so a
- * caller that resets a device (cudaDeviceReset) must not call this entry point on
- * that device afterwards; devices 0 .. 127 only.  All calls share the array and it
- * keeps the last call's contents: calls that overlap on the GPU race and must be
- * serialised by the caller.  Sizes beyond the limits return SUB_EINVAL with a message in
+ * the library holds until the process exits.  Every call asks the runtime for the
+ * array's address on the current device; the first call on a device loads the module
+ * there (which may allocate), so make it before any stream capture and before any
+ * phase that must not allocate.  All calls share the array and it keeps the last call's
+ * contents: calls that overlap on the GPU race and must be serialised by the caller.  Sizes beyond the limits return SUB_EINVAL with a message in
  * sub_last_error(NULL); CUDA failures return SUB_ECUDA. */
 int sub_running_mean_noalloc(const double* x, double* out, int64_t n, int32_t window,
                              void* stream);

@@ -16,7 +16,6 @@
 // the per-chunk scales and the underflow flags of all the bins and chunks it reads.
 
 #include <cstdio>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -43,8 +42,6 @@ constexpr long long kWords = 2 * kCells + kChunks;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kWords];
 
-std::mutex g_mu;
-unsigned long long* g_addr[128] = {nullptr};  // device address of the array, per device
 
 }  // namespace
 
@@ -76,30 +73,18 @@ extern "C" int sub_running_mean_noalloc(const double* x, double* out, int64_t n,
     set_global_error(msg);
     return SUB_ECUDA;
   }
-  if (dev < 0 || dev >= 128) {
-    snprintf(msg, sizeof(msg), "sub_running_mean_noalloc: device %d is beyond the 128 devices "
-             "this entry point keeps addresses for", dev);
+  // The host-side name of the array is only a stand-in: the runtime gives its device
+  // address on the current device.  Asked on every call (it allocates nothing once the
+  // module is loaded), so that no address outlives a reset of the device's context.
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    snprintf(msg, sizeof(msg), "sub_running_mean_noalloc: cudaGetSymbolAddress failed: %s",
+             cudaGetErrorString(e));
     set_global_error(msg);
-    return SUB_EINVAL;
+    return SUB_ECUDA;
   }
-  unsigned long long* base = nullptr;
-  {
-    // Once per device, with that device current: the host-side name of the array is
-    // only a stand-in, so ask the runtime for its device address.
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        snprintf(msg, sizeof(msg), "sub_running_mean_noalloc: cudaGetSymbolAddress failed: %s",
-                 cudaGetErrorString(e));
-        set_global_error(msg);
-        return SUB_ECUDA;
-      }
-      g_addr[dev] = (unsigned long long*)p;
-    }
-    base = g_addr[dev];
-  }
+  unsigned long long* base = (unsigned long long*)p;
   SmoothPlan pl = {};
   pl.W = window;
   pl.Kc = ((window + 31) / 32) * 32;
