@@ -1157,6 +1157,24 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
       __syncthreads();  // before the next chunk overwrites shared memory
       continue;
     }
+    // a chunk of zeros (no power in it: much of the band's high-frequency end before any
+    // removal) is sorted already: every key 0, ties in position order
+    {
+      bool nz = false;
+#pragma unroll
+      for (int a = 0; a < E; ++a) nz |= (tid * E + a < len) && k[a] != (K)0;
+      if (!__syncthreads_or(nz)) {
+#pragma unroll
+        for (int a = 0; a < E; ++a) {
+          const int i = tid * E + a;
+          if (i < len) {
+            skey[base + i] = (K)0;
+            srank[base + i] = (uint16_t)i;
+          }
+        }
+        continue;
+      }
+    }
     bool first_smem = true;
     for (int kk = 2; kk <= kpad; kk <<= 1) {
       int jj = kk >> 1;
@@ -1475,9 +1493,26 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   __shared__ int warp_ones[32];
 
   // 1. merged ranks.  Chunk u-1 precedes chunk u on equal keys (its positions are lower).
-  for (int i = tid; i < len0; i += T) sk[i] = skey[span + i];
-  for (int i = tid; i < len1; i += T) sk[Kc + i] = skey[span + Kc + i];
-  __syncthreads();
+  bool nz = false;
+  for (int i = tid; i < len0; i += T) {
+    const K v = skey[span + i];
+    sk[i] = v;
+    nz |= v != (K)0;
+  }
+  for (int i = tid; i < len1; i += T) {
+    const K v = skey[span + Kc + i];
+    sk[Kc + i] = v;
+    nz |= v != (K)0;
+  }
+  if (!__syncthreads_or(nz)) {
+    // both chunks hold only zeros: every window's median is 0
+    const int nz_out = (int)(j_hi - j_lo);
+    for (int t = tid; t < nz_out; t += T) {
+      const double rel = sg_store(o, j_lo + t, __dmul_rn(kMedianBias, 0.0));
+      relmax = rel > relmax ? rel : relmax;
+    }
+    return relmax;
+  }
   {
     // merge path: thread t emits the merged indices [d0, d1) of the two sorted chunks,
     // starting where a binary search on the diagonal d0 puts it
@@ -1706,6 +1741,21 @@ __device__ __forceinline__ void chunk_prefix(const SpecIn& in, long long n, cons
   }
   __syncthreads();
   const int sigma = sigma_from_max(warp_max[0]);
+  if (warp_max[0] == 0ull) {
+    // a chunk of zeros: every prefix is 0 and nothing fell below one unit
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i < per && p0 + i < len) {
+        pre_lo[base + p0 + i] = 0ull;
+        pre_hi[base + p0 + i] = 0ull;
+      }
+    }
+    if (threadIdx.x == 0) {
+      uflow[b] = 0u;
+      sig[b] = sigma;
+    }
+    return;
+  }
   // pass 2: thread totals in fixed point; note inputs > 0 below one unit
   U128 run{0ull, 0ull};
   int uf = 0;
