@@ -905,6 +905,14 @@ __device__ __forceinline__ double sg_store(const SgOut& o, long long j, double v
   return rel;
 }
 
+// Sum over the CTA of every thread's count c (0 <= c <= cmax, cmax the same in every thread),
+// by barrier reductions of its bits: a barrier, and no shared memory.
+__device__ __forceinline__ int cta_count(int c, int cmax) {
+  int total = 0;
+  for (int bit = 0; (1 << bit) <= cmax; ++bit) total += __syncthreads_count((c >> bit) & 1) << bit;
+  return total;
+}
+
 // ============================================================================ chunk sort
 // Chunks of Kc >= W consecutive bins: any window of at most W bins lies in at most two
 // consecutive chunks.  Each chunk is sorted once (keys: the bits of the non-negative
@@ -1158,12 +1166,14 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
       continue;
     }
     // a chunk of zeros (no power in it: much of the band's high-frequency end before any
-    // removal) is sorted already: every key 0, ties in position order
+    // removal) is sorted already: every key 0, ties in position order; a chunk with few
+    // nonzero bins is that order with the few merged in (the re-sort from an all-zero state)
     {
-      bool nz = false;
+      int nzc = 0;
 #pragma unroll
-      for (int a = 0; a < E; ++a) nz |= (tid * E + a < len) && k[a] != (K)0;
-      if (!__syncthreads_or(nz)) {
+      for (int a = 0; a < E; ++a) nzc += ((tid * E + a < len) && k[a] != (K)0) ? 1 : 0;
+      const int nzt = cta_count(nzc, E);
+      if (nzt == 0) {
 #pragma unroll
         for (int a = 0; a < E; ++a) {
           const int i = tid * E + a;
@@ -1173,6 +1183,20 @@ __global__ void __launch_bounds__(1024) k_chunk_sort(SpecIn in, long long n, Smo
           }
         }
         continue;
+      }
+      if (nzt <= kResortMax) {
+        K kz[E];
+        int rid[E];
+#pragma unroll
+        for (int a = 0; a < E; ++a) {
+          kz[a] = (K)0;
+          rid[a] = tid * E + a < len ? tid * E + a : 0;
+        }
+        if (resort_few_changes<E, K>(k, kz, rid, len, kpad, skey + base, srank + base,
+                                     sort_raw)) {
+          __syncthreads();  // before the next chunk overwrites shared memory
+          continue;
+        }
       }
     }
     bool first_smem = true;
@@ -1493,19 +1517,29 @@ __device__ __forceinline__ double median_tile(const K* __restrict__ skey,
   __shared__ int warp_ones[32];
 
   // 1. merged ranks.  Chunk u-1 precedes chunk u on equal keys (its positions are lower).
-  bool nz = false;
+  int nzc = 0;  // this thread's nonzero keys of the span
   for (int i = tid; i < len0; i += T) {
     const K v = skey[span + i];
     sk[i] = v;
-    nz |= v != (K)0;
+    nzc += v != (K)0 ? 1 : 0;
   }
   for (int i = tid; i < len1; i += T) {
     const K v = skey[span + Kc + i];
     sk[Kc + i] = v;
-    nz |= v != (K)0;
+    nzc += v != (K)0 ? 1 : 0;
   }
-  if (!__syncthreads_or(nz)) {
-    // both chunks hold only zeros: every window's median is 0
+  // Every window lies in the span; a window of c bins with fewer than ceil(c / 2) nonzero
+  // values has a zero median (both middle elements are zeros).  The smallest window of
+  // the tile is at one of its ends.
+  auto win = [&](long long j) {
+    const long long s0 = j - h > 0 ? j - h : 0;
+    const long long e0 = j - h + pl.W - 1 < n - 1 ? j - h + pl.W - 1 : n - 1;
+    return (int)(e0 - s0 + 1);
+  };
+  const int cmin = min(win(j_lo), win(j_hi - 1));
+  const int nzt = cta_count(nzc, 2 * ((Kc + T - 1) / T));  // a thread loads at most that many
+  if (nzt < (cmin + 1) / 2) {
+    // every window's median is 0
     const int nz_out = (int)(j_hi - j_lo);
     for (int t = tid; t < nz_out; t += T) {
       const double rel = sg_store(o, j_lo + t, __dmul_rn(kMedianBias, 0.0));
