@@ -274,7 +274,7 @@ static int reserve_sources(sub_ctx* c, int64_t n) {
     drop_graph(c);
     dfree(c, c->A); dfree(c, c->f); dfree(c, c->fdot); dfree(c, c->resolved);
     void* cds[] = {c->cd.src, c->cd.pk, c->cd.len, c->cd.a2, c->cd.amp, c->cd.lo, c->cd.hi,
-                   c->cd.res};
+                   c->cd.res, c->cd.wide};
     for (void* q : cds) dfree(c, q);
     c->A = c->f = c->fdot = nullptr;
     c->resolved = nullptr;
@@ -290,7 +290,8 @@ static int reserve_sources(sub_ctx* c, int64_t n) {
         (rc = dalloc(c, (void**)&c->cd.len, m * 4)) ||
         (rc = dalloc(c, (void**)&c->cd.a2, m * 8)) || (rc = dalloc(c, (void**)&c->cd.amp, m * 8)) ||
         (rc = dalloc(c, (void**)&c->cd.lo, m * 8)) ||
-        (rc = dalloc(c, (void**)&c->cd.hi, m * 8)) || (rc = dalloc(c, (void**)&c->cd.res, m))) {
+        (rc = dalloc(c, (void**)&c->cd.hi, m * 8)) || (rc = dalloc(c, (void**)&c->cd.res, m)) ||
+        (rc = dalloc(c, (void**)&c->cd.wide, m * 8))) {
       return rc;
     }
     c->cap_N = (int64_t)m;

@@ -264,7 +264,8 @@ __device__ __noinline__ double prepass_slow_warp(double A, double fs, double fds
 
 // Record of a kept candidate (rare; out of line).
 __device__ __noinline__ void emit_candidate(Cands cd, long long c, long long s, double A,
-                                            double fs, double fds, const Grid g) {
+                                            double fs, double fds, const Grid g,
+                                            unsigned long long* nwide) {
   Sweep sw = make_sweep(fs, fds, g.T, g.T2);
   const double a2 = __dmul_rn(A, A);
   cd.src[c] = s;
@@ -277,6 +278,7 @@ __device__ __noinline__ void emit_candidate(Cands cd, long long c, long long s, 
   cd.lo[c] = sw.lo;
   cd.hi[c] = sw.hi;
   cd.res[c] = 0;
+  if (sw.kb - sw.ka + 1 > kSnrLaneBins) cd.wide[atomicAdd(nwide, 1ull)] = c;
 }
 
 // The decision for one source once r (its rho_0^2 / 4 in units of 2^-96) is known: count
@@ -300,7 +302,7 @@ __device__ __forceinline__ void prepass_decide(double r, u64 tk_bits, u64 tl_bit
     b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
     if (live) {
       long long c = (long long)b0 + __popc(m & ((1u << lane) - 1u));
-      emit_candidate(cd, c, s, A, fs, fds, g);
+      emit_candidate(cd, c, s, A, fs, fds, g, &rs->nwide);
     }
   }
 }
@@ -2116,10 +2118,10 @@ __device__ __forceinline__ void remove_part(const Cands& cd, long long c, const 
 
 // Every lane screens one candidate of a group of 32: still unresolved, and S_n changed on
 // a bin of its sweep (else rho is the value already found below rho_th).  Candidates of a
-// few bins are then done by their own lane; longer sweeps (loud high-frequency sources
-// cover up to hundreds of bins) by the whole warp, the lanes sharing the bins, so that no
-// launch waits on one thread walking a long sweep.
-constexpr int kSnrLaneBins = 4;
+// few bins are done by their own lane.  Longer sweeps (loud high-frequency sources cover up
+// to hundreds of bins, and more) come from their own list, one per warp in turn over the
+// grid, the lanes sharing the bins: no launch waits on one thread walking a long sweep, nor
+// on one warp walking many.
 
 __global__ void __launch_bounds__(256) k_snr_resolve(
     Cands cd, Grid g, Tables tb, const double* __restrict__ Sg, const float* __restrict__ inv_f,
@@ -2127,11 +2129,12 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
     unsigned long long* __restrict__ acc, RunState* rs, Dirty d, int Kc, int sg_radius) {
   // the loop state, read by one thread per CTA (every thread of the grid loading the same
   // words would queue on one L2 line)
-  __shared__ long long snr_head[3];  // stop, iteration, live candidates
+  __shared__ long long snr_head[4];  // stop, iteration, live candidates, long sweeps
   if (threadIdx.x == 0) {
     snr_head[0] = (rs->final_pass || rtol_stop(rs, rtol)) ? 1 : 0;
     snr_head[1] = rs->iter;
     snr_head[2] = (long long)rs->nlive;
+    snr_head[3] = (long long)rs->nwide;
   }
   __syncthreads();
   if (snr_head[0]) return;
@@ -2147,7 +2150,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
   const long long ngroups = (nlive + 31) / 32;
   for (long long grp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; grp < ngroups;
        grp += nwarps) {
-    bool todo = false, wide = false;
+    bool todo = false;
     const long long c = grp + (long long)lane * ngroups;
     int4 pk = make_int4(0, 0, 0, 0);
     unsigned char done = 1;
@@ -2155,7 +2158,7 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
       done = cd.res[c];
       pk = cd.pk[c];
     }
-    if (!done) {
+    if (!done && pk.y <= kSnrLaneBins) {  // the long sweeps are taken below
       const int ka = pk.x;
       const int nbin = pk.y;
       long long c0 = ka < 0 ? 0 : ka / Kc;
@@ -2165,9 +2168,8 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
         long long c1 = kl / Kc;
         for (long long cc = c0; cc <= c1 && !todo; ++cc) todo = di.any(cc, sg_radius);
       }
-      wide = todo && nbin > kSnrLaneBins;
     }
-    if (todo && !wide) {
+    if (todo) {
       int kcount;
       const float r2 = screen_part(cd, c, pk, g, tb, inv_f, 0, 1, kcount);
       int dec = screen_decide(r2, kcount, th2f, mode);
@@ -2185,12 +2187,24 @@ __global__ void __launch_bounds__(256) k_snr_resolve(
         remove_part(cd, c, g, tb, acc, di, Kc, 0, 1);
       }
     }
-    unsigned pending = __ballot_sync(0xFFFFFFFFu, wide);
-    while (pending) {
-      const long long cw = grp + (long long)(__ffs(pending) - 1) * ngroups;
-      pending &= pending - 1;
+  }
+  // the long sweeps, one per warp at a time
+  const long long nwide = snr_head[3];
+  for (long long wi = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; wi < nwide;
+       wi += nwarps) {
+    const long long cw = cd.wide[wi];
+    if (cd.res[cw]) continue;  // the same in every lane
+    const int4 pkw = cd.pk[cw];
+    const long long c0 = pkw.x < 0 ? 0 : pkw.x / Kc;
+    long long kl = (long long)pkw.x + pkw.y - 1;
+    if (kl > g.nb - 1) kl = g.nb - 1;
+    bool t = false;
+    if (kl >= 0)
+      for (long long cc = c0 + lane; cc <= kl / Kc; cc += 32) t = t || di.any(cc, sg_radius);
+    if (!__any_sync(0xFFFFFFFFu, t)) continue;
+    {
       int kcount;
-      float r2 = screen_part(cd, cw, cd.pk[cw], g, tb, inv_f, lane, 32, kcount);
+      float r2 = screen_part(cd, cw, pkw, g, tb, inv_f, lane, 32, kcount);
       // butterfly sums: every lane ends with the same values.  The sum's longest sequential
       // chain is the largest lane count, and the butterfly adds five roundings: the screen's
       // bound takes that many terms, not every bin of the sweep

@@ -21,7 +21,10 @@ struct Cands {
   double* lo;         // sweep endpoints in bin units (exact path)
   double* hi;
   unsigned char* res; // 1 once resolved
+  long long* wide;    // the candidates whose sweeps cross more than kSnrLaneBins bins
 };
+// Sweeps of at most this many bins are screened by one lane; longer ones by a whole warp.
+constexpr int kSnrLaneBins = 4;
 
 // Loop state kept on the device for one run.
 struct RunState {
@@ -40,6 +43,7 @@ struct RunState {
   unsigned long long work[4];    // work-list items the loop kernels were handed (by list)
   unsigned long long nnear;      // FP64 decisions with |rho^2 / rho_th^2 - 1| < 2e-9
   unsigned long long nuncertain; // FP32 decisions (mixed precision) inside the screen's bound
+  unsigned long long nwide;      // entries of Cands::wide
   unsigned err;
   unsigned pad;
 };

@@ -288,10 +288,10 @@ static int64_t bins_of(double T_obs, double f_min, double f_max) {
 }
 
 // Device bytes of a context before it exists: the per-bin buffers (about 130 B/bin), the
-// 16 MB of hot-bin replicas and the per-source buffers (78 B/source), rounded up.
+// 16 MB of hot-bin replicas and the per-source buffers (94 B/source), rounded up.
 static int64_t predicted_bytes(const sub_server* s, double T_obs, int64_t n) {
   const int64_t nb = bins_of(T_obs, s->p.f_min, s->p.f_max);
-  return nb * 136 + ((int64_t)24 << 20) + n * 80;
+  return nb * 136 + ((int64_t)24 << 20) + n * 96;
 }
 
 static void CUDART_CB job_done(void* arg) {
