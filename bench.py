@@ -701,9 +701,10 @@ def main():
                 parity = {}
             parity["full_oracle_run"] = full
 
-    # per run: work lists, catalog pass, replica fold; then the iterations (and a final
-    # estimate when max_iter stops the loop)
-    launches = args.steps * (3 + st.iterations * kernels_per_iteration(est)
+    # per run: work lists, the two catalog passes (the one for generated catalogs leaves a
+    # stored catalog at once), replica fold; then the iterations (and a final estimate when
+    # max_iter stops the loop)
+    launches = args.steps * (4 + st.iterations * kernels_per_iteration(est)
                              + (0 if st.converged else kernels_per_iteration(est)))
     line = {
         "metric": "sources subtracted/sec to convergence", "value": value, "unit": "sources/s",
